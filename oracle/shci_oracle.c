@@ -1,0 +1,554 @@
+/*
+ * CPU oracle for the SHCI variational hot path -- TEST INFRASTRUCTURE ONLY.
+ *
+ * Only tests/, __graft_entry__.smoke() and bench.py's cpu_baseline / reference
+ * legs may load this library.  It shares no code with the CUDA library: it is
+ * a plain, slow, obviously correct restatement of what the method computes,
+ * written in the spin-orbital operator language rather than the alpha/beta
+ * string language the GPU kernels use.
+ *
+ * Conventions (readings of the paper, which does not print them):
+ *   - Determinants are bit-packed uint64 words, orbital n at bit (n & 63) of
+ *     word (n >> 6) (Sec. IV.A); a determinant row is W alpha words then W
+ *     beta words.
+ *   - Spin-orbital so in [0, 2n): so < n is alpha orbital so, so >= n is beta
+ *     orbital so - n.  |D> = prod_{so ascending, occupied} a+_so |0>, i.e. all
+ *     alpha creators (ascending) to the left of all beta creators (ascending).
+ *   - H = E_core + sum_{PQ} h_PQ a+_P a_Q + 1/2 sum_{PQRS} (PQ|RS) a+_P a+_R a_S a_Q
+ *     over spin-orbitals, (PQ|RS) = (pq|rs) delta(s_P,s_Q) delta(s_R,s_S),
+ *     chemists' notation, real orbitals, 8-fold packed storage.
+ *   - Matrix elements are nonzero only for the diagonal and for single and
+ *     double excitations (Sec. III): the Slater-Condon rules below.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef struct {
+    int n;              /* spatial orbitals */
+    int W;              /* 64-bit words per spin string */
+    double e_core;
+    const double *h;    /* n*n row-major */
+    const double *eri;  /* packed */
+} oints;
+
+/* ------------------------------------------------------------ integrals */
+
+static int64_t pair_of(int p, int q)
+{
+    if (p < q) { int t = p; p = q; q = t; }
+    return (int64_t)p * (p + 1) / 2 + q;
+}
+
+/* (pq|rs), chemists' notation, from the 8-fold packed array. */
+static double eri_at(const oints *I, int p, int q, int r, int s)
+{
+    int64_t a = pair_of(p, q), b = pair_of(r, s);
+    if (a < b) { int64_t t = a; a = b; b = t; }
+    return I->eri[a * (a + 1) / 2 + b];
+}
+
+/* spin-orbital helpers */
+static int so_spin(const oints *I, int so) { return so >= I->n; }
+static int so_orb(const oints *I, int so) { return so >= I->n ? so - I->n : so; }
+
+/* (PQ|RS) over spin-orbitals: zero unless spin(P)=spin(Q) and spin(R)=spin(S). */
+static double eri_so(const oints *I, int P, int Q, int R, int S)
+{
+    if (so_spin(I, P) != so_spin(I, Q) || so_spin(I, R) != so_spin(I, S)) return 0.0;
+    return eri_at(I, so_orb(I, P), so_orb(I, Q), so_orb(I, R), so_orb(I, S));
+}
+
+static double h_so(const oints *I, int P, int Q)
+{
+    if (so_spin(I, P) != so_spin(I, Q)) return 0.0;
+    return I->h[so_orb(I, P) * I->n + so_orb(I, Q)];
+}
+
+/* ------------------------------------------------------------ operators */
+
+static int occ(const oints *I, const uint64_t *d, int so)
+{
+    int spin = so_spin(I, so), p = so_orb(I, so);
+    return (int)((d[spin * I->W + (p >> 6)] >> (p & 63)) & 1u);
+}
+
+static void put(const oints *I, uint64_t *d, int so, int v)
+{
+    int spin = so_spin(I, so), p = so_orb(I, so);
+    uint64_t bit = (uint64_t)1 << (p & 63);
+    if (v) d[spin * I->W + (p >> 6)] |= bit;
+    else d[spin * I->W + (p >> 6)] &= ~bit;
+}
+
+/* number of occupied spin-orbitals that precede so in the creator ordering */
+static int n_before(const oints *I, const uint64_t *d, int so)
+{
+    int c = 0;
+    for (int t = 0; t < so; t++) c += occ(I, d, t);
+    return c;
+}
+
+/* a_so |d>: returns the phase (+1/-1) and updates d, or 0 if so is empty. */
+static int annihilate(const oints *I, uint64_t *d, int so)
+{
+    if (!occ(I, d, so)) return 0;
+    int ph = (n_before(I, d, so) & 1) ? -1 : 1;
+    put(I, d, so, 0);
+    return ph;
+}
+
+/* a+_so |d>: returns the phase and updates d, or 0 if so is occupied. */
+static int create(const oints *I, uint64_t *d, int so)
+{
+    if (occ(I, d, so)) return 0;
+    int ph = (n_before(I, d, so) & 1) ? -1 : 1;
+    put(I, d, so, 1);
+    return ph;
+}
+
+/* ------------------------------------------------------------ Slater-Condon */
+
+static double diag_element(const oints *I, const uint64_t *d)
+{
+    int nso = 2 * I->n;
+    double e = I->e_core;
+    for (int k = 0; k < nso; k++) {
+        if (!occ(I, d, k)) continue;
+        e += h_so(I, k, k);
+        for (int l = 0; l < nso; l++) {
+            if (!occ(I, d, l)) continue;
+            e += 0.5 * (eri_so(I, k, k, l, l) - eri_so(I, k, l, l, k));
+        }
+    }
+    return e;
+}
+
+/* <D_i| H |D_j> */
+static double matrix_element(const oints *I, const uint64_t *di, const uint64_t *dj)
+{
+    int nso = 2 * I->n;
+    int holes[3], parts[3], nh = 0, np = 0;   /* holes: in j only; particles: in i only */
+    for (int so = 0; so < nso; so++) {
+        int a = occ(I, di, so), b = occ(I, dj, so);
+        if (b && !a) { if (nh < 3) holes[nh] = so; nh++; }
+        if (a && !b) { if (np < 3) parts[np] = so; np++; }
+    }
+    if (nh != np || nh > 2) return 0.0;
+    if (nh == 0) return diag_element(I, di);
+    uint64_t t[8];
+    memcpy(t, dj, sizeof(uint64_t) * 2 * I->W);
+    if (nh == 1) {
+        int q = holes[0], p = parts[0];
+        int ph = annihilate(I, t, q);
+        ph *= create(I, t, p);                 /* a+_p a_q |D_j> = ph |D_i> */
+        double v = h_so(I, p, q);
+        for (int k = 0; k < nso; k++) {
+            if (!(occ(I, di, k) && occ(I, dj, k))) continue;   /* common occupied */
+            v += eri_so(I, p, q, k, k) - eri_so(I, p, k, k, q);
+        }
+        return ph * v;
+    }
+    {
+        int q = holes[0], s = holes[1], p = parts[0], r = parts[1];
+        int ph = annihilate(I, t, q);
+        ph *= annihilate(I, t, s);
+        ph *= create(I, t, r);
+        ph *= create(I, t, p);                 /* a+_p a+_r a_s a_q |D_j> = ph |D_i> */
+        double v = eri_so(I, p, q, r, s) - eri_so(I, p, s, r, q);
+        return ph * v;
+    }
+}
+
+static int exc_degree2(int W, const uint64_t *a, const uint64_t *b)
+{
+    int c = 0;
+    for (int w = 0; w < 2 * W; w++) c += __builtin_popcountll(a[w] ^ b[w]);
+    return c;   /* twice the excitation degree */
+}
+
+/* ------------------------------------------------------------ exported API */
+
+double oracle_hij(int n, int W, double e_core, const double *h, const double *eri,
+                  const uint64_t *di, const uint64_t *dj)
+{
+    oints I = {n, W, e_core, h, eri};
+    return matrix_element(&I, di, dj);
+}
+
+void oracle_hdiag(int n, int W, double e_core, const double *h, const double *eri,
+                  int64_t n_det, const uint64_t *dets, double *out)
+{
+    oints I = {n, W, e_core, h, eri};
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < n_det; i++) out[i] = diag_element(&I, dets + i * 2 * W);
+}
+
+/*
+ * Brute force (a) of Sec. III: loop over all pairs i < j and keep those whose
+ * determinants differ by one or two excitations.  Writes up to cap pairs in
+ * (i, j) lexicographic order and returns the total count.
+ */
+int64_t oracle_pairs_allpairs(int64_t n_det, int W, const uint64_t *dets, int64_t cap,
+                              int64_t *i_out, int64_t *j_out)
+{
+    int64_t *cnt = (int64_t *)calloc((size_t)n_det + 1, sizeof(int64_t));
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < n_det; i++) {
+        int64_t c = 0;
+        for (int64_t j = i + 1; j < n_det; j++) {
+            int d = exc_degree2(W, dets + i * 2 * W, dets + j * 2 * W);
+            if (d == 2 || d == 4) c++;
+        }
+        cnt[i + 1] = c;
+    }
+    for (int64_t i = 0; i < n_det; i++) cnt[i + 1] += cnt[i];
+    int64_t total = cnt[n_det];
+    if (total <= cap) {
+#pragma omp parallel for schedule(dynamic, 16)
+        for (int64_t i = 0; i < n_det; i++) {
+            int64_t o = cnt[i];
+            for (int64_t j = i + 1; j < n_det; j++) {
+                int d = exc_degree2(W, dets + i * 2 * W, dets + j * 2 * W);
+                if (d == 2 || d == 4) { i_out[o] = i; j_out[o] = j; o++; }
+            }
+        }
+    }
+    free(cnt);
+    return total;
+}
+
+/* ---- open-addressing table from determinant words to index (brute force b) */
+
+typedef struct { int64_t cap; int64_t *slot; const uint64_t *dets; int W; } dtable;
+
+static uint64_t mix64(uint64_t z)
+{
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+static uint64_t det_hash(int W, const uint64_t *d)
+{
+    uint64_t hsh = 0x9E3779B97F4A7C15ull;
+    for (int w = 0; w < 2 * W; w++) hsh = mix64(hsh ^ d[w]);
+    return hsh;
+}
+
+static int dtable_init(dtable *t, int64_t n_det, int W, const uint64_t *dets)
+{
+    t->cap = 16;
+    while (t->cap < 2 * n_det + 16) t->cap <<= 1;
+    t->slot = (int64_t *)malloc(sizeof(int64_t) * t->cap);
+    if (!t->slot) return -1;
+    for (int64_t s = 0; s < t->cap; s++) t->slot[s] = -1;
+    t->dets = dets; t->W = W;
+    for (int64_t i = 0; i < n_det; i++) {
+        uint64_t s = det_hash(W, dets + i * 2 * W) & (uint64_t)(t->cap - 1);
+        while (t->slot[s] >= 0) {
+            if (memcmp(dets + t->slot[s] * 2 * W, dets + i * 2 * W, 16 * W) == 0) return -2;
+            s = (s + 1) & (uint64_t)(t->cap - 1);
+        }
+        t->slot[s] = i;
+    }
+    return 0;
+}
+
+static int64_t dtable_find(const dtable *t, const uint64_t *d)
+{
+    uint64_t s = det_hash(t->W, d) & (uint64_t)(t->cap - 1);
+    while (t->slot[s] >= 0) {
+        if (memcmp(t->dets + t->slot[s] * 2 * t->W, d, 16 * t->W) == 0) return t->slot[s];
+        s = (s + 1) & (uint64_t)(t->cap - 1);
+    }
+    return -1;
+}
+
+/* 0: ok; -2: duplicate determinants */
+int oracle_check_unique(int64_t n_det, int W, const uint64_t *dets)
+{
+    dtable t;
+    int rc = dtable_init(&t, n_det, W, dets);
+    free(t.slot);
+    return rc;
+}
+
+static int cmp_i64(const void *a, const void *b)
+{
+    int64_t x = *(const int64_t *)a, y = *(const int64_t *)b;
+    return (x > y) - (x < y);
+}
+
+/* all determinants of V that one or two excitations of d reach (indices, unsorted) */
+static int64_t generate_connections(const oints *I, const dtable *t, const uint64_t *d,
+                                    int64_t *out, int64_t cap)
+{
+    int nso = 2 * I->n;
+    int64_t m = 0;
+    uint64_t x[8];
+    int W2 = 2 * I->W;
+    for (int q = 0; q < nso; q++) {
+        if (!occ(I, d, q)) continue;
+        for (int p = 0; p < nso; p++) {            /* singles q -> p, same spin */
+            if (occ(I, d, p) || so_spin(I, p) != so_spin(I, q)) continue;
+            memcpy(x, d, 8 * W2); put(I, x, q, 0); put(I, x, p, 1);
+            int64_t j = dtable_find(t, x);
+            if (j >= 0) { if (m < cap) out[m] = j; m++; }
+        }
+        for (int s = q + 1; s < nso; s++) {        /* doubles {q,s} -> {p,r} */
+            if (!occ(I, d, s)) continue;
+            for (int p = 0; p < nso; p++) {
+                if (occ(I, d, p)) continue;
+                for (int r = p + 1; r < nso; r++) {
+                    if (occ(I, d, r)) continue;
+                    int nq = so_spin(I, q) + so_spin(I, s), npr = so_spin(I, p) + so_spin(I, r);
+                    if (nq != npr) continue;        /* conserve the number of beta electrons */
+                    memcpy(x, d, 8 * W2);
+                    put(I, x, q, 0); put(I, x, s, 0); put(I, x, p, 1); put(I, x, r, 1);
+                    int64_t j = dtable_find(t, x);
+                    if (j >= 0) { if (m < cap) out[m] = j; m++; }
+                }
+            }
+        }
+    }
+    return m;
+}
+
+/*
+ * Brute force (b) of Sec. III: generate every single and double excitation of
+ * each determinant and look it up in V.  Same output contract as
+ * oracle_pairs_allpairs.  Returns -2 on duplicate determinants, -1 on OOM.
+ */
+int64_t oracle_pairs_generate(int n, int64_t n_det, int W, const uint64_t *dets, int64_t cap,
+                              int64_t *i_out, int64_t *j_out)
+{
+    oints I = {n, W, 0.0, NULL, NULL};
+    dtable t;
+    int rc = dtable_init(&t, n_det, W, dets);
+    if (rc) { free(t.slot); return rc; }
+    int64_t *cnt = (int64_t *)calloc((size_t)n_det + 1, sizeof(int64_t));
+    int64_t max_conn = 0;
+    {
+        /* bound: singles ne*(2n-ne) plus doubles C(ne,2)*C(2n-ne,2) */
+        int64_t ne = 0;
+        for (int w = 0; w < 2 * W; w++) ne += __builtin_popcountll(dets[w]);
+        int64_t nv = 2 * (int64_t)n - ne;
+        max_conn = ne * nv + (ne * (ne - 1) / 2) * (nv * (nv - 1) / 2) + 16;
+    }
+    int64_t total = 0;
+#pragma omp parallel
+    {
+        int64_t *buf = (int64_t *)malloc(sizeof(int64_t) * max_conn);
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t i = 0; i < n_det; i++) {
+            int64_t m = generate_connections(&I, &t, dets + i * 2 * W, buf, max_conn);
+            int64_t c = 0;
+            for (int64_t k = 0; k < m; k++) c += buf[k] > i;
+            cnt[i + 1] = c;
+        }
+#pragma omp single
+        {
+            for (int64_t i = 0; i < n_det; i++) cnt[i + 1] += cnt[i];
+            total = cnt[n_det];
+        }
+        if (total <= cap) {
+#pragma omp for schedule(dynamic, 16)
+            for (int64_t i = 0; i < n_det; i++) {
+                int64_t m = generate_connections(&I, &t, dets + i * 2 * W, buf, max_conn);
+                int64_t o = cnt[i];
+                qsort(buf, (size_t)m, sizeof(int64_t), cmp_i64);
+                for (int64_t k = 0; k < m; k++)
+                    if (buf[k] > i) { i_out[o] = i; j_out[o] = buf[k]; o++; }
+            }
+        }
+        free(buf);
+    }
+    free(cnt);
+    free(t.slot);
+    return total;
+}
+
+/* H_ij for a list of pairs */
+void oracle_hij_list(int n, int W, double e_core, const double *h, const double *eri,
+                     const uint64_t *dets, int64_t m, const int64_t *ii, const int64_t *jj,
+                     double *out)
+{
+    oints I = {n, W, e_core, h, eri};
+#pragma omp parallel for schedule(static)
+    for (int64_t k = 0; k < m; k++)
+        out[k] = matrix_element(&I, dets + ii[k] * 2 * W, dets + jj[k] * 2 * W);
+}
+
+/*
+ * Row i of the full Hamiltonian by brute force over all j: the connected
+ * columns (j != i, ascending) and their values.  Returns the number of
+ * connected columns (writes at most cap).
+ */
+int64_t oracle_row(int n, int W, double e_core, const double *h, const double *eri,
+                   int64_t n_det, const uint64_t *dets, int64_t i, int64_t cap,
+                   int64_t *cols, double *vals)
+{
+    oints I = {n, W, e_core, h, eri};
+    int64_t m = 0;
+    const uint64_t *di = dets + i * 2 * W;
+    for (int64_t j = 0; j < n_det; j++) {
+        if (j == i) continue;
+        int d = exc_degree2(W, di, dets + j * 2 * W);
+        if (d == 2 || d == 4) {
+            if (m < cap) { cols[m] = j; vals[m] = matrix_element(&I, di, dets + j * 2 * W); }
+            m++;
+        }
+    }
+    return m;
+}
+
+/*
+ * sigma = H c for the listed rows, by brute force over all columns, with
+ * long-double accumulation.  c is [k][n_det]; out is [k][n_rows].
+ */
+void oracle_sigma_rows(int n, int W, double e_core, const double *h, const double *eri,
+                       int64_t n_det, const uint64_t *dets, int k, const double *c,
+                       int64_t n_rows, const int64_t *rows, double *out)
+{
+    oints I = {n, W, e_core, h, eri};
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t r = 0; r < n_rows; r++) {
+        int64_t i = rows[r];
+        const uint64_t *di = dets + i * 2 * W;
+        long double acc[16];
+        for (int v = 0; v < k; v++) acc[v] = 0.0L;
+        for (int64_t j = 0; j < n_det; j++) {
+            int d = exc_degree2(W, di, dets + j * 2 * W);
+            if (d > 4) continue;
+            double hij = matrix_element(&I, di, dets + j * 2 * W);
+            for (int v = 0; v < k; v++) acc[v] += (long double)hij * c[v * n_det + j];
+        }
+        for (int v = 0; v < k; v++) out[v * n_rows + r] = (double)acc[v];
+    }
+}
+
+/*
+ * sigma = H c from an upper-triangle pair list (i < j) plus the diagonal, with
+ * long-double accumulation (sequential, deterministic).
+ */
+void oracle_sigma_pairs(int64_t n_det, int64_t m, const int64_t *ii, const int64_t *jj,
+                        const double *hij, const double *diag, int k, const double *c,
+                        double *out)
+{
+    long double *acc = (long double *)calloc((size_t)n_det * k, sizeof(long double));
+    for (int v = 0; v < k; v++)
+        for (int64_t i = 0; i < n_det; i++)
+            acc[v * n_det + i] = (long double)diag[i] * c[v * n_det + i];
+    for (int64_t p = 0; p < m; p++) {
+        int64_t i = ii[p], j = jj[p];
+        for (int v = 0; v < k; v++) {
+            acc[v * n_det + i] += (long double)hij[p] * c[v * n_det + j];
+            acc[v * n_det + j] += (long double)hij[p] * c[v * n_det + i];
+        }
+    }
+    for (int64_t x = 0; x < n_det * k; x++) out[x] = (double)acc[x];
+    free(acc);
+}
+
+/* ------------------------------------------------------------ density matrices */
+
+/*
+ * One- and two-body reduced density matrices of Psi = sum_i c_i |D_i> within V:
+ *   gamma_pq    = sum_s <Psi| a+_ps a_qs |Psi>
+ *   Gamma_pqrs  = sum_{s,t} <Psi| a+_ps a+_rt a_st a_qs |Psi>
+ * by applying the operator string to every |D_i> and projecting on V.  The
+ * requested entries are given as index lists (spatial orbitals).
+ */
+static double rdm1_entry(const oints *I, const dtable *t, int64_t n_det, const uint64_t *dets,
+                         const double *c, int p, int q)
+{
+    long double acc = 0.0L;
+    uint64_t x[8];
+    int W2 = 2 * I->W;
+    for (int spin = 0; spin < 2; spin++) {
+        int P = p + spin * I->n, Q = q + spin * I->n;
+        for (int64_t i = 0; i < n_det; i++) {
+            if (c[i] == 0.0) continue;
+            memcpy(x, dets + i * W2, 8 * W2);
+            int ph = annihilate(I, x, Q);
+            if (!ph) continue;
+            ph *= create(I, x, P);
+            if (!ph) continue;
+            int64_t j = dtable_find(t, x);
+            if (j >= 0) acc += (long double)ph * c[j] * c[i];
+        }
+    }
+    return (double)acc;
+}
+
+static double rdm2_entry(const oints *I, const dtable *t, int64_t n_det, const uint64_t *dets,
+                         const double *c, int p, int q, int r, int s)
+{
+    long double acc = 0.0L;
+    uint64_t x[8];
+    int W2 = 2 * I->W;
+    for (int s1 = 0; s1 < 2; s1++)
+        for (int s2 = 0; s2 < 2; s2++) {
+            int P = p + s1 * I->n, Q = q + s1 * I->n, R = r + s2 * I->n, S = s + s2 * I->n;
+            for (int64_t i = 0; i < n_det; i++) {
+                if (c[i] == 0.0) continue;
+                memcpy(x, dets + i * W2, 8 * W2);
+                int ph = annihilate(I, x, Q);
+                if (!ph) continue;
+                ph *= annihilate(I, x, S);
+                if (!ph) continue;
+                ph *= create(I, x, R);
+                if (!ph) continue;
+                ph *= create(I, x, P);
+                if (!ph) continue;
+                int64_t j = dtable_find(t, x);
+                if (j >= 0) acc += (long double)ph * c[j] * c[i];
+            }
+        }
+    return (double)acc;
+}
+
+/* entries of gamma: idx = [m][2] (p, q); returns 0, or -2 on duplicates */
+int oracle_rdm1(int n, int W, int64_t n_det, const uint64_t *dets, const double *c,
+                int64_t m, const int32_t *idx, double *out)
+{
+    oints I = {n, W, 0.0, NULL, NULL};
+    dtable t;
+    int rc = dtable_init(&t, n_det, W, dets);
+    if (rc) { free(t.slot); return rc; }
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t e = 0; e < m; e++)
+        out[e] = rdm1_entry(&I, &t, n_det, dets, c, idx[2 * e], idx[2 * e + 1]);
+    free(t.slot);
+    return 0;
+}
+
+/* entries of Gamma: idx = [m][4] (p, q, r, s) */
+int oracle_rdm2(int n, int W, int64_t n_det, const uint64_t *dets, const double *c,
+                int64_t m, const int32_t *idx, double *out)
+{
+    oints I = {n, W, 0.0, NULL, NULL};
+    dtable t;
+    int rc = dtable_init(&t, n_det, W, dets);
+    if (rc) { free(t.slot); return rc; }
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t e = 0; e < m; e++)
+        out[e] = rdm2_entry(&I, &t, n_det, dets, c, idx[4 * e], idx[4 * e + 1],
+                            idx[4 * e + 2], idx[4 * e + 3]);
+    free(t.slot);
+    return 0;
+}
+
+int oracle_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

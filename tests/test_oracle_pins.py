@@ -1,0 +1,313 @@
+"""Pins for the CPU oracle: checks against things other than the oracle itself.
+
+* the second-quantised Hamiltonian built from operator matrices (tests/jw.py),
+* hand-worked excitation signs (tests/golden/slater_condon_signs.json),
+* closed forms (one electron; no two-body term; one alpha + one beta electron),
+* invariants (Hermiticity, orbital-rotation invariance of the full-CI spectrum),
+* the two brute-force pair definitions of Sec. III agreeing with each other,
+* the Davidson iteration against a dense eigensolver and ARPACK,
+* density-matrix identities and central finite differences of the energy,
+* planted mistakes in a copy of the oracle's C source being caught.
+"""
+import itertools
+import json
+import os
+import shutil
+import subprocess
+import ctypes
+
+import numpy as np
+import pytest
+
+import shci_synth as S
+from tests import jw
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def small_system(n, rank, seed):
+    h, eri, ec = S.integrals(n, rank, seed)
+    return h, eri, ec
+
+
+def rotate(h, eri, U):
+    n = h.shape[0]
+    g = jw.eri_full(eri, n)
+    h2 = U.T @ h @ U
+    g2 = np.einsum("pqrs,pa,qb,rc,sd->abcd", g, U, U, U, U, optimize=True)
+    packed = np.empty(S.eri_len(n))
+    for p in range(n):
+        for q in range(p + 1):
+            for r in range(n):
+                for s in range(r + 1):
+                    a = p * (p + 1) // 2 + q
+                    b = r * (r + 1) // 2 + s
+                    if a >= b:
+                        packed[a * (a + 1) // 2 + b] = g2[p, q, r, s]
+    return 0.5 * (h2 + h2.T), packed
+
+
+# ------------------------------------------------------------------ JW pin
+
+@pytest.mark.parametrize("n,na,nb", [(3, 1, 1), (3, 2, 1), (4, 2, 2), (4, 3, 1), (4, 2, 1)])
+def test_matrix_elements_match_second_quantised_h(oracle_mod, n, na, nb):
+    h, eri, _ = small_system(n, 5, 100 + 10 * n + na)
+    e_core = 0.37
+    dets = S.fci_dets(n, na, nb)
+    ref = jw.projected(h, eri, dets, e_core)
+    got = oracle_mod.System(h, eri, e_core).dense_h(dets)
+    np.testing.assert_allclose(got, ref, atol=1e-12, rtol=0)
+    # the pair set of brute force (a) is exactly the structurally connected set
+    nz = np.abs(np.triu(ref, 1)) > 1e-14
+    ii, jj = oracle_mod.pairs_allpairs(dets)
+    mask = np.zeros_like(nz)
+    mask[ii, jj] = True
+    assert not np.any(nz & ~mask)          # every nonzero element is a listed pair
+
+
+# ------------------------------------------------------------------ hand signs
+
+def test_hand_worked_signs(oracle_mod):
+    spec = json.load(open(os.path.join(HERE, "golden", "slater_condon_signs.json")))
+    n = spec["integrals"]["n_orb"]
+    h, eri, _ = S.integrals(n, spec["integrals"]["rank"], spec["integrals"]["seed"])
+    g = jw.eri_full(eri, n)
+    O = oracle_mod.System(h, eri, 0.0)
+    for case in spec["cases"]:
+        def det(occ):
+            a = S.strings_from_occ(np.array([occ[0]], dtype=np.int64).reshape(1, -1), n)
+            b = S.strings_from_occ(np.array([occ[1]], dtype=np.int64).reshape(1, -1), n)
+            return np.concatenate([a, b], axis=1)[0]
+        val = 0.0
+        for coef, kind, idx in case["terms"]:
+            val += coef * (h[idx[0], idx[1]] if kind == "h" else g[tuple(idx)])
+        want = case["sign"] * val
+        got = O.hij(det(case["i"]), det(case["j"]))
+        assert abs(got - want) < 1e-14, case["name"]
+        # Hermiticity: the reverse element through the other hole/particle assignment
+        assert abs(O.hij(det(case["j"]), det(case["i"])) - want) < 1e-14, case["name"]
+
+
+# ------------------------------------------------------------------ closed forms
+
+def test_one_electron_is_h(oracle_mod):
+    n = 7
+    h, eri, _ = small_system(n, 4, 5)
+    dets = S.fci_dets(n, 1, 0)
+    H = oracle_mod.System(h, eri, 0.0).dense_h(dets)
+    np.testing.assert_allclose(H, h, atol=1e-15, rtol=0)
+
+
+def test_no_two_body_term_gives_orbital_sums(oracle_mod):
+    n, na, nb = 6, 2, 3
+    h, eri, _ = small_system(n, 4, 6)
+    eri = np.zeros_like(eri)
+    dets = S.fci_dets(n, na, nb)
+    w = np.linalg.eigvalsh(oracle_mod.System(h, eri, 0.0).dense_h(dets))
+    eps = np.linalg.eigvalsh(h)
+    sums = sorted(sum(eps[list(a)]) + sum(eps[list(b)])
+                  for a in itertools.combinations(range(n), na)
+                  for b in itertools.combinations(range(n), nb))
+    np.testing.assert_allclose(w, sums, atol=1e-12)
+
+
+def test_one_alpha_one_beta_is_kronecker_form(oracle_mod):
+    n = 6
+    h, eri, _ = small_system(n, 5, 9)
+    g = jw.eri_full(eri, n)
+    dets = S.fci_dets(n, 1, 1)               # alpha index major, beta minor
+    H = oracle_mod.System(h, eri, 0.0).dense_h(dets)
+    V = np.einsum("prqs->pqrs", g).reshape(n * n, n * n)   # V[(p,q),(r,s)] = (pr|qs)
+    ref = np.kron(h, np.eye(n)) + np.kron(np.eye(n), h) + V
+    np.testing.assert_allclose(H, ref, atol=1e-13, rtol=0)
+
+
+# ------------------------------------------------------------------ invariants
+
+def test_hermitian_random_pairs(oracle_mod):
+    cfg = S.config("sel_24o_6a6b_1m")
+    h, eri, ec, dets = S.make_system(cfg, n_det=3000)
+    O = oracle_mod.System(h, eri, ec)
+    ii, jj = oracle_mod.pairs_allpairs(dets)
+    rng = np.random.default_rng(0)
+    sel = rng.choice(ii.size, size=min(4000, ii.size), replace=False)
+    a = O.hij_list(dets, ii[sel], jj[sel])
+    b = O.hij_list(dets, jj[sel], ii[sel])
+    np.testing.assert_allclose(a, b, atol=1e-14, rtol=0)
+
+
+def test_fci_spectrum_invariant_under_orbital_rotation(oracle_mod):
+    n, na, nb = 6, 3, 2
+    h, eri, _ = small_system(n, 6, 11)
+    dets = S.fci_dets(n, na, nb)
+    w0 = np.linalg.eigvalsh(oracle_mod.System(h, eri, 0.0).dense_h(dets))
+    U, _ = np.linalg.qr(np.random.default_rng(3).normal(size=(n, n)))
+    h2, eri2 = rotate(h, eri, U)
+    w1 = np.linalg.eigvalsh(oracle_mod.System(h2, eri2, 0.0).dense_h(dets))
+    np.testing.assert_allclose(w0, w1, atol=1e-10)
+
+
+# ------------------------------------------------------------------ pair sets
+
+@pytest.mark.parametrize("cfgname,n_det", [("fci_10o_4a4b", None), ("sel_24o_6a6b_1m", 20000),
+                                           ("sel_20o_5a5b_1m", 20000)])
+def test_two_brute_force_pair_definitions_agree(oracle_mod, cfgname, n_det):
+    cfg = S.config(cfgname)
+    h, eri, ec, dets = S.make_system(cfg, n_det=n_det)
+    a = oracle_mod.pairs_allpairs(dets)
+    b = oracle_mod.pairs_generate(dets, cfg.n_orb)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    if cfgname == "fci_10o_4a4b":
+        # full-CI: every determinant has (24+24+90+90+576) = 804 connections
+        assert a[0].size == 44100 * 804 // 2
+
+
+def test_duplicates_detected(oracle_mod):
+    dets = S.fci_dets(5, 2, 2)
+    assert not oracle_mod.has_duplicates(dets)
+    bad = np.concatenate([dets, dets[3:4]])
+    assert oracle_mod.has_duplicates(bad)
+
+
+# ------------------------------------------------------------------ sigma
+
+def test_sigma_rows_and_pairs_match_dense(oracle_mod):
+    cfg = S.config("sel_24o_6a6b_1m")
+    h, eri, ec, dets = S.make_system(cfg, n_det=1500)
+    O = oracle_mod.System(h, eri, ec)
+    H = O.dense_h(dets)
+    c = S.random_vectors(dets.shape[0], 2, 5)
+    ref = c @ H.T
+    rows = np.arange(dets.shape[0])
+    np.testing.assert_allclose(O.sigma_rows(dets, c, rows), ref, atol=1e-11)
+    ii, jj, v = O.upper_pairs(dets)
+    np.testing.assert_allclose(oracle_mod.sigma_pairs(dets.shape[0], ii, jj, v, O.hdiag(dets), c), ref,
+                               atol=1e-11)
+    cols, vals = O.row(dets, 17)
+    dense_row = H[17].copy()
+    dense_row[17] = 0.0
+    nzc = np.nonzero(np.abs(dense_row) > 0)[0]
+    assert set(nzc.tolist()) <= set(cols.tolist())
+    np.testing.assert_allclose(vals, H[17, cols], atol=1e-15)
+
+
+# ------------------------------------------------------------------ eigenpairs
+
+def test_davidson_matches_dense_and_arpack(oracle_mod):
+    import scipy.sparse.linalg as sla
+    cfg = S.config("sel_24o_6a6b_1m")
+    h, eri, ec, dets = S.make_system(cfg, n_det=4000)
+    O = oracle_mod.System(h, eri, ec)
+    w = np.linalg.eigvalsh(O.dense_h(dets))[:2]
+    H = O.sparse_h(dets)
+    e, C = oracle_mod.davidson(H.dot, H.diagonal(), k=2, tol=1e-12, res_tol=1e-8)
+    np.testing.assert_allclose(e, w, atol=1e-9)
+    ea = np.sort(sla.eigsh(H, k=2, which="SA", tol=1e-12)[0])
+    np.testing.assert_allclose(e, ea, atol=1e-9)
+    # eigenvectors: residual small and orthonormal
+    for a in range(2):
+        r = H.dot(C[a]) - e[a] * C[a]
+        assert np.linalg.norm(r) < 1e-7
+    np.testing.assert_allclose(C @ C.T, np.eye(2), atol=1e-10)
+
+
+# ------------------------------------------------------------------ RDMs and gradients
+
+def _ground(oracle_mod, h, eri, ec, dets):
+    O = oracle_mod.System(h, eri, ec)
+    w, v = np.linalg.eigh(O.dense_h(dets))
+    return O, w[0], v[:, 0]
+
+
+def test_rdm_traces_and_energy_identity(oracle_mod):
+    n, na, nb = 5, 2, 2
+    h, eri, _ = small_system(n, 5, 21)
+    dets = S.fci_dets(n, na, nb)
+    O, E, c = _ground(oracle_mod, h, eri, 0.25, dets)
+    g1 = oracle_mod.rdm1_full(dets, c, n)
+    g2 = oracle_mod.rdm2_full(dets, c, n)
+    N = na + nb
+    assert abs(np.trace(g1) - N) < 1e-12
+    assert abs(np.einsum("pprr->", g2) - N * (N - 1)) < 1e-10
+    np.testing.assert_allclose(g1, g1.T, atol=1e-13)
+    G = jw.eri_full(eri, n)
+    E2 = 0.25 + np.sum(h * g1) + 0.5 * np.sum(G * g2)
+    assert abs(E2 - E) < 1e-11
+    # packed folding: sum_slot eri[slot] * dE/deri[slot] reproduces the two-body energy
+    gh, ge = O.energy_gradient(dets, c)
+    assert abs(np.dot(eri, ge) - 0.5 * np.sum(G * g2)) < 1e-11
+
+
+def test_rdm_no_two_body_closed_form(oracle_mod):
+    n, na, nb = 6, 2, 3
+    h, eri, _ = small_system(n, 4, 23)
+    eri = np.zeros_like(eri)
+    dets = S.fci_dets(n, na, nb)
+    O, E, c = _ground(oracle_mod, h, eri, 0.0, dets)
+    eps, U = np.linalg.eigh(h)
+    ref = U[:, :na] @ U[:, :na].T + U[:, :nb] @ U[:, :nb].T
+    np.testing.assert_allclose(oracle_mod.rdm1_full(dets, c, n), ref, atol=1e-10)
+
+
+def test_gradient_matches_central_differences(oracle_mod):
+    n, na, nb = 5, 2, 2
+    h, eri, _ = small_system(n, 5, 31)
+    dets = S.fci_dets(n, na, nb)
+    O, E, c = _ground(oracle_mod, h, eri, 0.0, dets)
+    gh, ge = O.energy_gradient(dets, c)
+    rng = np.random.default_rng(4004)
+    step = 1e-5
+    for _ in range(4):
+        dh = rng.normal(size=(n, n))
+        dh = 0.5 * (dh + dh.T)
+        de = rng.normal(size=eri.size)
+        ep = np.linalg.eigvalsh(oracle_mod.System(h + step * dh, eri + step * de, 0.0).dense_h(dets))[0]
+        em = np.linalg.eigvalsh(oracle_mod.System(h - step * dh, eri - step * de, 0.0).dense_h(dets))[0]
+        fd = (ep - em) / (2 * step)
+        an = np.sum(gh * dh) + np.dot(ge, de)
+        assert abs(fd - an) < 1e-7 * max(1.0, abs(an))
+
+
+# ------------------------------------------------------------------ planted mistakes
+
+MUTATIONS = {
+    "single exchange sign": ("v += eri_so(I, p, q, k, k) - eri_so(I, p, k, k, q);",
+                             "v += eri_so(I, p, q, k, k) + eri_so(I, p, k, k, q);"),
+    "double exchange dropped": ("double v = eri_so(I, p, q, r, s) - eri_so(I, p, s, r, q);",
+                                "double v = eri_so(I, p, q, r, s);"),
+    "double operand transposed": ("double v = eri_so(I, p, q, r, s) - eri_so(I, p, s, r, q);",
+                                  "double v = eri_so(I, p, r, q, s) - eri_so(I, p, s, r, q);"),
+    "creation phase ignored": ("    int ph = (n_before(I, d, so) & 1) ? -1 : 1;\n    put(I, d, so, 1);",
+                               "    int ph = 1;\n    put(I, d, so, 1);"),
+    "diagonal exchange dropped": ("e += 0.5 * (eri_so(I, k, k, l, l) - eri_so(I, k, l, l, k));",
+                                  "e += 0.5 * (eri_so(I, k, k, l, l));"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_planted_mistake_is_caught(oracle_mod, tmp_path, name):
+    """A mistake planted in a copy of the oracle's C source must fail the JW pin."""
+    src = open(os.path.join(os.path.dirname(oracle_mod.__file__), "shci_oracle.c")).read()
+    old, new = MUTATIONS[name]
+    assert old in src
+    mut = tmp_path / "mut.c"
+    mut.write_text(src.replace(old, new))
+    so = tmp_path / "libmut.so"
+    subprocess.run(["gcc", "-O1", "-shared", "-fPIC", "-std=c11", "-o", str(so), str(mut), "-lm"], check=True)
+    lib = ctypes.CDLL(str(so))
+    f64p = ctypes.POINTER(ctypes.c_double)
+    u64p = ctypes.POINTER(ctypes.c_uint64)
+    lib.oracle_hij.restype = ctypes.c_double
+    lib.oracle_hij.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, f64p, f64p, u64p, u64p]
+    n, na, nb = 4, 2, 2
+    h, eri, _ = small_system(n, 5, 140 + na)
+    dets = S.fci_dets(n, na, nb)
+    ref = jw.projected(h, eri, dets, 0.0)
+    got = np.empty_like(ref)
+    for i in range(dets.shape[0]):
+        for j in range(dets.shape[0]):
+            di = np.ascontiguousarray(dets[i])
+            dj = np.ascontiguousarray(dets[j])
+            got[i, j] = lib.oracle_hij(n, 1, 0.0, h.ctypes.data_as(f64p), eri.ctypes.data_as(f64p),
+                                       di.ctypes.data_as(u64p), dj.ctypes.data_as(u64p))
+    assert np.max(np.abs(got - ref)) > 1e-6, "planted mistake was not detected"
