@@ -1,0 +1,418 @@
+"""Benchmark of the SHCI variational hot path on one GB300 (or N replicas).
+
+A step is one pass of the whole hot path over the selected-space workload
+(24 orbitals, 6 alpha + 6 beta electrons, |V| = 1,000,000, two roots, stored
+H): helper lists, connectivity and H_ij for every connected pair, the cached
+diagonal, then diagonally preconditioned Davidson to convergence (tol 1e-10,
+residual 1e-6) with sigma = H c applied from the stored matrix.
+
+Metric: full-matrix sigma nonzeros processed per second over the whole step
+(sum over sigma launches of (2 * nnz_upper + n_det) * vectors, divided by the
+step time, build included).  Time-to-E (Davidson wall time) and the build
+time are reported beside it, plus the dominant kernel's roofline.
+
+    python bench.py [--steps K] [--warmup W] [--impl ours|reference] [--gpus N]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import shci_synth as S  # noqa: E402
+
+WORKLOAD = "sel_24o_6a6b_1m"
+TOL = 1e-10
+MAX_ITER = 400
+NOMINAL_FP64_TFLOPS = 1.25     # GB300 dense FP64, nominal at the maximum SM clock
+
+
+def metric_name():
+    return "sigma H·c nonzeros/s and Davidson time-to-E (|ΔE|<1e-9 Ha) vs roofline, 1 GB300"
+
+
+def workload_desc(cfg):
+    return ("%s: %d orbitals, %da+%db electrons, |V|=%d selected determinants, %d roots, stored H, FP64"
+            % (cfg.name, cfg.n_orb, cfg.n_alpha, cfg.n_beta, cfg.n_det, cfg.roots))
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_digest(path):
+    import hashlib
+    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+
+
+def sigma_traffic(workload, stored_nnz):
+    """DRAM bytes per sigma launch from the committed ncu summary, scaled to this
+    workload's stored nonzeros; None if the summary is missing or was taken on
+    a different version of the kernel source."""
+    tpath = os.path.join(ROOT, "profiles", "sigma_stored_traffic.json")
+    src = os.path.join(ROOT, "paper_1809_04600_gb300", "csrc", "sigma.cu")
+    if not os.path.exists(tpath):
+        return None
+    try:
+        tj = json.load(open(tpath))
+        if tj.get("kernel_source_sha256_16") != kernel_source_digest(src):
+            return None
+        return float(tj["dram_bytes_per_stored_nnz"]) * stored_nnz
+    except Exception:
+        return None
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index=0):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ our arm
+
+def run_ours(args):
+    import torch
+    import paper_1809_04600_gb300 as P
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    P.build()
+    P.load_library()
+
+    cfg = S.config(args.config)
+    h, eri, ec, dets = S.make_system(cfg)
+    n = dets.shape[0]
+    stream = torch.cuda.current_stream()
+    d_h = torch.from_numpy(h).cuda()
+    d_eri = torch.from_numpy(eri).cuda()
+    d_dets = torch.from_numpy(dets.view(np.int64)).cuda()
+    vecs = torch.empty((cfg.roots, n), dtype=torch.float64, device="cuda")
+    ctx = P.Context(local, stream)
+    H = ctx.handle
+
+    def step():
+        P.shci_load_integrals(H, cfg.n_orb, ec, d_h, d_eri)
+        nnz = P.shci_build_connectivity(H, cfg.n_alpha, cfg.n_beta, d_dets, P.SHCI_STORED)
+        t0 = time.perf_counter()
+        e, it, rc = P.shci_davidson(H, cfg.roots, TOL, MAX_ITER, vecs=vecs)
+        t_dav = time.perf_counter() - t0
+        if rc != 0:
+            raise RuntimeError("Davidson did not converge")
+        return nnz, e, it, t_dav
+
+    for _ in range(args.warmup):
+        step()
+    # timed region: device-timed with CUDA events on the library's stream
+    P.shci_set_timing(H, True)
+    launches0 = P.shci_get_stats(H)["kernel_launches"]
+    sampler = ClockSampler(local)
+    sampler.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    t_wall = time.perf_counter()
+    dav_times, builds, iters, energies = [], [], [], None
+    for _ in range(args.steps):
+        nnz, e, it, t_dav = step()
+        dav_times.append(t_dav)
+        builds.append(P.shci_get_stats(H)["build_ms"] / 1e3)
+        iters.append(it)
+        energies = e
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    ms = ev0.elapsed_time(ev1)
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    st = P.shci_get_stats(H)
+    launches = st["kernel_launches"] - launches0
+    nnz_full = 2 * st["nnz_upper"] + n
+    vec_mults = st["sigma_vectors"]             # vectors multiplied in the timed region
+    sigma_ms = st["sigma_ms_total"]
+    units = float(nnz_full) * vec_mults         # full-matrix nonzeros processed
+    if dist:
+        import torch.distributed as dist_
+        t = torch.tensor([ms], device="cuda")
+        dist_.all_reduce(t, op=dist_.ReduceOp.MAX)
+        ms = float(t.item())
+        u = torch.tensor([units], device="cuda", dtype=torch.float64)
+        dist_.all_reduce(u)
+        units = float(u.item())
+    value = units / (ms / 1e3)
+
+    # roofline of the dominant kernel (stored sigma): one FP64 FMA per stored
+    # nonzero per vector; bytes: 12 per stored nonzero + diag + vectors
+    per_launch_ms = sigma_ms / max(1, st["sigma_launches"])
+    kbar = vec_mults / max(1, st["sigma_launches"])
+    flops = 2.0 * nnz_full * kbar
+    bytes_alg = 12.0 * (nnz_full - n) + n * (8.0 + 16.0 * kbar)
+    achieved_tf = flops / (per_launch_ms / 1e3) / 1e12
+    hbm_peak, peak_kind = load_peaks()
+    achieved_gbs = bytes_alg / (per_launch_ms / 1e3) / 1e9
+    traffic = sigma_traffic(cfg.name, nnz_full - n)
+
+    # end-to-end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(P, H, cfg, h, eri, ec, dets, nnz_full, args)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(cfg, h, eri, ec, dets, args)
+
+    out = {
+        "metric": metric_name(),
+        "value": value,
+        "unit": "nnz/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": workload_desc(cfg), "n_det": n, "nnz_upper": st["nnz_upper"],
+                   "roots": cfg.roots, "tol": TOL, "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "inputs larger than L2: the stored H (%.1f GB) is rebuilt and streamed every step"
+                         % (12.0 * (nnz_full - n) / 1e9)},
+        "time_to_E_s": float(np.mean(dav_times)),
+        "build_s": float(np.mean(builds)),
+        "davidson_iters": int(np.mean(iters)),
+        "energies": [float(x) for x in energies],
+        "sigma_kernel_ms": per_launch_ms,
+        "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved_tf / NOMINAL_FP64_TFLOPS, "traffic": traffic,
+                     "kernel": "k_sigma_stored (FP64 FMA per stored nonzero per vector)",
+                     "peak_kind": "nominal FP64 (GB300 dense FP64, 2 DFMA/clk/SM at 2070 MHz)"},
+        "roofline_hbm": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": achieved_gbs / hbm_peak, "peak_kind": peak_kind},
+        "clocks": clocks,
+        "gpu_launches": int(launches),
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+    }
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_e2e(P, H, cfg, h, eri, ec, dets, nnz_full, args):
+    """Same metric through the C ABI with host buffers: integrals and
+    determinants copied host->device, energies and Ritz vectors copied back,
+    all inside the timed region."""
+    import torch
+    n = dets.shape[0]
+    hp = torch.from_numpy(h).pin_memory()
+    ep = torch.from_numpy(eri).pin_memory()
+    dp = torch.from_numpy(dets.view(np.int64)).pin_memory()
+    vout = torch.empty((cfg.roots, n), dtype=torch.float64).pin_memory()
+    steps = max(1, min(args.steps, 3))
+    P.shci_set_timing(H, False)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    vecs_total = 0
+    for _ in range(steps):
+        s0 = P.shci_get_stats(H)["sigma_vectors"]
+        P.shci_load_integrals(H, cfg.n_orb, ec, hp, ep)
+        P.shci_build_connectivity(H, cfg.n_alpha, cfg.n_beta, dp, P.SHCI_STORED)
+        e, it, rc = P.shci_davidson(H, cfg.roots, TOL, MAX_ITER, vecs=vout)
+        vecs_total += P.shci_get_stats(H)["sigma_vectors"] - s0
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t) / steps
+    h2d = h.nbytes + eri.nbytes + dets.nbytes
+    d2h = 8 * cfg.roots + vout.numel() * 8
+    return {"value": float(nnz_full) * (vecs_total / steps) / dt, "unit": "nnz/s", "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "steps": steps, "s_per_step": dt}
+
+
+# ------------------------------------------------------------------ CPU oracle arm
+
+def cpu_baseline(cfg, h, eri, ec, dets, args, n_rows=None):
+    """The oracle as it stands on the host cores: sigma = H c for a bounded
+    sample of rows of the same workload (each row by brute force over all of V,
+    k = roots vectors).  Returns throughput in full-matrix nonzeros/s."""
+    import oracle
+    oracle.build()
+    O = oracle.System(h, eri, ec)
+    n = dets.shape[0]
+    rng = np.random.default_rng(2024)
+    n_rows = n_rows or args.cpu_rows
+    rows = np.sort(rng.choice(n, n_rows, replace=False))
+    c = S.random_vectors(n, cfg.roots, 7)
+    t = time.perf_counter()
+    O.sigma_rows(dets, c, rows)
+    dt = time.perf_counter() - t
+    nnz_rows = sum(O.row(dets, int(i))[0].size + 1 for i in rows[:min(40, n_rows)])
+    nnz_per_row = nnz_rows / min(40, n_rows)
+    value = nnz_per_row * n_rows * cfg.roots / dt
+    return {"value": value, "unit": "nnz/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": "%d uniformly sampled rows of the %d-determinant space, %d vectors, each row by brute force "
+                      "over all determinants (%.1f s); nonzeros/row estimated from 40 rows" %
+                      (n_rows, n, cfg.roots, dt), "seconds": dt}
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cfg = S.config(args.config)
+    h, eri, ec, dets = S.make_system(cfg)
+    for _ in range(args.warmup):
+        cpu_baseline(cfg, h, eri, ec, dets, args, n_rows=max(8, args.cpu_rows // 10))
+    vals, secs = [], []
+    res = None
+    for _ in range(args.steps):
+        res = cpu_baseline(cfg, h, eri, ec, dets, args, n_rows=max(8, args.cpu_rows // 4))
+        vals.append(res["value"])
+        secs.append(res["seconds"])
+    value = float(np.mean(vals))
+    out = {
+        "impl": "reference",
+        "metric": metric_name(),
+        "value": value,
+        "unit": "nnz/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": 1e3 * float(np.mean(secs)),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": workload_desc(cfg), "n_det": dets.shape[0], "roots": cfg.roots},
+        "cpu_baseline": {"value": value, "unit": "nnz/s", "cores": res["cores"], "kind": "oracle",
+                         "sample": res["sample"]},
+        "e2e": {"value": value, "unit": "nnz/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out))
+
+
+def run_sigma_only(args):
+    """Profiling driver: build the stored H of the workload (or a smaller space
+    of the same shape with --n-det) and launch the sigma kernel repeatedly with
+    `roots` vectors.  Prints the mean kernel time; not a bench line."""
+    import torch
+    import paper_1809_04600_gb300 as P
+    P.build()
+    P.load_library()
+    cfg = S.config(args.config)
+    h, eri, ec, dets = S.make_system(cfg, n_det=args.n_det)
+    n = dets.shape[0]
+    ctx = P.Context(0, torch.cuda.current_stream())
+    P.shci_load_integrals(ctx.handle, cfg.n_orb, ec, torch.from_numpy(h).cuda(), torch.from_numpy(eri).cuda())
+    P.shci_build_connectivity(ctx.handle, cfg.n_alpha, cfg.n_beta, torch.from_numpy(dets.view(np.int64)).cuda())
+    x = torch.randn((cfg.roots, n), dtype=torch.float64, device="cuda")
+    y = torch.empty_like(x)
+    P.shci_set_timing(ctx.handle, True)
+    for _ in range(args.sigma_only):
+        P.shci_sigma(ctx.handle, x, y)
+    st = P.shci_get_stats(ctx.handle)
+    print(json.dumps({"n_det": n, "nnz_upper": st["nnz_upper"], "k": cfg.roots,
+                      "sigma_ms": st["sigma_ms_total"] / max(1, st["sigma_launches"])}))
+    ctx.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default=WORKLOAD)
+    ap.add_argument("--cpu-rows", type=int, default=120000)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n-det", type=int, default=None,
+                    help="profiling only: a smaller space of the same shape (not a bench line)")
+    ap.add_argument("--sigma-only", type=int, default=0,
+                    help="profiling only: build once, then launch the sigma kernel this many times")
+    args = ap.parse_args()
+    if args.sigma_only:
+        run_sigma_only(args)
+    elif args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,167 @@
+/*
+ * shci.h -- C ABI of the GB300 library for the variational hot path of fast
+ * semistochastic heat-bath configuration interaction (Li, Otten, Holmes,
+ * Sharma, Umrigar, arXiv:1809.04600).
+ *
+ * The library holds one Hamiltonian (integrals) and one variational space V
+ * (a list of determinants) per context.  It finds every connected determinant
+ * pair of V, evaluates the Slater-Condon element H_ij with its fermionic sign,
+ * applies sigma = H c (from a stored sparse H or recomputed on the fly) and
+ * runs a diagonally preconditioned Davidson solver for the lowest roots.  All
+ * arithmetic on matrix elements and vectors is IEEE binary64.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Determinants: uint64 rows of 2*W words, W = ceil(n_orb / 64): the alpha
+ *   string's W words, then the beta string's W words.  Spatial orbital n of a
+ *   string is bit (n & 63) of word (n >> 6) (Sec. IV.A).  n_orb <= 128.
+ * - Fermionic sign convention: |D> = prod_{alpha occupied, ascending} a+ *
+ *   prod_{beta occupied, ascending} a+ |0>.  Eigenvalues and |H_ij| do not
+ *   depend on this choice; signed results are self-consistent under it.
+ * - Hamiltonian: H = E_core + sum h_pq a+_ps a_qs
+ *                  + 1/2 sum (pq|rs) a+_ps a+_rt a_st a_qs  (real orbitals).
+ * - Integrals: h is n_orb*n_orb row-major (symmetric); eri_packed holds the
+ *   chemists' (pq|rs) with 8-fold symmetry: pq = p(p+1)/2 + q (p >= q),
+ *   slot = PQ(PQ+1)/2 + RS (PQ >= RS); length npair(npair+1)/2 with
+ *   npair = n_orb(n_orb+1)/2.
+ * - Vectors are float64 [k][n_det] (vector-major).
+ * - mem_space: SHCI_MEM_HOST for host pointers (pageable or pinned; the call
+ *   copies through the context's stream and synchronises before returning),
+ *   SHCI_MEM_DEVICE for pointers on the context's device.
+ * - Ownership: the library never frees a caller pointer.  It owns copies of
+ *   the integrals and determinants, the helper lists, the stored H and its
+ *   workspaces until the next build or shci_destroy.
+ * - Errors: every int-returning call returns an shci_status; on failure
+ *   shci_last_error() describes it.  The library never exits or aborts.
+ *   Device-side waits are bounded, so a failing call leaves no sticky CUDA
+ *   error behind (a genuine device fault still would: SHCI_ERR_CUDA).
+ * - Streams: all device work runs on the context's stream (the one passed to
+ *   shci_create, or a stream the context creates).  Calls return after the
+ *   work they enqueue has completed unless stated otherwise.
+ */
+#ifndef SHCI_H
+#define SHCI_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct shci_ctx shci_ctx;
+
+enum shci_status {
+    SHCI_OK = 0,
+    SHCI_ERR_INVALID = 1,        /* bad argument or input (sizes, popcounts, duplicates) */
+    SHCI_ERR_OOM = 2,            /* device allocation failed */
+    SHCI_ERR_CUDA = 3,           /* a CUDA runtime call failed */
+    SHCI_ERR_NOT_CONVERGED = 4,  /* Davidson hit max_iter; best estimates returned */
+    SHCI_ERR_TIMEOUT = 5,        /* a bounded device wait ran out */
+    SHCI_ERR_STATE = 6           /* call out of order (e.g. sigma before build) */
+};
+
+enum shci_mem_space { SHCI_MEM_HOST = 0, SHCI_MEM_DEVICE = 1 };
+
+/* How H is applied: stored upper+lower sparse rows, recomputed each product,
+ * or stored when it fits the device's free memory (with a margin). */
+enum shci_mode { SHCI_STORED = 0, SHCI_ON_THE_FLY = 1, SHCI_AUTO = 2 };
+
+/* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
+ * on that device (NULL: the context creates and owns a non-blocking stream).
+ * Returns SHCI_ERR_INVALID for a bad device, SHCI_ERR_CUDA otherwise. */
+int shci_create(shci_ctx **out, int device, void *cuda_stream);
+
+/* Free every device buffer the context owns.  NULL is ignored. */
+void shci_destroy(shci_ctx *ctx);
+
+/* Message for the last failing call on this context ("" if none).  Valid
+ * until the next call on the context.  ctx == NULL gives the message of the
+ * last failed shci_create in this thread. */
+const char *shci_last_error(const shci_ctx *ctx);
+
+/* Load the Hamiltonian's integrals (the one- and two-electron integrals the
+ * method takes as input, Sec. II; real orbitals, chemists' notation).
+ * n_orb in [1, 128].  Invalidates any previous build.  Returns
+ * SHCI_ERR_INVALID if h is not symmetric to 1e-12. */
+int shci_load_integrals(shci_ctx *ctx, int n_orb, double e_core, const double *h,
+                        const double *eri_packed, int mem_space);
+
+/* Build the connectivity of V = dets[0 .. n_det) (Sec. III): helper lists
+ * (unique alpha/beta strings, per-string determinant lists, alpha-single
+ * lists; Table I), the cached diagonal H_ii (Sec. IV.B) and, in SHCI_STORED
+ * mode, every off-diagonal H_ij != structural zero in both triangles.
+ * dets: [n_det][2W] uint64 as above, every alpha string with n_alpha bits and
+ * every beta string with n_beta bits below n_orb; determinants must be
+ * distinct (SHCI_ERR_INVALID otherwise).  n_det in [1, 2^31 - 1].
+ * *nnz_upper_out (may be NULL) receives the number of connected pairs i < j,
+ * i.e. the upper-triangle nonzeros.  In SHCI_ON_THE_FLY mode the count pass
+ * still runs, so the count is exact.  Determinant order is the caller's. */
+int shci_build_connectivity(shci_ctx *ctx, int n_alpha, int n_beta, int64_t n_det,
+                            const uint64_t *dets, int mem_space, int mode,
+                            int64_t *nnz_upper_out);
+
+/* The cached diagonal H_ii, [n_det]. */
+int shci_get_diag(shci_ctx *ctx, double *diag, int mem_space);
+
+/* Export the stored upper triangle as (i, j, H_ij), i < j, rows ascending and
+ * each row in ascending j.  Host buffers of capacity `cap`; *n_out receives
+ * the pair count (nothing is written when cap < count).  For parity checks
+ * and debugging; SHCI_ERR_STATE unless built in SHCI_STORED mode. */
+int shci_get_pairs(shci_ctx *ctx, int64_t cap, int64_t *i_out, int64_t *j_out,
+                   double *hij_out, int64_t *n_out);
+
+/* One stored row of the full symmetric H without its diagonal: the connected
+ * columns j != row in ascending order and their H_ij (host buffers of
+ * capacity `cap`; *n_out receives the row length, nothing is written when
+ * cap is smaller).  For sampled-row parity checks on large spaces;
+ * SHCI_ERR_STATE unless built in SHCI_STORED mode. */
+int shci_get_row(shci_ctx *ctx, int64_t row, int64_t cap, int64_t *cols, double *vals, int64_t *n_out);
+
+/* sigma = H c for k vectors (k in [1, 8]), c and sigma [k][n_det] (Sec. IV.B:
+ * the matrix-vector product of the Davidson step).  Uses the stored H, or the
+ * on-the-fly product in SHCI_ON_THE_FLY mode.  c and sigma must not overlap. */
+int shci_sigma(shci_ctx *ctx, int k, const double *c, double *sigma, int mem_space);
+
+/* Lowest k_roots (in [1, 8]) eigenpairs of H on V by diagonally
+ * preconditioned Davidson (Sec. II.A).  Converged when, for every root, the
+ * Ritz value moved by less than `tol` since the previous iteration and the
+ * residual norm ||H x - theta x|| is below 0.1 * sqrt(tol).
+ * guess: NULL (start from the unit vectors of the k_roots lowest H_ii) or
+ * [k_roots][n_det] starting vectors (orthonormalised by the call), in
+ * mem_space.  energies: host [k_roots], ascending.  vecs: [k_roots][n_det]
+ * orthonormal Ritz vectors in mem_space, or NULL.  iters_out may be NULL.
+ * Returns SHCI_ERR_NOT_CONVERGED (with the last estimates written) after
+ * max_iter iterations. */
+int shci_davidson(shci_ctx *ctx, int k_roots, double tol, int max_iter, const double *guess,
+                  double *energies, double *vecs, int mem_space, int *iters_out);
+
+/* Library-side measurements of the last build / Davidson run (for reports). */
+typedef struct {
+    int64_t n_det;
+    int64_t nnz_upper;          /* connected pairs i < j */
+    int64_t n_alpha_strings;    /* unique alpha strings in V */
+    int64_t n_beta_strings;
+    int64_t n_alpha_singles;    /* entries of the alpha-single lists */
+    int64_t candidates;         /* candidate pairs screened per build pass */
+    double build_ms;            /* last shci_build_connectivity, device time */
+    double sigma_ms_total;      /* sum of sigma-kernel times since reset */
+    int64_t sigma_launches;     /* sigma-kernel launches since reset */
+    int64_t sigma_vectors;      /* vectors multiplied since reset */
+    int64_t kernel_launches;    /* all kernels this context launched since reset */
+    int davidson_iters;
+    int mode;                   /* SHCI_STORED or SHCI_ON_THE_FLY after a build */
+    int n_words;                /* W */
+} shci_stats_t;
+
+/* Fill *out.  Kernel times are recorded only while timing is enabled. */
+int shci_get_stats(shci_ctx *ctx, shci_stats_t *out);
+
+/* Enable (1) or disable (0) per-launch CUDA-event timing of the sigma
+ * kernels, and reset the accumulated counters. */
+int shci_set_timing(shci_ctx *ctx, int enable);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SHCI_H */

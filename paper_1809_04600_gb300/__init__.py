@@ -1,0 +1,13 @@
+"""GB300 (sm_103a) library for the variational hot path of fast semistochastic
+heat-bath configuration interaction (arXiv:1809.04600).
+
+The compute lives in the CUDA library ``libshci.so`` (C ABI: include/shci.h);
+this package only builds and binds it.  Importing the package does not load
+the library; the first call does, and fails loudly if it was not built.
+"""
+from .binding import (  # noqa: F401
+    EXPORTED, SHCI_AUTO, SHCI_MEM_DEVICE, SHCI_MEM_HOST, SHCI_ON_THE_FLY, SHCI_STORED, Context, ShciError,
+    load_library, shci_build_connectivity, shci_create, shci_davidson, shci_destroy, shci_get_diag,
+    shci_get_pairs, shci_get_row, shci_get_stats, shci_last_error, shci_load_integrals, shci_set_timing, shci_sigma,
+)
+from .build_lib import build  # noqa: F401

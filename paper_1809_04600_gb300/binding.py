@@ -1,0 +1,249 @@
+"""Thin ctypes binding of the C ABI in include/shci.h.
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library (``libshci.so``).  Functions keep the C names.  Arrays may be torch
+tensors (on the context's device, or on the host) or numpy arrays (host); the
+``mem_space`` argument of the C call is derived from where the data lives.
+If the compiled library is missing, loading fails loudly -- there is no
+fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libshci.so")
+
+SHCI_OK = 0
+SHCI_ERR_INVALID = 1
+SHCI_ERR_OOM = 2
+SHCI_ERR_CUDA = 3
+SHCI_ERR_NOT_CONVERGED = 4
+SHCI_ERR_TIMEOUT = 5
+SHCI_ERR_STATE = 6
+SHCI_MEM_HOST = 0
+SHCI_MEM_DEVICE = 1
+SHCI_STORED = 0
+SHCI_ON_THE_FLY = 1
+SHCI_AUTO = 2
+
+_STATUS = {1: "INVALID", 2: "OOM", 3: "CUDA", 4: "NOT_CONVERGED", 5: "TIMEOUT", 6: "STATE"}
+
+# every symbol include/shci.h declares (checked by the tests)
+EXPORTED = [
+    "shci_create", "shci_destroy", "shci_last_error", "shci_load_integrals", "shci_build_connectivity",
+    "shci_get_diag", "shci_get_pairs", "shci_get_row", "shci_sigma", "shci_davidson", "shci_get_stats", "shci_set_timing",
+]
+
+
+class ShciError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("shci error %s (%d): %s" % (_STATUS.get(code, "?"), code, msg))
+        self.code = code
+
+
+class shci_stats_t(ctypes.Structure):
+    _fields_ = [
+        ("n_det", ctypes.c_int64), ("nnz_upper", ctypes.c_int64), ("n_alpha_strings", ctypes.c_int64),
+        ("n_beta_strings", ctypes.c_int64), ("n_alpha_singles", ctypes.c_int64), ("candidates", ctypes.c_int64),
+        ("build_ms", ctypes.c_double), ("sigma_ms_total", ctypes.c_double), ("sigma_launches", ctypes.c_int64),
+        ("sigma_vectors", ctypes.c_int64), ("kernel_launches", ctypes.c_int64), ("davidson_iters", ctypes.c_int),
+        ("mode", ctypes.c_int), ("n_words", ctypes.c_int),
+    ]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libshci.so (build it first with build_lib.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError("the CUDA library %s is not built; run paper_1809_04600_gb300.build_lib.build()" % path)
+    lib = ctypes.CDLL(path)
+    vp, i32, i64, f64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+    sig = {
+        "shci_create": (i32, [ctypes.POINTER(vp), i32, vp]),
+        "shci_destroy": (None, [vp]),
+        "shci_last_error": (ctypes.c_char_p, [vp]),
+        "shci_load_integrals": (i32, [vp, i32, f64, vp, vp, i32]),
+        "shci_build_connectivity": (i32, [vp, i32, i32, i64, vp, i32, i32, ctypes.POINTER(i64)]),
+        "shci_get_diag": (i32, [vp, vp, i32]),
+        "shci_get_pairs": (i32, [vp, i64, vp, vp, vp, ctypes.POINTER(i64)]),
+        "shci_get_row": (i32, [vp, i64, i64, vp, vp, ctypes.POINTER(i64)]),
+        "shci_sigma": (i32, [vp, i32, vp, vp, i32]),
+        "shci_davidson": (i32, [vp, i32, f64, i32, vp, vp, vp, i32, ctypes.POINTER(i32)]),
+        "shci_get_stats": (i32, [vp, ctypes.POINTER(shci_stats_t)]),
+        "shci_set_timing": (i32, [vp, i32]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+# ------------------------------------------------------------------ marshalling
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x, dtype):
+    """(pointer, mem_space, keepalive) for a numpy array or torch tensor."""
+    if x is None:
+        return None, SHCI_MEM_HOST, None
+    if _is_torch(x):
+        import torch
+        want = {np.float64: (torch.float64,), np.uint64: (torch.uint64, torch.int64),
+                np.int64: (torch.int64,)}[dtype]
+        if x.dtype not in want:
+            raise TypeError("expected %s, got %s" % (want[0], x.dtype))
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr(), (SHCI_MEM_DEVICE if x.is_cuda else SHCI_MEM_HOST), x
+    a = np.ascontiguousarray(x, dtype=dtype)
+    return a.ctypes.data, SHCI_MEM_HOST, a
+
+
+def _check(ctx, rc):
+    if rc != SHCI_OK:
+        raise ShciError(rc, load_library().shci_last_error(ctx).decode())
+
+
+# ------------------------------------------------------------------ C-named calls
+
+def shci_create(device: int = 0, stream=None):
+    """Returns an opaque context handle.  ``stream`` is a torch.cuda.Stream,
+    a raw cudaStream_t integer, or None (the context owns a stream)."""
+    lib = load_library()
+    h = ctypes.c_void_p()
+    raw = None
+    if stream is not None:
+        raw = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    rc = lib.shci_create(ctypes.byref(h), int(device), raw)
+    if rc != SHCI_OK:
+        raise ShciError(rc, lib.shci_last_error(None).decode())
+    return h
+
+
+def shci_destroy(ctx):
+    load_library().shci_destroy(ctx)
+
+
+def shci_last_error(ctx) -> str:
+    return load_library().shci_last_error(ctx).decode()
+
+
+def shci_load_integrals(ctx, n_orb, e_core, h, eri_packed):
+    ph, mh, kh = _ptr(h, np.float64)
+    pe, me, ke = _ptr(eri_packed, np.float64)
+    if mh != me:
+        raise ValueError("h and eri_packed must live in the same memory space")
+    _check(ctx, load_library().shci_load_integrals(ctx, int(n_orb), float(e_core), ph, pe, mh))
+
+
+def shci_build_connectivity(ctx, n_alpha, n_beta, dets, mode=SHCI_STORED) -> int:
+    pd, md, kd = _ptr(dets, np.uint64)
+    n_det = dets.shape[0]
+    nnz = ctypes.c_int64(0)
+    _check(ctx, load_library().shci_build_connectivity(ctx, int(n_alpha), int(n_beta), int(n_det), pd, md,
+                                                       int(mode), ctypes.byref(nnz)))
+    return nnz.value
+
+
+def shci_get_diag(ctx, out):
+    p, m, k = _ptr(out, np.float64)
+    _check(ctx, load_library().shci_get_diag(ctx, p, m))
+    return out
+
+
+def shci_get_pairs(ctx):
+    """(i, j, H_ij) numpy arrays of the stored upper triangle, rows ascending."""
+    lib = load_library()
+    n = ctypes.c_int64(0)
+    _check(ctx, lib.shci_get_pairs(ctx, 0, None, None, None, ctypes.byref(n)))
+    ii = np.empty(n.value, np.int64)
+    jj = np.empty(n.value, np.int64)
+    vv = np.empty(n.value, np.float64)
+    _check(ctx, lib.shci_get_pairs(ctx, n.value, ii.ctypes.data, jj.ctypes.data, vv.ctypes.data, ctypes.byref(n)))
+    return ii, jj, vv
+
+
+def shci_get_row(ctx, row):
+    """(cols, vals) of one stored row without the diagonal, ascending columns."""
+    lib = load_library()
+    n = ctypes.c_int64(0)
+    _check(ctx, lib.shci_get_row(ctx, int(row), 0, None, None, ctypes.byref(n)))
+    cols = np.empty(n.value, np.int64)
+    vals = np.empty(n.value, np.float64)
+    _check(ctx, lib.shci_get_row(ctx, int(row), n.value, cols.ctypes.data, vals.ctypes.data, ctypes.byref(n)))
+    return cols, vals
+
+
+def shci_sigma(ctx, c, sigma):
+    """sigma[k, n] = H c[k, n] (both torch CUDA tensors, or both host arrays)."""
+    pc, mc, kc = _ptr(c, np.float64)
+    ps, ms, ks = _ptr(sigma, np.float64)
+    if mc != ms:
+        raise ValueError("c and sigma must live in the same memory space")
+    k = 1 if len(c.shape) == 1 else c.shape[0]
+    _check(ctx, load_library().shci_sigma(ctx, int(k), pc, ps, mc))
+    return sigma
+
+
+def shci_davidson(ctx, k_roots, tol=1e-10, max_iter=200, guess=None, vecs=None, check=True):
+    """(energies[k], iterations, status).  vecs (torch CUDA tensor or numpy) receives Ritz vectors."""
+    lib = load_library()
+    e = np.empty(k_roots, np.float64)
+    pg, mg, kg = _ptr(guess, np.float64)
+    pv, mv, kv = _ptr(vecs, np.float64)
+    if guess is not None and vecs is not None and mg != mv:
+        raise ValueError("guess and vecs must live in the same memory space")
+    mem = mv if vecs is not None else mg
+    it = ctypes.c_int(0)
+    rc = lib.shci_davidson(ctx, int(k_roots), float(tol), int(max_iter), pg, e.ctypes.data, pv, mem,
+                           ctypes.byref(it))
+    if check and rc not in (SHCI_OK,):
+        _check(ctx, rc)
+    return e, it.value, rc
+
+
+def shci_get_stats(ctx) -> dict:
+    s = shci_stats_t()
+    _check(ctx, load_library().shci_get_stats(ctx, ctypes.byref(s)))
+    return {name: getattr(s, name) for name, _ in shci_stats_t._fields_}
+
+
+def shci_set_timing(ctx, enable: bool):
+    _check(ctx, load_library().shci_set_timing(ctx, 1 if enable else 0))
+
+
+class Context:
+    """Owning wrapper: ``with Context(device, stream) as ctx: ...``."""
+
+    def __init__(self, device=0, stream=None):
+        self.handle = shci_create(device, stream)
+
+    def close(self):
+        if self.handle is not None:
+            shci_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

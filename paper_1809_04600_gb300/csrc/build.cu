@@ -1,0 +1,630 @@
+// Integrals, helper lists (Table I), the cached diagonal and the stored
+// Hamiltonian (Sec. III).  Every connected pair is found by screening
+// candidates with XOR/popcount in warp-wide rounds and written, with its
+// Slater-Condon value, into both rows of a symmetric sparse matrix.
+#include <algorithm>
+#include <atomic>
+#include <numeric>
+
+#include "context.cuh"
+
+std::atomic<long long> g_kernel_launches{0};
+#define LAUNCHED(n) (g_kernel_launches += (n))
+
+namespace shci {
+
+// ====================================================================== integrals
+
+__global__ void k_mean_field_tables(const double *__restrict__ eri, int n, double *__restrict__ jk1,
+                                    double *__restrict__ j1, double *__restrict__ jdiag,
+                                    double *__restrict__ kdiag) {
+    DevInts I{};
+    I.eri = eri;
+    I.n = n;
+    int64_t total = (int64_t)n * n * n;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        int k = (int)(t % n);
+        int q = (int)((t / n) % n);
+        int p = (int)(t / ((int64_t)n * n));
+        double j = eri_get(I, p, q, k, k);
+        double x = eri_get(I, p, k, k, q);
+        j1[t] = j;
+        jk1[t] = j - x;
+        if (p == q) {
+            jdiag[p * n + k] = eri_get(I, p, p, k, k);
+            kdiag[p * n + k] = eri_get(I, p, k, k, p);
+        }
+    }
+}
+
+void load_integrals(shci_ctx *c, int n_orb, double e_core, const double *h, const double *eri, int mem) {
+    if (n_orb < 1 || n_orb > SHCI_MAX_ORB) throw ShciError{SHCI_ERR_INVALID, "n_orb must be in [1, 128]"};
+    if (!h || !eri) throw ShciError{SHCI_ERR_INVALID, "null integral pointer"};
+    int64_t npair = (int64_t)n_orb * (n_orb + 1) / 2;
+    int64_t neri = npair * (npair + 1) / 2;
+    std::vector<double> hh((size_t)n_orb * n_orb);
+    cudaMemcpyKind kind = mem == SHCI_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    if (mem == SHCI_MEM_HOST) {
+        std::copy(h, h + (size_t)n_orb * n_orb, hh.begin());
+    } else {
+        CUDA_TRY(cudaMemcpyAsync(hh.data(), h, sizeof(double) * hh.size(), cudaMemcpyDeviceToHost, c->st));
+        CUDA_TRY(cudaStreamSynchronize(c->st));
+    }
+    for (int p = 0; p < n_orb; p++)
+        for (int q = 0; q < p; q++)
+            if (!(std::abs(hh[p * n_orb + q] - hh[q * n_orb + p]) <= 1e-12))
+                throw ShciError{SHCI_ERR_INVALID, "h is not symmetric"};
+    c->built = false;
+    c->h.alloc(hh.size());
+    c->eri.alloc((size_t)neri);
+    c->jk1.alloc((size_t)n_orb * n_orb * n_orb);
+    c->j1.alloc((size_t)n_orb * n_orb * n_orb);
+    c->jdiag.alloc((size_t)n_orb * n_orb);
+    c->kdiag.alloc((size_t)n_orb * n_orb);
+    CUDA_TRY(cudaMemcpyAsync(c->h.p, hh.data(), sizeof(double) * hh.size(), cudaMemcpyHostToDevice, c->st));
+    CUDA_TRY(cudaMemcpyAsync(c->eri.p, eri, sizeof(double) * neri, kind, c->st));
+    int64_t total = (int64_t)n_orb * n_orb * n_orb;
+    k_mean_field_tables<<<(unsigned)std::min<int64_t>(ceil_div(total, 256), 4096), 256, 0, c->st>>>(
+        c->eri.p, n_orb, c->jk1.p, c->j1.p, c->jdiag.p, c->kdiag.p);
+    KERNEL_CHECK();
+    LAUNCHED(1);
+    CUDA_TRY(cudaStreamSynchronize(c->st));
+    c->n_orb = n_orb;
+    c->e_core = e_core;
+    c->have_ints = true;
+}
+
+DevInts dev_ints(const shci_ctx *c) {
+    DevInts I;
+    I.h = c->h.p;
+    I.eri = c->eri.p;
+    I.jk1 = c->jk1.p;
+    I.j1 = c->j1.p;
+    I.jdiag = c->jdiag.p;
+    I.kdiag = c->kdiag.p;
+    I.e_core = c->e_core;
+    I.n = c->n_orb;
+    return I;
+}
+
+// ====================================================================== helper lists
+
+// flags: bit 0 wrong alpha popcount, bit 1 wrong beta popcount, bit 2 bits beyond n_orb
+template <int W>
+__global__ void k_validate(const uint64_t *__restrict__ dets, int64_t n, int n_orb, int na, int nb, int *flags) {
+    int f = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int ca = 0, cb = 0;
+#pragma unroll
+        for (int k = 0; k < W; k++) {
+            uint64_t a = dets[i * 2 * W + k], b = dets[i * 2 * W + W + k];
+            ca += __popcll(a);
+            cb += __popcll(b);
+            int lo = 64 * k;
+            uint64_t valid = n_orb - lo >= 64 ? ~0ull : (n_orb - lo <= 0 ? 0ull : ((1ull << (n_orb - lo)) - 1));
+            if ((a | b) & ~valid) f |= 4;
+        }
+        if (ca != na) f |= 1;
+        if (cb != nb) f |= 2;
+    }
+    if (f) atomicOr(flags, f);
+}
+
+// keys[i] = spin string `spin` of determinant i; vals[i] = i
+template <int W>
+__global__ void k_extract_strings(const uint64_t *__restrict__ dets, int64_t n, int spin, uint64_t *__restrict__ keys,
+                                  uint32_t *__restrict__ vals) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int k = 0; k < W; k++) keys[i * W + k] = dets[i * 2 * W + spin * W + k];
+        vals[i] = (uint32_t)i;
+    }
+}
+
+template <int KW>
+__global__ void k_head_flags(const uint64_t *__restrict__ keys, int64_t n, int64_t *__restrict__ flags) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t f = 1;
+        if (i > 0) {
+            f = 0;
+#pragma unroll
+            for (int k = 0; k < KW; k++) f |= keys[i * KW + k] != keys[(i - 1) * KW + k];
+        }
+        flags[i] = f;
+    }
+}
+
+// after an exclusive scan of head flags: write unique strings and the string index of each det
+template <int W>
+__global__ void k_unique_write(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ vals,
+                               const int64_t *__restrict__ flags, const int64_t *__restrict__ excl, int64_t n,
+                               uint64_t *__restrict__ ustr, int32_t *__restrict__ sidx) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t id = excl[i] + flags[i] - 1;
+        if (flags[i]) {
+#pragma unroll
+            for (int k = 0; k < W; k++) ustr[id * W + k] = keys[i * W + k];
+        }
+        sidx[vals[i]] = (int32_t)id;
+    }
+}
+
+// composite key (major << 32 | minor) per determinant
+__global__ void k_composite(const int32_t *__restrict__ major, const int32_t *__restrict__ minor, int64_t n,
+                            uint64_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        keys[i] = ((uint64_t)(uint32_t)major[i] << 32) | (uint32_t)minor[i];
+        vals[i] = (uint32_t)i;
+    }
+}
+
+// group offsets from sorted composite keys; members and the other spin's string; duplicates -> flag
+template <int W>
+__global__ void k_group_build(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ vals, int64_t n,
+                              const uint64_t *__restrict__ dets, int other_spin, int64_t n_groups,
+                              int64_t *__restrict__ off, int32_t *__restrict__ mdet, uint64_t *__restrict__ mstr,
+                              int *flags) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t k = keys[i];
+        int64_t g = (int64_t)(k >> 32);
+        if (i == 0 || (keys[i - 1] >> 32) != (uint64_t)g) off[g] = i;
+        if (i > 0 && keys[i - 1] == k) atomicOr(flags, 8);   // duplicate determinant
+        uint32_t d = vals[i];
+        mdet[i] = (int32_t)d;
+#pragma unroll
+        for (int w = 0; w < W; w++) mstr[i * W + w] = dets[(int64_t)d * 2 * W + other_spin * W + w];
+        if (i == n - 1) off[n_groups] = n;
+    }
+}
+
+// alpha^(-1) keys: each unique alpha string with one of its electrons removed
+template <int W>
+__global__ void k_minus_one_keys(const uint64_t *__restrict__ astr, int64_t Ua, int ne, uint64_t *__restrict__ keys,
+                                 uint32_t *__restrict__ vals) {
+    for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < Ua; a += (int64_t)gridDim.x * blockDim.x) {
+        Str<W> s = load_str<W>(astr, a);
+        Str<W> m = s;
+        for (int e = 0; e < ne; e++) {
+            int b = lowest_bit<W>(m);
+            clear_bit<W>(m, b);
+            Str<W> key = s;
+            clear_bit<W>(key, b);
+            int64_t t = a * ne + e;
+#pragma unroll
+            for (int w = 0; w < W; w++) keys[t * W + w] = key.w[w];
+            vals[t] = (uint32_t)t;
+        }
+    }
+}
+
+// for each sorted entry: its segment start / length, stored at the entry's original slot
+template <int W>
+__global__ void k_segment_info(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ vals, int64_t n,
+                               int64_t *__restrict__ seg_start, int32_t *__restrict__ seg_len) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        auto same = [&](int64_t x, int64_t y) {
+            bool eq = true;
+#pragma unroll
+            for (int w = 0; w < W; w++) eq &= keys[x * W + w] == keys[y * W + w];
+            return eq;
+        };
+        if (i > 0 && same(i, i - 1)) continue;   // only segment heads work
+        int64_t e = i + 1;
+        while (e < n && same(e, i)) e++;
+        for (int64_t t = i; t < e; t++) {
+            seg_start[vals[t]] = i;
+            seg_len[vals[t]] = (int32_t)(e - i);
+        }
+    }
+}
+
+__global__ void k_singles_count(const int32_t *__restrict__ seg_len, int64_t Ua, int ne, int64_t *__restrict__ cnt) {
+    for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < Ua; a += (int64_t)gridDim.x * blockDim.x) {
+        int64_t c = 0;
+        for (int e = 0; e < ne; e++) c += seg_len[a * ne + e] - 1;
+        cnt[a] = c;
+    }
+}
+
+__global__ void k_singles_fill(const int64_t *__restrict__ seg_start, const int32_t *__restrict__ seg_len,
+                               const uint32_t *__restrict__ vals, int64_t Ua, int ne, const int64_t *__restrict__ off,
+                               int32_t *__restrict__ out) {
+    for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < Ua; a += (int64_t)gridDim.x * blockDim.x) {
+        int64_t pos = off[a];
+        for (int e = 0; e < ne; e++) {
+            int64_t s = seg_start[a * ne + e];
+            int len = seg_len[a * ne + e];
+            for (int t = 0; t < len; t++) {
+                int64_t b = vals[s + t] / ne;
+                if (b != a) out[pos++] = (int32_t)b;
+            }
+        }
+    }
+}
+
+template <int W>
+__global__ void k_diag(const uint64_t *__restrict__ dets, int64_t n, DevInts I, double *__restrict__ diag) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        Str<W> a = load_str<W>(dets, 2 * i);
+        Str<W> b = load_str<W>(dets, 2 * i + 1);
+        diag[i] = hii<W>(I, a, b);
+    }
+}
+
+// ====================================================================== connectivity
+
+// Candidate segments of determinant i's row (Algorithms 1 and 2, Sec. III):
+//   0     determinants sharing beta(D_i): same-spin alpha singles/doubles
+//   1     determinants sharing alpha(D_i): same-spin beta singles/doubles
+//   2+t   determinants whose alpha string is the t-th alpha single of alpha(D_i):
+//         opposite-spin doubles when their beta string is a beta single of beta(D_i)
+struct ConnArgs {
+    const uint64_t *dets;
+    const int32_t *ia, *ib;
+    const int64_t *ga_off, *gb_off, *as_off;
+    const int32_t *ga_det, *gb_det, *as_idx;
+    const uint64_t *ga_str, *gb_str, *astr;
+    int64_t n_det;
+    int *work_counter;
+    int64_t *cnt;              // count pass: connections per row
+    unsigned long long *cand;  // count pass: candidates screened
+    const int64_t *rowptr;     // fill pass
+    int32_t *col;
+    double *val;
+};
+
+constexpr int CONN_THREADS = 256;
+
+template <int W, bool FILL>
+__global__ void __launch_bounds__(CONN_THREADS) k_connect(ConnArgs A, DevInts I) {
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    unsigned long long cand_local = 0;
+    while (true) {
+        int i = 0;
+        if (lane == 0) i = atomicAdd(A.work_counter, 1);
+        i = __shfl_sync(0xffffffffu, i, 0);
+        if ((int64_t)i >= A.n_det) break;
+        const int a = A.ia[i], b = A.ib[i];
+        const Str<W> Ai = load_str<W>(A.dets, 2 * (int64_t)i);
+        const Str<W> Bi = load_str<W>(A.dets, 2 * (int64_t)i + 1);
+        const int64_t s_beg = A.as_off[a];
+        const int n_seg = 2 + (int)(A.as_off[a + 1] - s_beg);
+        int64_t found = 0;
+        int64_t out_pos = FILL ? A.rowptr[i] : 0;
+        for (int base = 0; base < n_seg; base += 32) {
+            // this lane's segment
+            int sid = base + lane;
+            int64_t start = 0;
+            int len = 0, type = 2, k = 0;
+            if (sid < n_seg) {
+                if (sid == 0) {
+                    start = A.gb_off[b];
+                    len = (int)(A.gb_off[b + 1] - start);
+                    type = 0;
+                } else if (sid == 1) {
+                    start = A.ga_off[a];
+                    len = (int)(A.ga_off[a + 1] - start);
+                    type = 1;
+                } else {
+                    k = A.as_idx[s_beg + sid - 2];
+                    start = A.ga_off[k];
+                    len = (int)(A.ga_off[k + 1] - start);
+                    type = 2;
+                }
+            }
+            int incl = len;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                int u = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += u;
+            }
+            const int excl = incl - len;
+            const int total = __shfl_sync(0xffffffffu, incl, 31);
+            if (!FILL) cand_local += (lane == 0) ? (unsigned long long)total : 0ull;
+            for (int t0 = 0; t0 < total; t0 += 32) {
+                const int t = t0 + lane;
+                // owner segment: largest lane L with excl_L <= t
+                int lo = 0;
+#pragma unroll
+                for (int step = 16; step >= 1; step >>= 1) {
+                    int cand = lo + step;
+                    int ex = __shfl_sync(0xffffffffu, excl, cand & 31);
+                    if (cand < 32 && ex <= t) lo = cand;
+                }
+                const int64_t s_start = __shfl_sync(0xffffffffu, start, lo);
+                const int s_excl = __shfl_sync(0xffffffffu, excl, lo);
+                const int s_type = __shfl_sync(0xffffffffu, type, lo);
+                const int s_k = __shfl_sync(0xffffffffu, k, lo);
+                bool match = false;
+                Str<W> other;
+                int32_t j = 0;
+                if (t < total) {
+                    const int64_t m = s_start + (t - s_excl);
+                    if (s_type == 0) {
+                        other = load_str<W>(A.gb_str, m);       // alpha string of D_j
+                        int d = xor_popc<W>(Ai, other);
+                        match = (d == 2) | (d == 4);
+                        if (match) j = A.gb_det[m];
+                    } else {
+                        other = load_str<W>(A.ga_str, m);       // beta string of D_j
+                        int d = xor_popc<W>(Bi, other);
+                        match = s_type == 1 ? ((d == 2) | (d == 4)) : (d == 2);
+                        if (match) j = A.ga_det[m];
+                    }
+                }
+                const unsigned mask = __ballot_sync(0xffffffffu, match);
+                if (FILL && match) {
+                    Str<W> Aj, Bj;
+                    if (s_type == 0) {
+                        Aj = other;
+                        Bj = Bi;
+                    } else if (s_type == 1) {
+                        Aj = Ai;
+                        Bj = other;
+                    } else {
+                        Aj = load_str<W>(A.astr, s_k);
+                        Bj = other;
+                    }
+                    const int64_t pos = out_pos + __popc(mask & lt);
+                    A.col[pos] = j;
+                    A.val[pos] = hij_offdiag<W>(I, Ai, Bi, Aj, Bj);
+                }
+                out_pos += __popc(mask);
+                found += __popc(mask);
+            }
+        }
+        if (!FILL && lane == 0) A.cnt[i] = found;
+    }
+    if (!FILL) {
+        if (lane == 0 && cand_local) atomicAdd(A.cand, cand_local);
+    }
+}
+
+// ====================================================================== host pipeline
+
+static inline unsigned grid_for(int64_t n, int threads = 256) {
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, threads), 152 * 32));
+}
+
+template <int W>
+static void unique_strings(shci_ctx *c, int spin, DevBuf<uint64_t> &ustr, DevBuf<int32_t> &sidx, int64_t &U) {
+    const int64_t n = c->n_det;
+    cudaStream_t st = c->st;
+    c->sort_keys.alloc((size_t)n * W);
+    c->sort_vals.alloc((size_t)n);
+    k_extract_strings<W><<<grid_for(n), 256, 0, st>>>(c->dets.p, n, spin, c->sort_keys.p, c->sort_vals.p);
+    KERNEL_CHECK();
+    radix_sort<W>(c->sort_keys.p, c->sort_vals.p, n, c->sw, st);
+    c->i64a.alloc((size_t)n + 1);
+    c->i64b.alloc((size_t)n + 1);
+    c->i64c.alloc((size_t)scan_tmp_len(n + 1));
+    k_head_flags<W><<<grid_for(n), 256, 0, st>>>(c->sort_keys.p, n, c->i64a.p);
+    exclusive_scan<int64_t>(c->i64a.p, c->i64b.p, n, c->i64c.p, st);
+    CUDA_TRY(cudaMemcpyAsync(&U, c->i64b.p + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    ustr.alloc((size_t)U * W);
+    sidx.alloc((size_t)n);
+    k_unique_write<W><<<grid_for(n), 256, 0, st>>>(c->sort_keys.p, c->sort_vals.p, c->i64a.p, c->i64b.p, n, ustr.p,
+                                                   sidx.p);
+    KERNEL_CHECK();
+    LAUNCHED(3);
+}
+
+template <int W>
+static void group_by(shci_ctx *c, const int32_t *major, const int32_t *minor, int64_t n_groups, int other_spin,
+                     DevBuf<int64_t> &off, DevBuf<int32_t> &mdet, DevBuf<uint64_t> &mstr) {
+    const int64_t n = c->n_det;
+    cudaStream_t st = c->st;
+    k_composite<<<grid_for(n), 256, 0, st>>>(major, minor, n, c->sort_keys.p, c->sort_vals.p);
+    KERNEL_CHECK();
+    radix_sort<1>(c->sort_keys.p, c->sort_vals.p, n, c->sw, st);
+    off.alloc((size_t)n_groups + 1);
+    mdet.alloc((size_t)n);
+    mstr.alloc((size_t)n * W);
+    k_group_build<W><<<grid_for(n), 256, 0, st>>>(c->sort_keys.p, c->sort_vals.p, n, c->dets.p, other_spin,
+                                                  n_groups, off.p, mdet.p, mstr.p, c->counter.p);
+    KERNEL_CHECK();
+    LAUNCHED(2);
+}
+
+template <int W>
+static void alpha_singles(shci_ctx *c) {
+    cudaStream_t st = c->st;
+    const int64_t Ua = c->Ua;
+    const int ne = c->n_alpha;
+    const int64_t nk = Ua * ne;
+    c->as_off.alloc((size_t)Ua + 1);
+    if (ne == 0 || nk == 0) {
+        CUDA_TRY(cudaMemsetAsync(c->as_off.p, 0, sizeof(int64_t) * (Ua + 1), st));
+        c->as_idx.alloc(1);
+        c->n_alpha_singles = 0;
+        return;
+    }
+    if (nk > 0x7FFFFFFFll) throw ShciError{SHCI_ERR_INVALID, "too many alpha strings"};
+    c->sort_keys.alloc((size_t)std::max<int64_t>(nk * W, c->n_det * W));
+    c->sort_vals.alloc((size_t)std::max<int64_t>(nk, c->n_det));
+    k_minus_one_keys<W><<<grid_for(Ua), 256, 0, st>>>(c->astr.p, Ua, ne, c->sort_keys.p, c->sort_vals.p);
+    KERNEL_CHECK();
+    radix_sort<W>(c->sort_keys.p, c->sort_vals.p, nk, c->sw, st);
+    DevBuf<int64_t> seg_start;
+    DevBuf<int32_t> seg_len;
+    seg_start.alloc((size_t)nk);
+    seg_len.alloc((size_t)nk);
+    k_segment_info<W><<<grid_for(nk), 256, 0, st>>>(c->sort_keys.p, c->sort_vals.p, nk, seg_start.p, seg_len.p);
+    c->i64a.alloc((size_t)std::max<int64_t>(Ua + 1, c->n_det + 1));
+    c->i64c.alloc((size_t)scan_tmp_len(std::max<int64_t>(Ua + 1, c->n_det + 1)));
+    k_singles_count<<<grid_for(Ua), 256, 0, st>>>(seg_len.p, Ua, ne, c->i64a.p);
+    exclusive_scan<int64_t>(c->i64a.p, c->as_off.p, Ua, c->i64c.p, st);
+    int64_t total = 0;
+    CUDA_TRY(cudaMemcpyAsync(&total, c->as_off.p + Ua, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    c->as_idx.alloc((size_t)std::max<int64_t>(total, 1));
+    k_singles_fill<<<grid_for(Ua), 256, 0, st>>>(seg_start.p, seg_len.p, c->sort_vals.p, Ua, ne, c->as_off.p,
+                                                 c->as_idx.p);
+    KERNEL_CHECK();
+    LAUNCHED(4);
+    CUDA_TRY(cudaStreamSynchronize(st));
+    c->n_alpha_singles = total;
+}
+
+template <int W>
+static void build_w(shci_ctx *c, int mode) {
+    cudaStream_t st = c->st;
+    const int64_t n = c->n_det;
+    c->counter.alloc(4);
+    CUDA_TRY(cudaMemsetAsync(c->counter.p, 0, 4 * sizeof(int), st));
+    k_validate<W><<<grid_for(n), 256, 0, st>>>(c->dets.p, n, c->n_orb, c->n_alpha, c->n_beta, c->counter.p);
+    KERNEL_CHECK();
+    LAUNCHED(1);
+    int flags = 0;
+    CUDA_TRY(cudaMemcpyAsync(&flags, c->counter.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    if (flags & 1) throw ShciError{SHCI_ERR_INVALID, "an alpha string does not hold n_alpha electrons"};
+    if (flags & 2) throw ShciError{SHCI_ERR_INVALID, "a beta string does not hold n_beta electrons"};
+    if (flags & 4) throw ShciError{SHCI_ERR_INVALID, "a determinant occupies an orbital >= n_orb"};
+
+    unique_strings<W>(c, 0, c->astr, c->ia, c->Ua);
+    unique_strings<W>(c, 1, c->bstr, c->ib, c->Ub);
+    group_by<W>(c, c->ia.p, c->ib.p, c->Ua, 1, c->ga_off, c->ga_det, c->ga_str);
+    group_by<W>(c, c->ib.p, c->ia.p, c->Ub, 0, c->gb_off, c->gb_det, c->gb_str);
+    CUDA_TRY(cudaMemcpyAsync(&flags, c->counter.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    if (flags & 8) throw ShciError{SHCI_ERR_INVALID, "duplicate determinants in V"};
+    alpha_singles<W>(c);
+
+    DevInts I = dev_ints(c);
+    c->diag.alloc((size_t)n);
+    k_diag<W><<<grid_for(n, 128), 128, 0, st>>>(c->dets.p, n, I, c->diag.p);
+    KERNEL_CHECK();
+    LAUNCHED(1);
+
+    // count pass
+    ConnArgs A{};
+    A.dets = c->dets.p;
+    A.ia = c->ia.p;
+    A.ib = c->ib.p;
+    A.ga_off = c->ga_off.p;
+    A.gb_off = c->gb_off.p;
+    A.as_off = c->as_off.p;
+    A.ga_det = c->ga_det.p;
+    A.gb_det = c->gb_det.p;
+    A.as_idx = c->as_idx.p;
+    A.ga_str = c->ga_str.p;
+    A.gb_str = c->gb_str.p;
+    A.astr = c->astr.p;
+    A.n_det = n;
+    DevBuf<unsigned long long> cand;
+    cand.alloc(1);
+    CUDA_TRY(cudaMemsetAsync(cand.p, 0, sizeof(unsigned long long), st));
+    c->rowptr.alloc((size_t)n + 1);
+    c->i64a.alloc((size_t)n + 1);
+    c->i64c.alloc((size_t)scan_tmp_len(n + 1));
+    A.work_counter = c->counter.p + 1;
+    A.cnt = c->i64a.p;
+    A.cand = cand.p;
+    int conn_blocks = c->n_sm * (2048 / CONN_THREADS);
+    k_connect<W, false><<<conn_blocks, CONN_THREADS, 0, st>>>(A, I);
+    KERNEL_CHECK();
+    LAUNCHED(1);
+    exclusive_scan<int64_t>(c->i64a.p, c->rowptr.p, n, c->i64c.p, st);
+    int64_t nnz = 0;
+    unsigned long long ncand = 0;
+    CUDA_TRY(cudaMemcpyAsync(&nnz, c->rowptr.p + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(&ncand, cand.p, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    c->nnz_full = nnz;
+    c->nnz_upper = nnz / 2;
+    c->candidates = (int64_t)ncand;
+    if (mode == SHCI_AUTO) {
+        size_t free_b = 0, total_b = 0;
+        CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+        double need = (double)nnz * 12.0;
+        mode = need < 0.8 * (double)free_b ? SHCI_STORED : SHCI_ON_THE_FLY;
+    }
+    c->mode = mode;
+    if (mode == SHCI_STORED) {
+        c->col.alloc((size_t)std::max<int64_t>(nnz, 1));
+        c->val.alloc((size_t)std::max<int64_t>(nnz, 1));
+        CUDA_TRY(cudaMemsetAsync(c->counter.p + 1, 0, sizeof(int), st));
+        A.rowptr = c->rowptr.p;
+        A.col = c->col.p;
+        A.val = c->val.p;
+        k_connect<W, true><<<conn_blocks, CONN_THREADS, 0, st>>>(A, I);
+        KERNEL_CHECK();
+        LAUNCHED(1);
+    } else {
+        c->col.reset();
+        c->val.reset();
+    }
+    CUDA_TRY(cudaStreamSynchronize(st));
+}
+
+void build(shci_ctx *c, int n_alpha, int n_beta, int64_t n_det, const uint64_t *dets, int mem, int mode) {
+    if (!c->have_ints) throw ShciError{SHCI_ERR_STATE, "load integrals before building"};
+    if (n_det < 1 || n_det > 0x7FFFFFFFll) throw ShciError{SHCI_ERR_INVALID, "n_det must be in [1, 2^31-1]"};
+    if (!dets) throw ShciError{SHCI_ERR_INVALID, "null determinant pointer"};
+    if (n_alpha < 0 || n_beta < 0 || n_alpha > c->n_orb || n_beta > c->n_orb)
+        throw ShciError{SHCI_ERR_INVALID, "electron counts out of range"};
+    if (mode != SHCI_STORED && mode != SHCI_ON_THE_FLY && mode != SHCI_AUTO)
+        throw ShciError{SHCI_ERR_INVALID, "unknown mode"};
+    if (mem != SHCI_MEM_HOST && mem != SHCI_MEM_DEVICE) throw ShciError{SHCI_ERR_INVALID, "unknown mem_space"};
+    const int W = (c->n_orb + 63) / 64;
+    c->built = false;
+    c->W = W;
+    c->n_alpha = n_alpha;
+    c->n_beta = n_beta;
+    c->n_det = n_det;
+    c->dets.alloc((size_t)n_det * 2 * W);
+    CUDA_TRY(cudaMemcpyAsync(c->dets.p, dets, sizeof(uint64_t) * n_det * 2 * W,
+                             mem == SHCI_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, c->st));
+    cudaEvent_t e0, e1;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    CUDA_TRY(cudaEventRecord(e0, c->st));
+    if (W == 1) build_w<1>(c, mode);
+    else build_w<2>(c, mode);
+    CUDA_TRY(cudaEventRecord(e1, c->st));
+    CUDA_TRY(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->stats.build_ms = ms;
+    c->built = true;
+}
+
+// ====================================================================== export
+
+void export_pairs(shci_ctx *c, int64_t cap, int64_t *i_out, int64_t *j_out, double *v_out, int64_t *n_out) {
+    if (!c->built || c->mode != SHCI_STORED) throw ShciError{SHCI_ERR_STATE, "no stored Hamiltonian"};
+    if (n_out) *n_out = c->nnz_upper;
+    if (cap < c->nnz_upper || c->nnz_upper == 0) return;
+    if (!i_out || !j_out) throw ShciError{SHCI_ERR_INVALID, "null output pointer"};
+    const int64_t n = c->n_det;
+    std::vector<int64_t> rp((size_t)n + 1);
+    std::vector<int32_t> cl((size_t)c->nnz_full);
+    std::vector<double> vl((size_t)c->nnz_full);
+    CUDA_TRY(cudaMemcpyAsync(rp.data(), c->rowptr.p, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost, c->st));
+    CUDA_TRY(cudaMemcpyAsync(cl.data(), c->col.p, sizeof(int32_t) * c->nnz_full, cudaMemcpyDeviceToHost, c->st));
+    CUDA_TRY(cudaMemcpyAsync(vl.data(), c->val.p, sizeof(double) * c->nnz_full, cudaMemcpyDeviceToHost, c->st));
+    CUDA_TRY(cudaStreamSynchronize(c->st));
+    int64_t o = 0;
+    std::vector<std::pair<int32_t, double>> row;
+    for (int64_t i = 0; i < n; i++) {
+        row.clear();
+        for (int64_t p = rp[i]; p < rp[i + 1]; p++)
+            if (cl[p] > i) row.emplace_back(cl[p], vl[p]);
+        std::sort(row.begin(), row.end(),
+                  [](const std::pair<int32_t, double> &x, const std::pair<int32_t, double> &y) { return x.first < y.first; });
+        for (auto &e : row) {
+            i_out[o] = i;
+            j_out[o] = e.first;
+            if (v_out) v_out[o] = e.second;
+            o++;
+        }
+    }
+}
+
+}  // namespace shci

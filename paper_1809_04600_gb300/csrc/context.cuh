@@ -1,0 +1,94 @@
+// The library context and the internal entry points shared by the .cu files.
+#pragma once
+#include "common.cuh"
+#include "prims.cuh"
+
+struct DavidsonWork {
+    int n_alloc = 0, m_alloc = 0, k_alloc = 0;
+    DevBuf<double> V, AV;        // [m_max][n]
+    DevBuf<double> X, Y;         // interleaved block [n][k] (sigma input / output)
+    DevBuf<double> T;            // [k][n] corrections / Ritz scratch
+    DevBuf<double> RV, RAV;      // [keep][n] thick-restart rotation targets
+    DevBuf<double> G;            // [m_max][m_max] projected matrix
+    DevBuf<double> evec;         // [m_max][m_max] subspace eigenvectors (column-major)
+    DevBuf<double> eval;         // [m_max]
+    DevBuf<double> partial;      // block partial sums for dot products
+    DevBuf<double> small;        // small device scalars (norms, coefficients)
+    DevBuf<double> host_pinned_dummy;
+    double *h_status = nullptr;  // pinned host mirror of the status block
+};
+
+struct shci_ctx {
+    int device = 0;
+    cudaStream_t st = nullptr;
+    bool own_stream = false;
+    std::string err;
+    int n_sm = 0;
+
+    // integrals
+    bool have_ints = false;
+    int n_orb = 0;
+    double e_core = 0.0;
+    DevBuf<double> h, eri, jk1, j1, jdiag, kdiag;
+
+    // variational space and helper lists (Table I)
+    bool built = false;
+    int mode = SHCI_STORED;
+    int W = 1, n_alpha = 0, n_beta = 0;
+    int64_t n_det = 0;
+    DevBuf<uint64_t> dets;                 // [n][2W]
+    int64_t Ua = 0, Ub = 0;                // unique alpha / beta strings
+    DevBuf<uint64_t> astr, bstr;           // [U][W]
+    DevBuf<int32_t> ia, ib;                // string index of each determinant
+    DevBuf<int64_t> ga_off, gb_off;        // determinants grouped by alpha / beta string
+    DevBuf<int32_t> ga_det, gb_det;        // member determinant indices
+    DevBuf<uint64_t> ga_str, gb_str;       // member beta / alpha strings [m][W]
+    DevBuf<int64_t> as_off;                // alpha-single lists over unique alpha strings
+    DevBuf<int32_t> as_idx;
+    DevBuf<double> diag;                   // H_ii
+
+    // stored H, both triangles, diagonal separate
+    DevBuf<int64_t> rowptr;
+    DevBuf<int32_t> col;
+    DevBuf<double> val;
+    int64_t nnz_full = 0, nnz_upper = 0;
+
+    // scratch
+    shci::SortWork sw;
+    DevBuf<uint64_t> sort_keys;
+    DevBuf<uint32_t> sort_vals;
+    DevBuf<int64_t> i64a, i64b, i64c;
+    DevBuf<int32_t> i32a;
+    DevBuf<int> counter;                   // dynamic work counters / flags
+    DevBuf<double> vec_a, vec_b;           // layout conversion for the ABI sigma
+
+    DavidsonWork dw;
+
+    // measurements
+    bool timing = false;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    shci_stats_t stats{};
+    int64_t candidates = 0;
+    int64_t n_alpha_singles = 0;
+};
+
+namespace shci {
+
+// integrals.cu / build.cu
+void load_integrals(shci_ctx *c, int n_orb, double e_core, const double *h, const double *eri, int mem);
+void build(shci_ctx *c, int n_alpha, int n_beta, int64_t n_det, const uint64_t *dets, int mem, int mode);
+void export_pairs(shci_ctx *c, int64_t cap, int64_t *i_out, int64_t *j_out, double *v_out, int64_t *n_out);
+
+// sigma.cu: y = H x for k vectors; `inter` selects the interleaved [n][k]
+// layout (otherwise vector-major [k][n]).
+void sigma(shci_ctx *c, int k, const double *x, double *y, bool inter);
+
+// davidson.cu
+int davidson(shci_ctx *c, int k, double tol, int max_iter, const double *guess, double *energies,
+             double *vecs, int mem, int *iters_out);
+
+DevInts dev_ints(const shci_ctx *c);
+
+inline void count_launch(shci_ctx *c, int n = 1) { c->stats.kernel_launches += n; }
+
+}  // namespace shci

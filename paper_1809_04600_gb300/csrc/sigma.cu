@@ -1,0 +1,116 @@
+// sigma = H c: the matrix-vector product of each Davidson step (Sec. IV.B).
+//
+// Stored mode keeps both triangles of H as CSR rows (diagonal separate), so a
+// row's product is a pure gather: one FP64 FMA per stored nonzero per vector
+// and no atomics.  (The paper stores the upper triangle and scatters the
+// transposed half with hardware atomics; on GB300, FP64 atomics in L2 run at
+// about a third of the FP64 FMA rate, so the scatter would dominate.)
+#include <algorithm>
+#include <atomic>
+
+#include "context.cuh"
+
+
+namespace shci {
+
+constexpr int SIGMA_THREADS = 256;
+
+// One warp per row.  x and y are [n][K] (INTER) or [K][n].
+template <int K, bool INTER>
+__global__ void __launch_bounds__(SIGMA_THREADS) k_sigma_stored(int64_t n, const int64_t *__restrict__ rowptr,
+                                                                const int32_t *__restrict__ col,
+                                                                const double *__restrict__ val,
+                                                                const double *__restrict__ diag,
+                                                                const double *__restrict__ x, double *__restrict__ y) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (SIGMA_THREADS / 32);
+    for (int64_t i = ((int64_t)blockIdx.x * SIGMA_THREADS + threadIdx.x) >> 5; i < n; i += warps) {
+        double acc[K];
+#pragma unroll
+        for (int q = 0; q < K; q++) acc[q] = 0.0;
+        const int64_t beg = rowptr[i], end = rowptr[i + 1];
+        for (int64_t p = beg + lane; p < end; p += 32) {
+            const int64_t j = __ldg(&col[p]);
+            const double v = __ldg(&val[p]);
+            if (INTER) {
+                if (K == 2) {
+                    const double2 c2 = __ldg(reinterpret_cast<const double2 *>(x) + j);
+                    acc[0] = fma(v, c2.x, acc[0]);
+                    acc[K - 1] = fma(v, c2.y, acc[K - 1]);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < K; q++) acc[q] = fma(v, __ldg(&x[j * K + q]), acc[q]);
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < K; q++) acc[q] = fma(v, __ldg(&x[q * n + j]), acc[q]);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < K; q++) {
+#pragma unroll
+            for (int o = 16; o >= 1; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+        }
+        if (lane == 0) {
+            const double d = diag[i];
+#pragma unroll
+            for (int q = 0; q < K; q++) {
+                const int64_t xi = INTER ? i * K + q : q * n + i;
+                y[xi] = fma(d, x[xi], acc[q]);
+            }
+        }
+    }
+}
+
+template <int K, bool INTER>
+static void launch_stored(shci_ctx *c, const double *x, double *y) {
+    int blocks = c->n_sm * (2048 / SIGMA_THREADS);
+    k_sigma_stored<K, INTER><<<blocks, SIGMA_THREADS, 0, c->st>>>(c->n_det, c->rowptr.p, c->col.p, c->val.p,
+                                                                 c->diag.p, x, y);
+    KERNEL_CHECK();
+}
+
+template <bool INTER>
+static void dispatch_stored(shci_ctx *c, int k, const double *x, double *y) {
+    switch (k) {
+        case 1: launch_stored<1, INTER>(c, x, y); break;
+        case 2: launch_stored<2, INTER>(c, x, y); break;
+        case 3: launch_stored<3, INTER>(c, x, y); break;
+        case 4: launch_stored<4, INTER>(c, x, y); break;
+        case 5: launch_stored<5, INTER>(c, x, y); break;
+        case 6: launch_stored<6, INTER>(c, x, y); break;
+        case 7: launch_stored<7, INTER>(c, x, y); break;
+        case 8: launch_stored<8, INTER>(c, x, y); break;
+        default: throw ShciError{SHCI_ERR_INVALID, "k must be in [1, 8]"};
+    }
+}
+
+void sigma_otf(shci_ctx *c, int k, const double *x, double *y, bool inter);
+
+void sigma(shci_ctx *c, int k, const double *x, double *y, bool inter) {
+    if (!c->built) throw ShciError{SHCI_ERR_STATE, "build the connectivity before sigma"};
+    if (c->timing) CUDA_TRY(cudaEventRecord(c->ev0, c->st));
+    if (c->mode == SHCI_STORED) {
+        if (inter) dispatch_stored<true>(c, k, x, y);
+        else dispatch_stored<false>(c, k, x, y);
+    } else {
+        sigma_otf(c, k, x, y, inter);
+    }
+    g_kernel_launches += 1;
+    c->stats.sigma_launches += 1;
+    c->stats.sigma_vectors += k;
+    if (c->timing) {
+        CUDA_TRY(cudaEventRecord(c->ev1, c->st));
+        CUDA_TRY(cudaEventSynchronize(c->ev1));
+        float ms = 0.f;
+        CUDA_TRY(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+        c->stats.sigma_ms_total += ms;
+    }
+}
+
+void sigma_otf(shci_ctx *c, int k, const double *x, double *y, bool inter) {
+    (void)k; (void)x; (void)y; (void)inter;
+    throw ShciError{SHCI_ERR_STATE, "on-the-fly sigma is not available in this build"};
+}
+
+}  // namespace shci

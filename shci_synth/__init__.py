@@ -268,7 +268,7 @@ CONFIGS = {
     "sel_24o_6a6b_1m": Config("sel_24o_6a6b_1m", 24, 6, 6, 60, 1002, 1_000_000, 2),
     # large shape like a transition-metal dimer: 76 orbitals, 14a14b, 12-orbital band
     "sel_76o_14a14b_50m": Config("sel_76o_14a14b_50m", 76, 14, 14, 300, 1003, 50_000_000, 1,
-                                 band=12, window=(10, 22, 4)),
+                                 band=12, window=(8, 16, 4)),
     # differentiation workload: 20 orbitals, 5a5b, |V| = 1e6
     "sel_20o_5a5b_1m": Config("sel_20o_5a5b_1m", 20, 5, 5, 40, 1004, 1_000_000, 1),
 }
