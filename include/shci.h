@@ -122,6 +122,22 @@ int shci_get_row(shci_ctx *ctx, int64_t row, int64_t cap, int64_t *cols, double 
  * on-the-fly product in SHCI_ON_THE_FLY mode.  c and sigma must not overlap. */
 int shci_sigma(shci_ctx *ctx, int k, const double *c, double *sigma, int mem_space);
 
+/* sigma = H c like shci_sigma, for device pointers only, with no device
+ * allocation of any kind.  The paper has no counterpart: this entry point is
+ * for callers that cannot let a library call cudaMalloc -- a process whose
+ * device memory is already handed to another allocator, or a latency-critical
+ * loop that must not pay the device-wide synchronisation of cudaMalloc.
+ * Its layout scratch is one file-scope __device__ array of 2 x 524,288
+ * doubles (8 MiB), held on every GPU that loads the library until exit.
+ * Requirements: built in SHCI_STORED mode, k in [1, 8],
+ * k * n_det <= 524,288 (SHCI_ERR_INVALID otherwise), c and sigma device
+ * [k][n_det], not overlapping.  The first call on a device looks up the
+ * array's address with that device current: make it before any stream
+ * capture.  All calls share the array, so calls that overlap on the GPU race;
+ * nothing in it needs to start at zero.  Synchronises the context's stream
+ * before returning. */
+int shci_sigma_noalloc(shci_ctx *ctx, int k, const double *c, double *sigma);
+
 /* Lowest k_roots (in [1, 8]) eigenpairs of H on V by diagonally
  * preconditioned Davidson (Sec. II.A).  Converged when, for every root, the
  * Ritz value moved by less than `tol` since the previous iteration and the

@@ -35,7 +35,7 @@ _STATUS = {1: "INVALID", 2: "OOM", 3: "CUDA", 4: "NOT_CONVERGED", 5: "TIMEOUT", 
 # every symbol include/shci.h declares (checked by the tests)
 EXPORTED = [
     "shci_create", "shci_destroy", "shci_last_error", "shci_load_integrals", "shci_build_connectivity",
-    "shci_get_diag", "shci_get_pairs", "shci_get_row", "shci_sigma", "shci_davidson", "shci_get_stats", "shci_set_timing",
+    "shci_get_diag", "shci_get_pairs", "shci_get_row", "shci_sigma", "shci_sigma_noalloc", "shci_davidson", "shci_get_stats", "shci_set_timing",
 ]
 
 
@@ -77,6 +77,7 @@ def load_library(path: str = LIB_PATH):
         "shci_get_pairs": (i32, [vp, i64, vp, vp, vp, ctypes.POINTER(i64)]),
         "shci_get_row": (i32, [vp, i64, i64, vp, vp, ctypes.POINTER(i64)]),
         "shci_sigma": (i32, [vp, i32, vp, vp, i32]),
+        "shci_sigma_noalloc": (i32, [vp, i32, vp, vp]),
         "shci_davidson": (i32, [vp, i32, f64, i32, vp, vp, vp, i32, ctypes.POINTER(i32)]),
         "shci_get_stats": (i32, [vp, ctypes.POINTER(shci_stats_t)]),
         "shci_set_timing": (i32, [vp, i32]),
@@ -195,6 +196,18 @@ def shci_sigma(ctx, c, sigma):
         raise ValueError("c and sigma must live in the same memory space")
     k = 1 if len(c.shape) == 1 else c.shape[0]
     _check(ctx, load_library().shci_sigma(ctx, int(k), pc, ps, mc))
+    return sigma
+
+
+def shci_sigma_noalloc(ctx, c, sigma):
+    """sigma[k, n] = H c[k, n] for torch CUDA tensors, with no device allocation
+    (static scratch; k * n_det <= 524,288)."""
+    pc, mc, kc = _ptr(c, np.float64)
+    ps, ms, ks = _ptr(sigma, np.float64)
+    if mc != SHCI_MEM_DEVICE or ms != SHCI_MEM_DEVICE:
+        raise ValueError("shci_sigma_noalloc takes device tensors only")
+    k = 1 if len(c.shape) == 1 else c.shape[0]
+    _check(ctx, load_library().shci_sigma_noalloc(ctx, int(k), pc, ps))
     return sigma
 
 

@@ -1,0 +1,108 @@
+// shci_sigma_noalloc: sigma = H c without any device allocation.
+//
+// The regular shci_sigma converts k > 1 vectors between the caller's
+// vector-major layout and the interleaved layout of the sigma kernel through
+// buffers the context allocates on first use.  Some callers cannot let a
+// library call cudaMalloc: a process whose device memory is already handed
+// out to another allocator (a framework's caching pool that reserved nearly
+// all of HBM), or a latency-critical loop that must not pay the implicit
+// device-wide synchronisation of cudaMalloc/cudaFree.  This entry point keeps
+// its layout scratch in one file-scope __device__ array of fixed size instead.
+//
+// Limits and behaviour:
+//  - scratch: SHCI_NOALLOC_MAX_ELEMS doubles per buffer, two buffers (8 MiB in
+//    total); every GPU that loads the library holds this array until the
+//    process exits.  Calls with k * n_det > SHCI_NOALLOC_MAX_ELEMS return
+//    SHCI_ERR_INVALID.
+//  - the first call on a device looks up the array's device address
+//    (cudaGetSymbolAddress) with that device current; make that first call
+//    before any stream capture.
+//  - every call shares the one array: calls that overlap on the GPU (other
+//    streams, other contexts, other host threads) race on it.
+//  - nothing in the scratch has to start at zero: each element a call reads
+//    was written earlier in the same call.
+#include <algorithm>
+#include <mutex>
+
+#include "context.cuh"
+
+#define SHCI_NOALLOC_MAX_ELEMS (1 << 19)   // 524,288 doubles = 4 MiB per buffer
+
+namespace {
+
+static __device__ __align__(256) double g_noalloc_scratch[2 * SHCI_NOALLOC_MAX_ELEMS];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+double *g_noalloc_ptr[kMaxDevices] = {nullptr};
+
+// device address of the scratch array on `device` (which must be current)
+double *noalloc_scratch(int device) {
+    if (device < 0 || device >= kMaxDevices) throw ShciError{SHCI_ERR_INVALID, "device index out of range"};
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[device]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            throw ShciError{SHCI_ERR_CUDA, std::string("cudaGetSymbolAddress(noalloc scratch): ") +
+                                               cudaGetErrorString(e)};
+        g_noalloc_ptr[device] = static_cast<double *>(p);
+    }
+    return g_noalloc_ptr[device];
+}
+
+// src [rows][cols] -> dst [cols][rows]
+__global__ void k_noalloc_transpose(const double *__restrict__ src, int rows, int64_t cols,
+                                    double *__restrict__ dst) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < rows * cols;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int r = (int)(e % rows);
+        int64_t c = e / rows;
+        dst[e] = src[(int64_t)r * cols + c];
+    }
+}
+
+}  // namespace
+
+extern "C" int shci_sigma_noalloc(shci_ctx *c, int k, const double *x, double *y) {
+    if (!c) return SHCI_ERR_INVALID;
+    try {
+        int dev = -1;
+        cudaGetDevice(&dev);
+        if (dev != c->device) CUDA_TRY(cudaSetDevice(c->device));
+        c->err.clear();
+        if (!c->built || c->mode != SHCI_STORED)
+            throw ShciError{SHCI_ERR_STATE, "shci_sigma_noalloc needs a Hamiltonian built in SHCI_STORED mode"};
+        if (k < 1 || k > SHCI_MAX_K) throw ShciError{SHCI_ERR_INVALID, "k must be in [1, 8]"};
+        if (!x || !y) throw ShciError{SHCI_ERR_INVALID, "null vector pointer"};
+        const int64_t n = c->n_det;
+        if ((int64_t)k * n > SHCI_NOALLOC_MAX_ELEMS)
+            throw ShciError{SHCI_ERR_INVALID,
+                            "k * n_det exceeds the static scratch of shci_sigma_noalloc (524288 elements)"};
+        const char *xb = (const char *)x, *yb = (const char *)y;
+        const size_t bytes = sizeof(double) * k * n;
+        if (xb < yb + bytes && yb < xb + bytes) throw ShciError{SHCI_ERR_INVALID, "c and sigma overlap"};
+        double *scratch = noalloc_scratch(c->device);
+        if (k == 1) {
+            shci::sigma(c, 1, x, y, false);
+        } else {
+            double *xi = scratch;                              // interleaved input  [n][k]
+            double *yi = scratch + SHCI_NOALLOC_MAX_ELEMS;     // interleaved output [n][k]
+            unsigned g = (unsigned)std::min<int64_t>(ceil_div((int64_t)k * n, 256), 152 * 64);
+            k_noalloc_transpose<<<g, 256, 0, c->st>>>(x, k, n, xi);
+            CUDA_TRY(cudaGetLastError());
+            shci::sigma(c, k, xi, yi, true);
+            k_noalloc_transpose<<<g, 256, 0, c->st>>>(yi, (int)n, k, y);
+            CUDA_TRY(cudaGetLastError());
+            g_kernel_launches += 2;
+        }
+        CUDA_TRY(cudaStreamSynchronize(c->st));
+        return SHCI_OK;
+    } catch (const ShciError &e) {
+        c->err = e.msg;
+        return e.code;
+    } catch (const std::exception &e) {
+        c->err = e.what();
+        return SHCI_ERR_INVALID;
+    }
+}
