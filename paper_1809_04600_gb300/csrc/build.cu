@@ -6,7 +6,7 @@
 #include <atomic>
 #include <numeric>
 
-#include "context.cuh"
+#include "enum_launch.cuh"
 
 std::atomic<long long> g_kernel_launches{0};
 #define LAUNCHED(n) (g_kernel_launches += (n))
@@ -254,133 +254,33 @@ __global__ void k_diag(const uint64_t *__restrict__ dets, int64_t n, DevInts I, 
 
 // ====================================================================== connectivity
 
-// Candidate segments of determinant i's row (Algorithms 1 and 2, Sec. III):
-//   0     determinants sharing beta(D_i): same-spin alpha singles/doubles
-//   1     determinants sharing alpha(D_i): same-spin beta singles/doubles
-//   2+t   determinants whose alpha string is the t-th alpha single of alpha(D_i):
-//         opposite-spin doubles when their beta string is a beta single of beta(D_i)
-struct ConnArgs {
-    const uint64_t *dets;
-    const int32_t *ia, *ib;
-    const int64_t *ga_off, *gb_off, *as_off;
-    const int32_t *ga_det, *gb_det, *as_idx;
-    const uint64_t *ga_str, *gb_str, *astr;
-    int64_t n_det;
-    int *work_counter;
-    int64_t *cnt;              // count pass: connections per row
-    unsigned long long *cand;  // count pass: candidates screened
-    const int64_t *rowptr;     // fill pass
-    int32_t *col;
-    double *val;
-};
+// (kernels in enumerate.cuh)
 
-constexpr int CONN_THREADS = 256;
-
-template <int W, bool FILL>
-__global__ void __launch_bounds__(CONN_THREADS) k_connect(ConnArgs A, DevInts I) {
-    const int lane = threadIdx.x & 31;
-    const unsigned lt = (1u << lane) - 1u;
-    unsigned long long cand_local = 0;
-    while (true) {
-        int i = 0;
-        if (lane == 0) i = atomicAdd(A.work_counter, 1);
-        i = __shfl_sync(0xffffffffu, i, 0);
-        if ((int64_t)i >= A.n_det) break;
-        const int a = A.ia[i], b = A.ib[i];
-        const Str<W> Ai = load_str<W>(A.dets, 2 * (int64_t)i);
-        const Str<W> Bi = load_str<W>(A.dets, 2 * (int64_t)i + 1);
-        const int64_t s_beg = A.as_off[a];
-        const int n_seg = 2 + (int)(A.as_off[a + 1] - s_beg);
-        int64_t found = 0;
-        int64_t out_pos = FILL ? A.rowptr[i] : 0;
-        for (int base = 0; base < n_seg; base += 32) {
-            // this lane's segment
-            int sid = base + lane;
-            int64_t start = 0;
-            int len = 0, type = 2, k = 0;
-            if (sid < n_seg) {
-                if (sid == 0) {
-                    start = A.gb_off[b];
-                    len = (int)(A.gb_off[b + 1] - start);
-                    type = 0;
-                } else if (sid == 1) {
-                    start = A.ga_off[a];
-                    len = (int)(A.ga_off[a + 1] - start);
-                    type = 1;
-                } else {
-                    k = A.as_idx[s_beg + sid - 2];
-                    start = A.ga_off[k];
-                    len = (int)(A.ga_off[k + 1] - start);
-                    type = 2;
-                }
-            }
-            int incl = len;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                int u = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += u;
-            }
-            const int excl = incl - len;
-            const int total = __shfl_sync(0xffffffffu, incl, 31);
-            if (!FILL) cand_local += (lane == 0) ? (unsigned long long)total : 0ull;
-            for (int t0 = 0; t0 < total; t0 += 32) {
-                const int t = t0 + lane;
-                // owner segment: largest lane L with excl_L <= t
-                int lo = 0;
-#pragma unroll
-                for (int step = 16; step >= 1; step >>= 1) {
-                    int cand = lo + step;
-                    int ex = __shfl_sync(0xffffffffu, excl, cand & 31);
-                    if (cand < 32 && ex <= t) lo = cand;
-                }
-                const int64_t s_start = __shfl_sync(0xffffffffu, start, lo);
-                const int s_excl = __shfl_sync(0xffffffffu, excl, lo);
-                const int s_type = __shfl_sync(0xffffffffu, type, lo);
-                const int s_k = __shfl_sync(0xffffffffu, k, lo);
-                bool match = false;
-                Str<W> other;
-                int32_t j = 0;
-                if (t < total) {
-                    const int64_t m = s_start + (t - s_excl);
-                    if (s_type == 0) {
-                        other = load_str<W>(A.gb_str, m);       // alpha string of D_j
-                        int d = xor_popc<W>(Ai, other);
-                        match = (d == 2) | (d == 4);
-                        if (match) j = A.gb_det[m];
-                    } else {
-                        other = load_str<W>(A.ga_str, m);       // beta string of D_j
-                        int d = xor_popc<W>(Bi, other);
-                        match = s_type == 1 ? ((d == 2) | (d == 4)) : (d == 2);
-                        if (match) j = A.ga_det[m];
-                    }
-                }
-                const unsigned mask = __ballot_sync(0xffffffffu, match);
-                if (FILL && match) {
-                    Str<W> Aj, Bj;
-                    if (s_type == 0) {
-                        Aj = other;
-                        Bj = Bi;
-                    } else if (s_type == 1) {
-                        Aj = Ai;
-                        Bj = other;
-                    } else {
-                        Aj = load_str<W>(A.astr, s_k);
-                        Bj = other;
-                    }
-                    const int64_t pos = out_pos + __popc(mask & lt);
-                    A.col[pos] = j;
-                    A.val[pos] = hij_offdiag<W>(I, Ai, Bi, Aj, Bj);
-                }
-                out_pos += __popc(mask);
-                found += __popc(mask);
-            }
-        }
-        if (!FILL && lane == 0) A.cnt[i] = found;
-    }
-    if (!FILL) {
-        if (lane == 0 && cand_local) atomicAdd(A.cand, cand_local);
-    }
+__global__ void k_add_i64(int64_t *__restrict__ a, const int64_t *__restrict__ b, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        a[i] += b[i];
 }
+
+static void make_items(shci_ctx *c, const int64_t *off, int64_t n_groups, DevBuf<int32_t> &item_group,
+                       DevBuf<int32_t> &item_first, int64_t &n_items) {
+    cudaStream_t st = c->st;
+    DevBuf<int64_t> cnt, start, tmp;
+    cnt.alloc((size_t)n_groups + 1);
+    start.alloc((size_t)n_groups + 1);
+    tmp.alloc((size_t)scan_tmp_len(n_groups + 1));
+    unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n_groups, 256), 4096));
+    k_items_count<<<g, 256, 0, st>>>(off, n_groups, cnt.p);
+    exclusive_scan<int64_t>(cnt.p, start.p, n_groups, tmp.p, st);
+    CUDA_TRY(cudaMemcpyAsync(&n_items, start.p + n_groups, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    if (n_items > 0x7FFFFFFFll) throw ShciError{SHCI_ERR_INVALID, "too many work items"};
+    item_group.alloc((size_t)std::max<int64_t>(n_items, 1));
+    item_first.alloc((size_t)std::max<int64_t>(n_items, 1));
+    k_items_fill<<<g, 256, 0, st>>>(off, start.p, n_groups, item_group.p, item_first.p);
+    KERNEL_CHECK();
+    g_kernel_launches += 2;
+}
+
 
 // ====================================================================== host pipeline
 
@@ -500,32 +400,25 @@ static void build_w(shci_ctx *c, int mode) {
     KERNEL_CHECK();
     LAUNCHED(1);
 
-    // count pass
-    ConnArgs A{};
-    A.dets = c->dets.p;
-    A.ia = c->ia.p;
-    A.ib = c->ib.p;
-    A.ga_off = c->ga_off.p;
-    A.gb_off = c->gb_off.p;
-    A.as_off = c->as_off.p;
-    A.ga_det = c->ga_det.p;
-    A.gb_det = c->gb_det.p;
-    A.as_idx = c->as_idx.p;
-    A.ga_str = c->ga_str.p;
-    A.gb_str = c->gb_str.p;
-    A.astr = c->astr.p;
-    A.n_det = n;
+    // work items: chunks of ENUM_NW rows of one alpha (beta) group
+    make_items(c, c->ga_off.p, c->Ua, c->item_a_group, c->item_a_first, c->n_items_a);
+    make_items(c, c->gb_off.p, c->Ub, c->item_b_group, c->item_b_first, c->n_items_b);
+
+    // count pass: entries of the beta-grouped part and of the alpha-grouped part of each row
     DevBuf<unsigned long long> cand;
     cand.alloc(1);
     CUDA_TRY(cudaMemsetAsync(cand.p, 0, sizeof(unsigned long long), st));
     c->rowptr.alloc((size_t)n + 1);
+    c->cnt_b.alloc((size_t)n);
     c->i64a.alloc((size_t)n + 1);
     c->i64c.alloc((size_t)scan_tmp_len(n + 1));
-    A.work_counter = c->counter.p + 1;
-    A.cnt = c->i64a.p;
+    EnumArgs A = enum_args(c);
     A.cand = cand.p;
-    int conn_blocks = c->n_sm * (2048 / CONN_THREADS);
-    k_connect<W, false><<<conn_blocks, CONN_THREADS, 0, st>>>(A, I);
+    A.cnt = c->cnt_b.p;
+    launch_enum<W, ENUM_COUNT, 0>(c, A, I, false);
+    A.cnt = c->i64a.p;
+    launch_enum<W, ENUM_COUNT, 0>(c, A, I, true);
+    k_add_i64<<<grid_for(n), 256, 0, st>>>(c->i64a.p, c->cnt_b.p, n);
     KERNEL_CHECK();
     LAUNCHED(1);
     exclusive_scan<int64_t>(c->i64a.p, c->rowptr.p, n, c->i64c.p, st);
@@ -547,13 +440,13 @@ static void build_w(shci_ctx *c, int mode) {
     if (mode == SHCI_STORED) {
         c->col.alloc((size_t)std::max<int64_t>(nnz, 1));
         c->val.alloc((size_t)std::max<int64_t>(nnz, 1));
-        CUDA_TRY(cudaMemsetAsync(c->counter.p + 1, 0, sizeof(int), st));
         A.rowptr = c->rowptr.p;
         A.col = c->col.p;
         A.val = c->val.p;
-        k_connect<W, true><<<conn_blocks, CONN_THREADS, 0, st>>>(A, I);
-        KERNEL_CHECK();
-        LAUNCHED(1);
+        A.part_off = nullptr;
+        launch_enum<W, ENUM_FILL, 0>(c, A, I, false);
+        A.part_off = c->cnt_b.p;
+        launch_enum<W, ENUM_FILL, 0>(c, A, I, true);
     } else {
         c->col.reset();
         c->val.reset();

@@ -46,6 +46,10 @@ struct shci_ctx {
     DevBuf<int64_t> as_off;                // alpha-single lists over unique alpha strings
     DevBuf<int32_t> as_idx;
     DevBuf<double> diag;                   // H_ii
+    // enumeration work items: chunks of rows of one alpha (beta) group
+    DevBuf<int32_t> item_a_group, item_a_first, item_b_group, item_b_first;
+    int64_t n_items_a = 0, n_items_b = 0;
+    DevBuf<int64_t> cnt_b;                 // entries of the beta-grouped part of each row
 
     // stored H, both triangles, diagonal separate
     DevBuf<int64_t> rowptr;

@@ -2,48 +2,53 @@
 // (Sec. II.A; the cached diagonal of Sec. IV.B is the preconditioner).
 //
 // Everything runs on the device in FP64: the block sigma product, the
-// projected matrix V^T H V, its eigen-decomposition (a parallel cyclic Jacobi
-// solver in one CTA), Ritz vectors, residuals, the preconditioner and the
-// Gram-Schmidt orthogonalisation.  The host only sequences launches and reads
-// a few scalars (Ritz values, residual norms) once per iteration.
+// projected matrix V^T H V, its eigen-decomposition (warm-started threshold
+// Jacobi in one CTA), Ritz vectors, residuals, the preconditioner and the
+// block orthonormalisation (classical Gram-Schmidt twice against the basis,
+// then Cholesky-QR twice within the block).  The host only sequences launches
+// and reads a few scalars twice per iteration (Ritz values and residual norms;
+// the number of accepted new vectors).
 #include <algorithm>
 #include <atomic>
 #include <cmath>
 
 #include "context.cuh"
 
-
 namespace shci {
 
 constexpr int DV_THREADS = 256;
-constexpr int DOT_ROWS = 16;  // partial-sum slots per block for A-rows
 
-// rows of A handled per multi-dot launch for NB columns of B (NA * NB <= 16)
+// ---------------------------------------------------------------- block Gram products
+
+// rows of A handled per block for NB columns of B (NA * NB <= 16 accumulators)
 template <int NB>
-struct DotShape {
+struct GramShape {
     static constexpr int NA = NB >= 16 ? 1 : 16 / NB;
 };
 
-// partial[blk][a][b] = sum over this block's slice of A[a][i] * B[b][i]
-// for a < na (<= NA), b < NB
+// partial[(slice * na + a) * NB + b] = sum over this slice of A[a][i] * B[b][i];
+// blockIdx.x = slice, blockIdx.y = group of NA rows of A
 template <int NB>
-__global__ void __launch_bounds__(DV_THREADS) k_multidot(const double *__restrict__ A, int na,
-                                                        const double *__restrict__ B, int64_t n,
-                                                        double *__restrict__ partial) {
-    constexpr int NA = DotShape<NB>::NA;
+__global__ void __launch_bounds__(DV_THREADS) k_gram(const double *__restrict__ A, int na,
+                                                    const double *__restrict__ B, int64_t n,
+                                                    double *__restrict__ partial) {
+    constexpr int NA = GramShape<NB>::NA;
+    const int a0 = blockIdx.y * NA;
+    const int cnt = min(NA, na - a0);
     double acc[NA][NB];
 #pragma unroll
     for (int a = 0; a < NA; a++)
 #pragma unroll
         for (int b = 0; b < NB; b++) acc[a][b] = 0.0;
-    for (int64_t i = blockIdx.x * (int64_t)DV_THREADS + threadIdx.x; i < n; i += (int64_t)gridDim.x * DV_THREADS) {
+    const int64_t stride = (int64_t)gridDim.x * DV_THREADS;
+    for (int64_t i = blockIdx.x * (int64_t)DV_THREADS + threadIdx.x; i < n; i += stride) {
         double bv[NB];
 #pragma unroll
         for (int b = 0; b < NB; b++) bv[b] = B[b * n + i];
 #pragma unroll
         for (int a = 0; a < NA; a++) {
-            if (a < na) {
-                const double av = A[a * n + i];
+            if (a < cnt) {
+                const double av = A[(int64_t)(a0 + a) * n + i];
 #pragma unroll
                 for (int b = 0; b < NB; b++) acc[a][b] = fma(av, bv[b], acc[a][b]);
             }
@@ -63,24 +68,29 @@ __global__ void __launch_bounds__(DV_THREADS) k_multidot(const double *__restric
     }
     __syncthreads();
     const int e = threadIdx.x;
-    if (e < na * NB) {
+    if (e < cnt * NB) {
         double s = 0.0;
 #pragma unroll
         for (int x = 0; x < DV_THREADS / 32; x++) s += red[e][x];
-        partial[(int64_t)blockIdx.x * DOT_ROWS * SHCI_MAX_K + (e / NB) * SHCI_MAX_K + (e % NB)] = s;
+        partial[((int64_t)blockIdx.x * na + a0 + e / NB) * NB + (e % NB)] = s;
     }
 }
 
-// out[(a0 + a) * ld + b0 + b] = sum_blk partial[blk][a][b]  (and the mirror when sym)
-__global__ void k_multidot_final(const double *__restrict__ partial, int nblk, int na, int nb, double *out, int ld,
-                                 int a0, int b0, int sym) {
-    int e = threadIdx.x;
+// out[(a0 + a) * ld + b0 + b] = sum_slice partial[(slice * na + a) * nb + b]; one warp per entry
+__global__ void k_gram_reduce(const double *__restrict__ partial, int nslices, int na, int nb, double *out, int ld,
+                              int a0, int b0, int sym) {
+    const int e = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
     if (e >= na * nb) return;
-    int a = e / nb, b = e % nb;
+    const int a = e / nb, b = e % nb;
     double s = 0.0;
-    for (int k = 0; k < nblk; k++) s += partial[(int64_t)k * DOT_ROWS * SHCI_MAX_K + a * SHCI_MAX_K + b];
-    out[(a0 + a) * ld + b0 + b] = s;
-    if (sym) out[(b0 + b) * ld + a0 + a] = s;
+    for (int x = lane; x < nslices; x += 32) s += partial[((int64_t)x * na + a) * nb + b];
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) {
+        out[(a0 + a) * ld + b0 + b] = s;
+        if (sym) out[(b0 + b) * ld + a0 + a] = s;
+    }
 }
 
 // ---------------------------------------------------------------- vector kernels
@@ -96,207 +106,300 @@ __global__ void k_unpack(const double *__restrict__ X, int k, int64_t n, double 
         for (int b = 0; b < k; b++) V[b * n + i] = X[i * k + b];
 }
 
-// T[l] -= sum_a C[a * ldc + l] * V[a]   for a < m, l < kb
-__global__ void k_project_out(const double *__restrict__ V, int m, const double *__restrict__ C, int ldc, int kb,
-                              int64_t n, double *__restrict__ T) {
-    __shared__ double cs[SHCI_MAX_SUB * SHCI_MAX_K];
-    for (int e = threadIdx.x; e < m * kb; e += blockDim.x) cs[e] = C[(e / kb) * ldc + (e % kb)];
+// T[l] -= sum_a C[a * KB + l] * V[a]   for a < m, l < KB
+template <int KB>
+__global__ void __launch_bounds__(DV_THREADS) k_project(const double *__restrict__ V, int m,
+                                                       const double *__restrict__ C, int64_t n,
+                                                       double *__restrict__ T) {
+    __shared__ double cs[SHCI_MAX_SUB * KB];
+    for (int e = threadIdx.x; e < m * KB; e += blockDim.x) cs[e] = C[e];
     __syncthreads();
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        double t[SHCI_MAX_K];
+    for (int64_t i = blockIdx.x * (int64_t)DV_THREADS + threadIdx.x; i < n; i += (int64_t)gridDim.x * DV_THREADS) {
+        double t[KB];
 #pragma unroll
-        for (int l = 0; l < SHCI_MAX_K; l++) t[l] = l < kb ? T[l * n + i] : 0.0;
-        for (int a = 0; a < m; a++) {
-            const double v = V[a * n + i];
+        for (int l = 0; l < KB; l++) t[l] = T[l * n + i];
+        int a = 0;
+        for (; a + 4 <= m; a += 4) {
+            const double v0 = V[(int64_t)a * n + i], v1 = V[(int64_t)(a + 1) * n + i];
+            const double v2 = V[(int64_t)(a + 2) * n + i], v3 = V[(int64_t)(a + 3) * n + i];
 #pragma unroll
-            for (int l = 0; l < SHCI_MAX_K; l++)
-                if (l < kb) t[l] = fma(-cs[a * kb + l], v, t[l]);
+            for (int l = 0; l < KB; l++) {
+                t[l] = fma(-cs[a * KB + l], v0, t[l]);
+                t[l] = fma(-cs[(a + 1) * KB + l], v1, t[l]);
+                t[l] = fma(-cs[(a + 2) * KB + l], v2, t[l]);
+                t[l] = fma(-cs[(a + 3) * KB + l], v3, t[l]);
+            }
+        }
+        for (; a < m; a++) {
+            const double v = V[(int64_t)a * n + i];
+#pragma unroll
+            for (int l = 0; l < KB; l++) t[l] = fma(-cs[a * KB + l], v, t[l]);
         }
 #pragma unroll
-        for (int l = 0; l < SHCI_MAX_K; l++)
-            if (l < kb) T[l * n + i] = t[l];
+        for (int l = 0; l < KB; l++) T[l * n + i] = t[l];
     }
 }
 
-// dst = src * (1 / sqrt(nrm2[0])) or zero if the norm is below tiny
-__global__ void k_normalize(const double *__restrict__ src, const double *__restrict__ nrm2, int64_t n,
-                            double *__restrict__ dst) {
-    double s2 = nrm2[0];
-    double f = s2 > 1e-26 ? 1.0 / sqrt(s2) : 0.0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        dst[i] = src[i] * f;
+// Cholesky-QR coefficients for kb vectors with Gram matrix S (kb x kb).
+// Column l is dropped when its component outside the span of the accepted
+// earlier columns has squared norm below rel * ref[l] (ref: S's diagonal, or
+// the squared norms before projection when given).  Writes M (kb x kb,
+// column l' of the accepted set) such that q_l' = sum_j M[j * kb + l'] t_j is
+// orthonormal, and *count = number accepted.  One thread; kb <= 8.
+__global__ void k_cholqr_coef(const double *__restrict__ S, int kb, const double *__restrict__ ref, double rel,
+                              double *__restrict__ M, int *__restrict__ count) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double R[SHCI_MAX_K][SHCI_MAX_K];
+    double Mi[SHCI_MAX_K][SHCI_MAX_K];   // Mi[j][l]: coefficient of t_j in q_l
+    int acc[SHCI_MAX_K];
+    int na = 0;
+    for (int l = 0; l < kb; l++)
+        for (int j = 0; j < kb; j++) { R[j][l] = 0.0; Mi[j][l] = 0.0; }
+    for (int l = 0; l < kb; l++) {
+        // R[j][l] for accepted j < l
+        for (int x = 0; x < na; x++) {
+            int j = acc[x];
+            double s = S[j * kb + l];
+            for (int y = 0; y < x; y++) s -= R[acc[y]][j] * R[acc[y]][l];
+            R[j][l] = s / R[j][j];
+        }
+        double d = S[l * kb + l];
+        for (int x = 0; x < na; x++) d -= R[acc[x]][l] * R[acc[x]][l];
+        double r0 = ref ? ref[l] : S[l * kb + l];
+        if (!(d > rel * r0) || !(d > 1e-300)) continue;      // numerically dependent: drop
+        R[l][l] = sqrt(d);
+        // q_l = (t_l - sum_{j acc} R[j][l] q_j) / R[l][l]
+        for (int j = 0; j < kb; j++) {
+            double v = (j == l) ? 1.0 : 0.0;
+            for (int x = 0; x < na; x++) v -= R[acc[x]][l] * Mi[j][acc[x]];
+            Mi[j][l] = v / R[l][l];
+        }
+        acc[na++] = l;
+    }
+    for (int j = 0; j < kb; j++)
+        for (int x = 0; x < kb; x++) M[j * kb + x] = x < na ? Mi[j][acc[x]] : 0.0;
+    *count = na;
 }
 
-// Ritz vectors and residuals for roots l < k of the subspace of size m:
-//   x_l = sum_a Y[a][l] V[a],  h_l = sum_a Y[a][l] AV[a],  r_l = h_l - theta_l x_l
-// mode 0: T[l] = r_l / (theta_l - H_ii) (clamped), partial |r_l|^2 per block
-// mode 1: X[l] = x_l, H[l] = h_l (restart / output)
-__global__ void __launch_bounds__(DV_THREADS) k_ritz(const double *__restrict__ V, const double *__restrict__ AV,
-                                                     int m, const double *__restrict__ evec, int ld,
-                                                     const double *__restrict__ eval, int k, int64_t n,
-                                                     const double *__restrict__ diag, int mode,
-                                                     double *__restrict__ T, double *__restrict__ Xo,
-                                                     double *__restrict__ Ho, double *__restrict__ partial) {
-    __shared__ double ys[SHCI_MAX_SUB * SHCI_MAX_K];
-    __shared__ double th[SHCI_MAX_K];
-    for (int e = threadIdx.x; e < m * k; e += blockDim.x) ys[e] = evec[(e % k) * ld + (e / k)];   // ys[a*k+l]
-    if (threadIdx.x < k) th[threadIdx.x] = eval[threadIdx.x];
+// out[l'] = sum_j M[j * KB + l'] T[j] for l' < KB; slots l' >= *count are
+// zero-filled when zero_fill, otherwise left untouched
+template <int KB>
+__global__ void __launch_bounds__(DV_THREADS) k_apply_coef(const double *__restrict__ T,
+                                                          const double *__restrict__ M,
+                                                          const int *__restrict__ count, int zero_fill, int64_t n,
+                                                          double *__restrict__ out) {
+    __shared__ double ms[KB * KB];
+    for (int e = threadIdx.x; e < KB * KB; e += blockDim.x) ms[e] = M[e];
     __syncthreads();
-    double rn[SHCI_MAX_K];
-#pragma unroll
-    for (int l = 0; l < SHCI_MAX_K; l++) rn[l] = 0.0;
+    const int na = *count;
     for (int64_t i = blockIdx.x * (int64_t)DV_THREADS + threadIdx.x; i < n; i += (int64_t)gridDim.x * DV_THREADS) {
-        double x[SHCI_MAX_K], h[SHCI_MAX_K];
+        double t[KB];
 #pragma unroll
-        for (int l = 0; l < SHCI_MAX_K; l++) { x[l] = 0.0; h[l] = 0.0; }
-        for (int a = 0; a < m; a++) {
-            const double v = V[a * n + i], av = AV[a * n + i];
+        for (int j = 0; j < KB; j++) t[j] = T[j * n + i];
 #pragma unroll
-            for (int l = 0; l < SHCI_MAX_K; l++) {
-                if (l < k) {
-                    x[l] = fma(ys[a * k + l], v, x[l]);
-                    h[l] = fma(ys[a * k + l], av, h[l]);
-                }
+        for (int l = 0; l < KB; l++) {
+            if (l < na) {
+                double s = 0.0;
+#pragma unroll
+                for (int j = 0; j < KB; j++) s = fma(ms[j * KB + l], t[j], s);
+                out[l * n + i] = s;
+            } else if (zero_fill) {
+                out[l * n + i] = 0.0;
             }
         }
-        if (mode == 0) {
+    }
+}
+
+// Ritz vectors and residuals for K roots of the subspace of size m:
+//   x_l = sum_a Y[a][l] V[a],  h_l = sum_a Y[a][l] AV[a],  r_l = h_l - theta_l x_l
+// MODE 0: T[l] = r_l / (theta_l - H_ii) (clamped), partial |r_l|^2 per block
+// MODE 1: Xo[l] = x_l, Ho[l] = h_l (restart / output)
+template <int K, int MODE>
+__global__ void __launch_bounds__(DV_THREADS) k_ritz(const double *__restrict__ V, const double *__restrict__ AV,
+                                                     int m, const double *__restrict__ evec, int ld,
+                                                     const double *__restrict__ eval, int64_t n,
+                                                     const double *__restrict__ diag, double *__restrict__ T,
+                                                     double *__restrict__ Xo, double *__restrict__ Ho,
+                                                     double *__restrict__ partial) {
+    __shared__ double ys[SHCI_MAX_SUB * K];
+    __shared__ double th[K];
+    for (int e = threadIdx.x; e < m * K; e += blockDim.x) ys[e] = evec[(e % K) * ld + (e / K)];   // ys[a*K+l]
+    if (threadIdx.x < K) th[threadIdx.x] = eval[threadIdx.x];
+    __syncthreads();
+    double rn[K];
+#pragma unroll
+    for (int l = 0; l < K; l++) rn[l] = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)DV_THREADS + threadIdx.x; i < n; i += (int64_t)gridDim.x * DV_THREADS) {
+        double x[K], h[K];
+#pragma unroll
+        for (int l = 0; l < K; l++) { x[l] = 0.0; h[l] = 0.0; }
+        int a = 0;
+        for (; a + 2 <= m; a += 2) {
+            const double v0 = V[(int64_t)a * n + i], w0 = AV[(int64_t)a * n + i];
+            const double v1 = V[(int64_t)(a + 1) * n + i], w1 = AV[(int64_t)(a + 1) * n + i];
+#pragma unroll
+            for (int l = 0; l < K; l++) {
+                x[l] = fma(ys[a * K + l], v0, x[l]);
+                h[l] = fma(ys[a * K + l], w0, h[l]);
+                x[l] = fma(ys[(a + 1) * K + l], v1, x[l]);
+                h[l] = fma(ys[(a + 1) * K + l], w1, h[l]);
+            }
+        }
+        for (; a < m; a++) {
+            const double v = V[(int64_t)a * n + i], w = AV[(int64_t)a * n + i];
+#pragma unroll
+            for (int l = 0; l < K; l++) {
+                x[l] = fma(ys[a * K + l], v, x[l]);
+                h[l] = fma(ys[a * K + l], w, h[l]);
+            }
+        }
+        if (MODE == 0) {
             const double d = diag[i];
 #pragma unroll
-            for (int l = 0; l < SHCI_MAX_K; l++) {
-                if (l < k) {
-                    const double r = fma(-th[l], x[l], h[l]);
-                    rn[l] = fma(r, r, rn[l]);
-                    double den = th[l] - d;
-                    if (fabs(den) < 1e-8) den = den < 0.0 ? -1e-8 : 1e-8;
-                    T[l * n + i] = r / den;
-                }
+            for (int l = 0; l < K; l++) {
+                const double r = fma(-th[l], x[l], h[l]);
+                rn[l] = fma(r, r, rn[l]);
+                double den = th[l] - d;
+                if (fabs(den) < 1e-8) den = den < 0.0 ? -1e-8 : 1e-8;
+                T[l * n + i] = r / den;
             }
         } else {
 #pragma unroll
-            for (int l = 0; l < SHCI_MAX_K; l++) {
-                if (l < k) {
-                    Xo[l * n + i] = x[l];
-                    Ho[l * n + i] = h[l];
-                }
+            for (int l = 0; l < K; l++) {
+                Xo[l * n + i] = x[l];
+                Ho[l * n + i] = h[l];
             }
         }
     }
-    if (mode == 0) {
-        __shared__ double red[DV_THREADS / 32];
+    if (MODE == 0) {
+        __shared__ double red[K][DV_THREADS / 32];
         const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-        for (int l = 0; l < k; l++) {
+#pragma unroll
+        for (int l = 0; l < K; l++) {
             double v = rn[l];
 #pragma unroll
             for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0) red[w] = v;
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                double s = 0.0;
-                for (int x = 0; x < DV_THREADS / 32; x++) s += red[x];
-                partial[(int64_t)blockIdx.x * SHCI_MAX_K + l] = s;
-            }
-            __syncthreads();
+            if (lane == 0) red[l][w] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < K) {
+            double s = 0.0;
+#pragma unroll
+            for (int x = 0; x < DV_THREADS / 32; x++) s += red[threadIdx.x][x];
+            partial[(int64_t)blockIdx.x * K + threadIdx.x] = s;
         }
     }
 }
 
+// out[l] = sum_blk partial[blk * k + l]; one warp per root
 __global__ void k_sum_partials(const double *__restrict__ partial, int nblk, int k, double *__restrict__ out) {
-    int l = threadIdx.x;
+    const int l = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (l >= k) return;
     double s = 0.0;
-    for (int b = 0; b < nblk; b++) s += partial[(int64_t)b * SHCI_MAX_K + l];
-    out[l] = s;
+    for (int b = lane; b < nblk; b += 32) s += partial[(int64_t)b * k + l];
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) out[l] = s;
 }
 
 // ---------------------------------------------------------------- subspace eigensolver
 
 // Eigen-decomposition of the symmetric m x m matrix G (row-major, leading
-// dimension ld) by cyclic Jacobi with Brent-Luk parallel ordering: each round
-// applies m/2 disjoint rotations at once.  Outputs eigenvalues ascending and
-// eigenvectors as columns: evec[l * ld + a] = component a of vector l.
-__global__ void k_jacobi(const double *__restrict__ G, int ld, int m, double *__restrict__ eval,
+// dimension ld) by cyclic Jacobi with Brent-Luk parallel ordering (m/2
+// disjoint rotations per round).
+//
+// Warm start: when m_prev > 0, evec holds the eigenvectors of G's leading
+// m_prev x m_prev block from the previous call (G only grew since), so in
+// the basis blockdiag(evec, I) the leading block is diag(eval) and only the
+// new border has to be transformed.  Rotations whose off-diagonal element is
+// below 1e-15 (|a_pp| + |a_qq|) are skipped, and only the active pairs are
+// applied; sweeps stop when one applies no rotation.  Output: eigenvalues
+// (the converged diagonal) ascending and
+// eigenvectors as columns, evec[l * ld + a] = component a of vector l.
+__global__ void k_jacobi(const double *__restrict__ G, int ld, int m, int m_prev, double *__restrict__ eval,
                          double *__restrict__ evec) {
     extern __shared__ double jsm[];
     double (*A)[SHCI_MAX_SUB + 1] = reinterpret_cast<double (*)[SHCI_MAX_SUB + 1]>(jsm);
     double (*Q)[SHCI_MAX_SUB + 1] = reinterpret_cast<double (*)[SHCI_MAX_SUB + 1]>(jsm + SHCI_MAX_SUB * (SHCI_MAX_SUB + 1));
+    double *Gs = jsm + 2 * SHCI_MAX_SUB * (SHCI_MAX_SUB + 1);          // exact G, m x m (stride m)
     __shared__ double cs[SHCI_MAX_SUB / 2], sn[SHCI_MAX_SUB / 2];
     __shared__ int pp[SHCI_MAX_SUB / 2], qq[SHCI_MAX_SUB / 2];
-    __shared__ double red[32];
-    __shared__ int done;
+    __shared__ int n_active, any_rot;
+    __shared__ double lam[SHCI_MAX_SUB];
     const int mm = (m + 1) & ~1;
     const int tid = threadIdx.x, nt = blockDim.x;
+    const int mp = (m_prev > 0 && m_prev <= m) ? m_prev : 0;
+    for (int e = tid; e < m * m; e += nt) {
+        int r = e / m, c = e % m;
+        Gs[e] = 0.5 * (G[r * ld + c] + G[c * ld + r]);
+    }
+    // Q = blockdiag(previous eigenvectors, I)
     for (int e = tid; e < mm * mm; e += nt) {
         int r = e / mm, c = e % mm;
-        double v;
-        if (r < m && c < m) v = 0.5 * (G[r * ld + c] + G[c * ld + r]);
-        else v = 0.0;
-        A[r][c] = v;
-        Q[r][c] = (r == c) ? 1.0 : 0.0;
+        double q = (r == c) ? 1.0 : 0.0;
+        if (r < mp && c < mp) q = evec[c * ld + r];
+        Q[r][c] = q;
     }
     __syncthreads();
-    if (mm != m) {
-        // padding index: decoupled, with a diagonal value above every Gershgorin bound
-        if (tid == 0) {
-            double bound = 0.0;
-            for (int r = 0; r < m; r++) {
-                double s = 0.0;
-                for (int c = 0; c < m; c++) s += fabs(A[r][c]);
-                bound = fmax(bound, s);
+    // A = Q^T G Q: leading block diag(previous eigenvalues), border transformed, trailing block copied
+    for (int e = tid; e < mm * mm; e += nt) {
+        int r = e / mm, c = e % mm;
+        double v = 0.0;
+        if (r < m && c < m) {
+            if (r < mp && c < mp) {
+                v = (r == c) ? eval[r] : 0.0;
+            } else if (r < mp) {          // (Q^T G)[r][c] for border column c
+                for (int s = 0; s < mp; s++) v = fma(Q[s][r], Gs[s * m + c], v);
+            } else if (c < mp) {
+                for (int s = 0; s < mp; s++) v = fma(Q[s][c], Gs[r * m + s], v);
+            } else {
+                v = Gs[r * m + c];
             }
-            A[m][m] = 2.0 * bound + 1.0;
         }
-        __syncthreads();
+        A[r][c] = v;
     }
+    __syncthreads();
+    if (mm != m && tid == 0) {
+        // padding index: decoupled, with a diagonal value above every Gershgorin bound
+        double bound = 0.0;
+        for (int r = 0; r < m; r++) {
+            double s = 0.0;
+            for (int c = 0; c < m; c++) s += fabs(A[r][c]);
+            bound = fmax(bound, s);
+        }
+        A[m][m] = 2.0 * bound + 1.0;
+    }
+    __syncthreads();
     for (int sweep = 0; sweep < 60; sweep++) {
-        // convergence test on the off-diagonal Frobenius norm
-        double off = 0.0, tot = 0.0;
-        for (int e = tid; e < mm * mm; e += nt) {
-            int r = e / mm, c = e % mm;
-            double v = A[r][c] * A[r][c];
-            tot += v;
-            if (r != c) off += v;
-        }
-        for (int o = 16; o >= 1; o >>= 1) {
-            off += __shfl_xor_sync(0xffffffffu, off, o);
-            tot += __shfl_xor_sync(0xffffffffu, tot, o);
-        }
-        if ((tid & 31) == 0) {
-            red[tid >> 5] = off;
-            red[16 + (tid >> 5)] = tot;
-        }
+        if (tid == 0) any_rot = 0;
         __syncthreads();
-        if (tid == 0) {
-            double so = 0.0, st = 0.0;
-            for (int x = 0; x < nt / 32; x++) {
-                so += red[x];
-                st += red[16 + x];
-            }
-            done = (so <= 1e-30 * st) || (so < 1e-300);
-        }
-        __syncthreads();
-        if (done) break;
         for (int round = 0; round < mm - 1; round++) {
+            if (tid == 0) n_active = 0;
+            __syncthreads();
             if (tid < mm / 2) {
                 int x = tid, y = mm - 1 - tid;
                 int p = x == 0 ? 0 : ((x - 1 + round) % (mm - 1)) + 1;
                 int q = y == 0 ? 0 : ((y - 1 + round) % (mm - 1)) + 1;
                 if (p > q) { int t = p; p = q; q = t; }
-                double apq = A[p][q];
-                double c = 1.0, s = 0.0;
-                if (apq != 0.0) {
+                const double apq = A[p][q];
+                if (fabs(apq) > 1e-15 * (fabs(A[p][p]) + fabs(A[q][q])) + 1e-300) {
                     double tau = (A[q][q] - A[p][p]) / (2.0 * apq);
                     double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-                    c = 1.0 / sqrt(1.0 + t * t);
-                    s = t * c;
+                    double c = 1.0 / sqrt(1.0 + t * t);
+                    int slot = atomicAdd(&n_active, 1);
+                    cs[slot] = c;
+                    sn[slot] = t * c;
+                    pp[slot] = p;
+                    qq[slot] = q;
                 }
-                cs[tid] = c;
-                sn[tid] = s;
-                pp[tid] = p;
-                qq[tid] = q;
             }
             __syncthreads();
+            const int na = n_active;
+            __syncthreads();             // every thread has read n_active before it is reset
+            if (na == 0) continue;       // uniform: every thread read the same count
+            if (tid == 0) any_rot = 1;
             // rows: A <- J^T A
-            for (int e = tid; e < (mm / 2) * mm; e += nt) {
+            for (int e = tid; e < na * mm; e += nt) {
                 int t = e / mm, j = e % mm;
                 int p = pp[t], q = qq[t];
                 double c = cs[t], s = sn[t];
@@ -306,7 +409,7 @@ __global__ void k_jacobi(const double *__restrict__ G, int ld, int m, double *__
             }
             __syncthreads();
             // columns: A <- A J, Q <- Q J
-            for (int e = tid; e < (mm / 2) * mm; e += nt) {
+            for (int e = tid; e < na * mm; e += nt) {
                 int t = e / mm, i = e % mm;
                 int p = pp[t], q = qq[t];
                 double c = cs[t], s = sn[t];
@@ -319,13 +422,19 @@ __global__ void k_jacobi(const double *__restrict__ G, int ld, int m, double *__
             }
             __syncthreads();
         }
+        __syncthreads();
+        const int rot = any_rot;
+        __syncthreads();                 // every thread has read any_rot before it is reset
+        if (!rot) break;
     }
+    for (int a = tid; a < mm; a += nt) lam[a] = A[a][a];
+    __syncthreads();
     // sort ascending (rank by value, ties by index) and write out the first m
     for (int a = tid; a < mm; a += nt) {
-        double va = A[a][a];
+        double va = lam[a];
         int rank = 0;
         for (int b = 0; b < mm; b++) {
-            double vb = A[b][b];
+            double vb = lam[b];
             rank += (vb < va) || (vb == va && b < a);
         }
         if (rank < m) {
@@ -335,7 +444,7 @@ __global__ void k_jacobi(const double *__restrict__ G, int ld, int m, double *__
     }
 }
 
-constexpr size_t JACOBI_SMEM = sizeof(double) * 2 * SHCI_MAX_SUB * (SHCI_MAX_SUB + 1);
+constexpr size_t JACOBI_SMEM = sizeof(double) * (2 * SHCI_MAX_SUB * (SHCI_MAX_SUB + 1) + SHCI_MAX_SUB * SHCI_MAX_SUB);
 
 // ---------------------------------------------------------------- guesses
 
@@ -388,74 +497,107 @@ __global__ void k_unit_vectors(const int64_t *__restrict__ idx, int k, int64_t n
 
 // ---------------------------------------------------------------- host driver
 
+__global__ void k_diag_copy(const double *__restrict__ S, int kb, double *__restrict__ out) {
+    int l = threadIdx.x;
+    if (l < kb) out[l] = S[l * kb + l];
+}
+
+#define DISPATCH_K(kval, F)                         \
+    switch (kval) {                                 \
+        case 1: F(1); break;                        \
+        case 2: F(2); break;                        \
+        case 3: F(3); break;                        \
+        case 4: F(4); break;                        \
+        case 5: F(5); break;                        \
+        case 6: F(6); break;                        \
+        case 7: F(7); break;                        \
+        case 8: F(8); break;                        \
+        default: throw ShciError{SHCI_ERR_INVALID, "block size out of range"}; \
+    }
+
 struct Dav {
     shci_ctx *c;
     int64_t n;
     int k, m_max, keep;
-    int dot_blocks, vec_blocks;
+    int vec_blocks, n_slots;
     cudaStream_t st;
+    double *coef, *gram_s, *pre, *mcoef;   // device small buffers
+    int *d_count;
 
     double *Vr(int a) { return c->dw.V.p + (int64_t)a * n; }
     double *AVr(int a) { return c->dw.AV.p + (int64_t)a * n; }
 
-    // out[a0 + a][b0 + b] (ld) = A[a] . B[b], a < na, b < nb; mirror if sym
     template <int NB>
-    void dots_nb(const double *A, int na, const double *B, double *out, int ld, int a0, int b0, bool sym) {
-        constexpr int NA = DotShape<NB>::NA;
-        for (int base = 0; base < na; base += NA) {
-            int cnt = std::min(NA, na - base);
-            k_multidot<NB><<<dot_blocks, DV_THREADS, 0, st>>>(A + (int64_t)base * n, cnt, B, n, c->dw.partial.p);
-            k_multidot_final<<<1, DOT_ROWS * SHCI_MAX_K, 0, st>>>(c->dw.partial.p, dot_blocks, cnt, NB, out, ld,
-                                                                  a0 + base, b0, sym ? 1 : 0);
-            KERNEL_CHECK();
-            g_kernel_launches += 2;
-        }
+    void gram_nb(const double *A, int na, const double *B, double *out, int ld, int a0, int b0, bool sym) {
+        constexpr int NA = GramShape<NB>::NA;
+        const int groups = (na + NA - 1) / NA;
+        const int slices = std::max(1, std::min<int>((int)ceil_div(n, DV_THREADS * 4), n_slots / groups));
+        dim3 grid(slices, groups);
+        k_gram<NB><<<grid, DV_THREADS, 0, st>>>(A, na, B, n, c->dw.partial.p);
+        const int outs = na * NB;
+        k_gram_reduce<<<(outs + 7) / 8, 256, 0, st>>>(c->dw.partial.p, slices, na, NB, out, ld, a0, b0, sym ? 1 : 0);
+        KERNEL_CHECK();
+        g_kernel_launches += 2;
     }
 
-    // out[a0 + a][b0 + b] (ld) = A[a] . B[b], a < na, b < nb; mirror if sym
-    void dots(const double *A, int na, const double *B, int nb, double *out, int ld, int a0, int b0, bool sym) {
+    // out[a0 + a][b0 + b] (leading dimension ld) = A[a] . B[b], a < na, b < nb; mirrored if sym
+    void gram(const double *A, int na, const double *B, int nb, double *out, int ld, int a0, int b0, bool sym) {
+        if (na <= 0 || nb <= 0) return;
         int b = 0;
         while (b < nb) {
             int left = nb - b;
             const double *Bb = B + (int64_t)b * n;
-            if (left >= 8) { dots_nb<8>(A, na, Bb, out, ld, a0, b0 + b, sym); b += 8; }
-            else if (left >= 4) { dots_nb<4>(A, na, Bb, out, ld, a0, b0 + b, sym); b += 4; }
-            else if (left >= 2) { dots_nb<2>(A, na, Bb, out, ld, a0, b0 + b, sym); b += 2; }
-            else { dots_nb<1>(A, na, Bb, out, ld, a0, b0 + b, sym); b += 1; }
+            if (left >= 8) { gram_nb<8>(A, na, Bb, out, ld, a0, b0 + b, sym); b += 8; }
+            else if (left >= 4) { gram_nb<4>(A, na, Bb, out, ld, a0, b0 + b, sym); b += 4; }
+            else if (left >= 2) { gram_nb<2>(A, na, Bb, out, ld, a0, b0 + b, sym); b += 2; }
+            else { gram_nb<1>(A, na, Bb, out, ld, a0, b0 + b, sym); b += 1; }
         }
     }
 
-    // orthonormalise the kb vectors T[0..kb) against V[0..m) and each other,
-    // appending the accepted ones to V; returns how many were accepted
+    void project(const double *C, int m, int kb, double *T) {
+#define F(KB) k_project<KB><<<vec_blocks, DV_THREADS, 0, st>>>(c->dw.V.p, m, C, n, T)
+        DISPATCH_K(kb, F)
+#undef F
+        KERNEL_CHECK();
+        g_kernel_launches += 1;
+    }
+
+    void apply_coef(const double *T, int kb, double *out, bool zero_fill) {
+#define F(KB) k_apply_coef<KB><<<vec_blocks, DV_THREADS, 0, st>>>(T, mcoef, d_count, zero_fill ? 1 : 0, n, out)
+        DISPATCH_K(kb, F)
+#undef F
+        KERNEL_CHECK();
+        g_kernel_launches += 1;
+    }
+
+    // Orthonormalise the kb vectors T[0..kb) against V[0..m) (classical
+    // Gram-Schmidt, twice) and among themselves (Cholesky-QR, twice), writing
+    // the accepted ones to V[m ..); returns how many were accepted.
     int orthonormalize_append(double *T, int kb, int m) {
-        double *coef = c->dw.small.p;                 // [SHCI_MAX_SUB][SHCI_MAX_K]
-        double *nrm = c->dw.small.p + SHCI_MAX_SUB * SHCI_MAX_K;
-        int added = 0;
-        for (int l = 0; l < kb; l++) {
-            double *t = T + (int64_t)l * n;
-            int mb = m + added;
-            for (int pass = 0; pass < 2; pass++) {
-                if (mb > 0) {
-                    dots(c->dw.V.p, mb, t, 1, coef, 1, 0, 0, false);
-                    k_project_out<<<vec_blocks, DV_THREADS, 0, st>>>(c->dw.V.p, mb, coef, 1, 1, n, t);
-                    KERNEL_CHECK();
-                    g_kernel_launches += 1;
-                }
-            }
-            dots(t, 1, t, 1, nrm, 1, 0, 0, false);
-            double h_n = 0.0;
-            CUDA_TRY(cudaMemcpyAsync(&h_n, nrm, sizeof(double), cudaMemcpyDeviceToHost, st));
-            CUDA_TRY(cudaStreamSynchronize(st));
-            if (!(h_n > 1e-20)) continue;            // linearly dependent: drop
-            k_normalize<<<vec_blocks, DV_THREADS, 0, st>>>(t, nrm, n, Vr(mb));
-            KERNEL_CHECK();
-            g_kernel_launches += 1;
-            added++;
+        double *T2 = c->dw.T.p + (int64_t)SHCI_MAX_K * n;
+        // squared norms before projection: reference for the dependence test
+        gram(T, kb, T, kb, gram_s, kb, 0, 0, false);
+        k_diag_copy<<<1, 32, 0, st>>>(gram_s, kb, pre);
+        g_kernel_launches += 1;
+        for (int pass = 0; pass < 2 && m > 0; pass++) {
+            gram(c->dw.V.p, m, T, kb, coef, kb, 0, 0, false);
+            project(coef, m, kb, T);
         }
+        gram(T, kb, T, kb, gram_s, kb, 0, 0, false);
+        k_cholqr_coef<<<1, 1, 0, st>>>(gram_s, kb, pre, 1e-20, mcoef, d_count);
+        apply_coef(T, kb, T2, true);
+        gram(T2, kb, T2, kb, gram_s, kb, 0, 0, false);
+        k_cholqr_coef<<<1, 1, 0, st>>>(gram_s, kb, nullptr, 1e-12, mcoef, d_count);
+        apply_coef(T2, kb, Vr(m), false);
+        KERNEL_CHECK();
+        g_kernel_launches += 2;
+        int added = 0;
+        CUDA_TRY(cudaMemcpyAsync(&added, d_count, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
         return added;
     }
 
-    // AV[m0 .. m0 + kb) = H V[m0 .. m0 + kb); G columns updated
+    // AV[m0 .. m0 + kb) = H V[m0 .. m0 + kb); G's new columns (and rows)
     void expand(int m0, int kb) {
         k_pack<<<vec_blocks, DV_THREADS, 0, st>>>(Vr(m0), kb, n, c->dw.X.p);
         KERNEL_CHECK();
@@ -463,7 +605,31 @@ struct Dav {
         k_unpack<<<vec_blocks, DV_THREADS, 0, st>>>(c->dw.Y.p, kb, n, AVr(m0));
         KERNEL_CHECK();
         g_kernel_launches += 2;
-        dots(c->dw.V.p, m0 + kb, AVr(m0), kb, c->dw.G.p, m_max, 0, m0, true);
+        gram(c->dw.V.p, m0 + kb, AVr(m0), kb, c->dw.G.p, m_max, 0, m0, true);
+    }
+
+    void ritz_residuals(int m, double *T, double *d_rn) {
+#define F(K)                                                                                                 \
+    k_ritz<K, 0><<<vec_blocks, DV_THREADS, 0, st>>>(c->dw.V.p, c->dw.AV.p, m, c->dw.evec.p, m_max,          \
+                                                    c->dw.eval.p, n, c->diag.p, T, nullptr, nullptr,         \
+                                                    c->dw.partial.p)
+        DISPATCH_K(k, F)
+#undef F
+        k_sum_partials<<<1, 32 * k, 0, st>>>(c->dw.partial.p, vec_blocks, k, d_rn);
+        KERNEL_CHECK();
+        g_kernel_launches += 2;
+    }
+
+    // x_l = V y_l and h_l = AV y_l for l in [j0, j0 + cnt)
+    void ritz_vectors(int m, int j0, int cnt, double *Xo, double *Ho) {
+#define F(K)                                                                                                 \
+    k_ritz<K, 1><<<vec_blocks, DV_THREADS, 0, st>>>(c->dw.V.p, c->dw.AV.p, m, c->dw.evec.p + (int64_t)j0 * m_max, \
+                                                    m_max, c->dw.eval.p + j0, n, c->diag.p, nullptr, Xo, Ho, \
+                                                    nullptr)
+        DISPATCH_K(cnt, F)
+#undef F
+        KERNEL_CHECK();
+        g_kernel_launches += 1;
     }
 };
 
@@ -489,8 +655,8 @@ int davidson(shci_ctx *c, int k, double tol, int max_iter, const double *guess, 
     d.m_max = (int)std::min<int64_t>(std::min(SHCI_MAX_SUB, 16 + 16 * k), c->n_det);
     if (d.m_max < k) d.m_max = k;
     d.keep = std::max(k, std::min(d.m_max - k, std::max(2 * k, d.m_max / 3)));
-    d.dot_blocks = std::max(1, std::min<int>((int)ceil_div(d.n, DV_THREADS * 8), c->n_sm * 4));
     d.vec_blocks = std::max(1, std::min<int>((int)ceil_div(d.n, DV_THREADS), c->n_sm * 8));
+    d.n_slots = c->n_sm * 8;
     const int64_t n = d.n;
     const double res_tol = 0.1 * std::sqrt(tol);
     DavidsonWork &w = c->dw;
@@ -504,8 +670,15 @@ int davidson(shci_ctx *c, int k, double tol, int max_iter, const double *guess, 
     w.G.alloc((size_t)d.m_max * d.m_max);
     w.evec.alloc((size_t)d.m_max * d.m_max);
     w.eval.alloc((size_t)d.m_max);
-    w.partial.alloc((size_t)std::max(d.dot_blocks, d.vec_blocks) * DOT_ROWS * SHCI_MAX_K);
-    w.small.alloc((size_t)SHCI_MAX_SUB * SHCI_MAX_K + 64);
+    w.partial.alloc((size_t)std::max(d.n_slots, d.vec_blocks) * SHCI_MAX_SUB * SHCI_MAX_K);
+    w.small.alloc((size_t)4 * SHCI_MAX_SUB * SHCI_MAX_K + 64);
+    d.coef = w.small.p;                                        // [m_max][kb]
+    d.gram_s = w.small.p + SHCI_MAX_SUB * SHCI_MAX_K;          // [kb][kb]
+    d.pre = w.small.p + 2 * SHCI_MAX_SUB * SHCI_MAX_K;         // [kb]
+    d.mcoef = w.small.p + 2 * SHCI_MAX_SUB * SHCI_MAX_K + 16;  // [kb][kb]
+    double *d_rn = w.small.p + 3 * SHCI_MAX_SUB * SHCI_MAX_K;  // [k]
+    c->counter.alloc(4);
+    d.d_count = c->counter.p + 3;
     DevBuf<int64_t> idx;
     idx.alloc(SHCI_MAX_K);
     cudaStream_t st = c->st;
@@ -539,17 +712,16 @@ int davidson(shci_ctx *c, int k, double tol, int max_iter, const double *guess, 
     d.expand(0, m);
 
     std::vector<double> theta_old(k, INFINITY), status(2 * SHCI_MAX_K);
-    double *d_rn = w.small.p + SHCI_MAX_SUB * SHCI_MAX_K + 8;
     int it = 0;
+    int m_eig = 0;          // size of the leading block whose eigenvectors are in evec
     bool conv = false;
     std::vector<double> theta(k), rnorm(k);
     for (it = 1; it <= max_iter; it++) {
-        k_jacobi<<<1, 256, JACOBI_SMEM, st>>>(w.G.p, d.m_max, m, w.eval.p, w.evec.p);
-        k_ritz<<<d.vec_blocks, DV_THREADS, 0, st>>>(w.V.p, w.AV.p, m, w.evec.p, d.m_max, w.eval.p, k, n, c->diag.p,
-                                                    0, T, nullptr, nullptr, w.partial.p);
-        k_sum_partials<<<1, 32, 0, st>>>(w.partial.p, d.vec_blocks, k, d_rn);
+        k_jacobi<<<1, 256, JACOBI_SMEM, st>>>(w.G.p, d.m_max, m, m_eig, w.eval.p, w.evec.p);
         KERNEL_CHECK();
-        g_kernel_launches += 3;
+        g_kernel_launches += 1;
+        m_eig = m;
+        d.ritz_residuals(m, T, d_rn);
         CUDA_TRY(cudaMemcpyAsync(status.data(), w.eval.p, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
         CUDA_TRY(cudaMemcpyAsync(status.data() + SHCI_MAX_K, d_rn, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
         CUDA_TRY(cudaStreamSynchronize(st));
@@ -569,19 +741,15 @@ int davidson(shci_ctx *c, int k, double tol, int max_iter, const double *guess, 
             const int keep = std::min(m, d.keep);
             for (int j0 = 0; j0 < keep; j0 += SHCI_MAX_K) {
                 const int cnt = std::min(SHCI_MAX_K, keep - j0);
-                k_ritz<<<d.vec_blocks, DV_THREADS, 0, st>>>(w.V.p, w.AV.p, m, w.evec.p + (int64_t)j0 * d.m_max,
-                                                            d.m_max, w.eval.p + j0, cnt, n, c->diag.p, 1, nullptr,
-                                                            w.RV.p + (int64_t)j0 * n, w.RAV.p + (int64_t)j0 * n,
-                                                            nullptr);
-                KERNEL_CHECK();
-                g_kernel_launches += 1;
+                d.ritz_vectors(m, j0, cnt, w.RV.p + (int64_t)j0 * n, w.RAV.p + (int64_t)j0 * n);
             }
             CUDA_TRY(cudaMemcpyAsync(w.V.p, w.RV.p, sizeof(double) * keep * n, cudaMemcpyDeviceToDevice, st));
             CUDA_TRY(cudaMemcpyAsync(w.AV.p, w.RAV.p, sizeof(double) * keep * n, cudaMemcpyDeviceToDevice, st));
             // recompute the projected block exactly (V^T H V over the kept Ritz vectors)
             CUDA_TRY(cudaMemsetAsync(w.G.p, 0, sizeof(double) * d.m_max * d.m_max, st));
-            d.dots(w.V.p, keep, w.AV.p, keep, w.G.p, d.m_max, 0, 0, true);
+            d.gram(w.V.p, keep, w.AV.p, keep, w.G.p, d.m_max, 0, 0, true);
             m = keep;
+            m_eig = 0;
             // the residual corrections in T[0..k) are still valid: they depend only on the Ritz pairs
         }
         // corrections for the roots that are not yet converged
@@ -603,12 +771,9 @@ int davidson(shci_ctx *c, int k, double tol, int max_iter, const double *guess, 
     c->stats.davidson_iters = it > max_iter ? max_iter : it;
     for (int l = 0; l < k; l++) energies[l] = theta[l];
     if (vecs) {
+        // evec/eval still describe the current G (nothing changed since the last solve)
         double *Xr = w.T.p + (int64_t)SHCI_MAX_K * n;
-        k_jacobi<<<1, 256, JACOBI_SMEM, st>>>(w.G.p, d.m_max, m, w.eval.p, w.evec.p);
-        k_ritz<<<d.vec_blocks, DV_THREADS, 0, st>>>(w.V.p, w.AV.p, m, w.evec.p, d.m_max, w.eval.p, k, n, c->diag.p,
-                                                    1, nullptr, Xr, w.X.p, nullptr);
-        KERNEL_CHECK();
-        g_kernel_launches += 2;
+        d.ritz_vectors(m, 0, k, Xr, w.X.p);
         CUDA_TRY(cudaMemcpyAsync(vecs, Xr, sizeof(double) * k * n,
                                  mem == SHCI_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
     }

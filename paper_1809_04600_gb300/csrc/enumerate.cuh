@@ -1,0 +1,450 @@
+// Enumeration of the connected determinant pairs of V (Sec. III, Algorithms
+// 1 and 2) with a per-pair action: count, write H_ij (stored H), or
+// accumulate H_ij c_j (on-the-fly sigma).
+//
+// Two kernels cover every pair (i, j), i != j, of one row i exactly once:
+//   k_enum_alpha: rows grouped by alpha string a.  Candidates are the
+//     determinants whose alpha string is a itself (same-spin beta
+//     excitations) or one of a's alpha singles k (opposite-spin doubles when
+//     the beta strings differ by one electron).  A CTA takes up to NW rows of
+//     one alpha group (one warp each), so every candidate list it needs is the
+//     same for all its warps: the list is staged tile by tile in shared memory
+//     and screened by each warp with XOR + popcount + ballot.
+//   k_enum_beta: rows grouped by beta string b; candidates share b
+//     (same-spin alpha excitations), staged the same way.
+// Row i's entries are laid out [beta-grouped part | alpha-grouped part].
+//
+// Only a few percent of the screened candidates are connected, so matches are
+// not evaluated where they are found: each warp appends them to a queue in
+// shared memory and evaluates H_ij 32 at a time, one per lane.
+#pragma once
+#include "common.cuh"
+
+namespace shci {
+
+constexpr int ENUM_NW = 8;                  // warps (rows) per CTA
+constexpr int ENUM_THREADS = 32 * ENUM_NW;
+constexpr int ENUM_TILE = 1024;             // candidates staged per tile
+constexpr int ENUM_QCAP = 64;               // per-warp queue of found pairs
+
+enum { ENUM_COUNT = 0, ENUM_FILL = 1, ENUM_SIGMA = 2 };
+
+struct EnumArgs {
+    const uint64_t *dets;
+    const uint64_t *astr, *bstr;            // unique strings
+    const int64_t *ga_off, *gb_off;         // groups by alpha / beta string
+    const int32_t *ga_det, *gb_det;         // member determinant
+    const uint64_t *ga_str, *gb_str;        // member's other string
+    const int64_t *as_off;                  // alpha singles
+    const int32_t *as_idx;
+    const int32_t *item_group;              // work item -> group index
+    const int32_t *item_first;              // work item -> first member offset within the group
+    int64_t n_items;
+    int *work_counter;
+    // count
+    int64_t *cnt;                           // entries per row of this kernel's part
+    unsigned long long *cand;               // candidates screened (statistics)
+    // fill
+    const int64_t *rowptr;
+    const int64_t *part_off;                // offset of this kernel's part within the row (may be null)
+    int32_t *col;
+    double *val;
+    // sigma
+    const double *x;                        // [n][K] interleaved
+    double *y;                              // [n][K]
+    const double *diag;
+    int accumulate;                         // 0: y = diag x + part, 1: y += part
+};
+
+// ---------------------------------------------------------------- matrix element pieces
+
+// single excitation q -> p inside one spin string: D_i has string si, D_j has sj,
+// both determinants have the other-spin string `other`
+template <int W>
+__device__ __forceinline__ double single_exc(const DevInts &I, const Str<W> &si, const Str<W> &sj,
+                                             const Str<W> &other) {
+    const int n = I.n;
+    Str<W> pi, qj, common;
+#pragma unroll
+    for (int k = 0; k < W; k++) {
+        uint64_t d = si.w[k] ^ sj.w[k];
+        pi.w[k] = si.w[k] & d;
+        qj.w[k] = sj.w[k] & d;
+        common.w[k] = si.w[k] & sj.w[k];
+    }
+    const int p = lowest_bit<W>(pi), q = lowest_bit<W>(qj);
+    const int neg = bits_between<W>(common, p < q ? p : q, p < q ? q : p);
+    const double *jk = I.jk1 + (int64_t)(p * n + q) * n;
+    const double *jo = I.j1 + (int64_t)(p * n + q) * n;
+    double v = __ldg(&I.h[p * n + q]);
+#pragma unroll
+    for (int k = 0; k < W; k++) {
+        uint64_t m = common.w[k];
+        while (m) {
+            int b = __ffsll((long long)m) - 1;
+            m &= m - 1;
+            v += __ldg(&jk[64 * k + b]);
+        }
+        uint64_t o = other.w[k];
+        while (o) {
+            int b = __ffsll((long long)o) - 1;
+            o &= o - 1;
+            v += __ldg(&jo[64 * k + b]);
+        }
+    }
+    return flip_sign(v, neg);
+}
+
+// same-spin double: holes q1 < q2 in sj, particles p1 < p2 in si
+template <int W>
+__device__ __forceinline__ double same_double(const DevInts &I, const Str<W> &si, const Str<W> &sj) {
+    Str<W> pm, qm;
+#pragma unroll
+    for (int k = 0; k < W; k++) {
+        uint64_t d = si.w[k] ^ sj.w[k];
+        pm.w[k] = si.w[k] & d;
+        qm.w[k] = sj.w[k] & d;
+    }
+    int p1 = lowest_bit<W>(pm); clear_bit<W>(pm, p1); int p2 = lowest_bit<W>(pm);
+    int q1 = lowest_bit<W>(qm); clear_bit<W>(qm, q1); int q2 = lowest_bit<W>(qm);
+    int neg = bits_between<W>(sj, p1 < q1 ? p1 : q1, p1 < q1 ? q1 : p1);
+    Str<W> x = sj;
+    flip_bit<W>(x, q1);
+    flip_bit<W>(x, p1);
+    neg += bits_between<W>(x, p2 < q2 ? p2 : q2, p2 < q2 ? q2 : p2);
+    return flip_sign(eri_get(I, p1, q1, p2, q2) - eri_get(I, p1, q2, p2, q1), neg);
+}
+
+// one-electron move inside a string: particle p (in si only), hole q (in sj
+// only), pair index of (p, q) and the parity of sj's electrons between them
+template <int W>
+__device__ __forceinline__ void move_info(const Str<W> &si, const Str<W> &sj, int &pq, int &neg) {
+    Str<W> pi, qj;
+#pragma unroll
+    for (int k = 0; k < W; k++) {
+        uint64_t d = si.w[k] ^ sj.w[k];
+        pi.w[k] = si.w[k] & d;
+        qj.w[k] = sj.w[k] & d;
+    }
+    const int p = lowest_bit<W>(pi), q = lowest_bit<W>(qj);
+    pq = pair_idx(p, q);
+    neg = bits_between<W>(sj, p < q ? p : q, p < q ? q : p);
+}
+
+__device__ __forceinline__ double eri_pairs(const DevInts &I, int pq, int rs) {
+    int hi = pq > rs ? pq : rs, lo = pq > rs ? rs : pq;
+    return __ldg(&I.eri[(int64_t)hi * (hi + 1) / 2 + lo]);
+}
+
+// H_ij for a queued pair.  si / other: the row's string of the spin that
+// differs and of the spin that does not (for an opposite-spin double: the
+// row's beta and alpha strings); sj: D_j's string of the differing spin.
+// ctx & 1 marks an opposite-spin double whose alpha part (pair index ctx >> 2,
+// sign bit (ctx >> 1) & 1) was computed once for the whole candidate group.
+template <int W>
+__device__ __forceinline__ double eval_pair(const DevInts &I, const Str<W> &si, const Str<W> &other,
+                                            const Str<W> &sj, int ctx) {
+    if (ctx & 1) {
+        int pq_b, neg_b;
+        move_info<W>(si, sj, pq_b, neg_b);
+        return flip_sign(eri_pairs(I, ctx >> 2, pq_b), ((ctx >> 1) & 1) + neg_b);
+    }
+    return xor_popc<W>(si, sj) == 2 ? single_exc<W>(I, si, sj, other) : same_double<W>(I, si, sj);
+}
+
+// ---------------------------------------------------------------- per-row state
+
+template <int W>
+struct WarpQueue {
+    int32_t j[ENUM_QCAP];
+    int32_t ctx[ENUM_QCAP];
+    uint64_t s[ENUM_QCAP * W];
+};
+
+template <int MODE, int K>
+struct RowAcc {
+    int64_t found = 0;
+    int64_t pos = 0;
+    int qn = 0;
+    double acc[K > 0 ? K : 1];
+};
+
+// evaluate the first `cnt` (<= 32) queued pairs, one per lane, and apply the action
+template <int W, int MODE, int K>
+__device__ __forceinline__ void flush(RowAcc<MODE, K> &R, const EnumArgs &A, const DevInts &I, WarpQueue<W> &Q,
+                                      const Str<W> &si, const Str<W> &other, int cnt) {
+    const int lane = threadIdx.x & 31;
+    if (lane < cnt) {
+        Str<W> sj;
+#pragma unroll
+        for (int k = 0; k < W; k++) sj.w[k] = Q.s[lane * W + k];
+        const int32_t j = Q.j[lane];
+        const double v = eval_pair<W>(I, si, other, sj, Q.ctx[lane]);
+        if (MODE == ENUM_FILL) {
+            A.col[R.pos + lane] = j;
+            A.val[R.pos + lane] = v;
+        } else if (MODE == ENUM_SIGMA) {
+            if (K == 2) {
+                const double2 c2 = __ldg(reinterpret_cast<const double2 *>(A.x) + j);
+                R.acc[0] = fma(v, c2.x, R.acc[0]);
+                R.acc[K - 1] = fma(v, c2.y, R.acc[K - 1]);
+            } else {
+#pragma unroll
+                for (int q = 0; q < K; q++) R.acc[q] = fma(v, __ldg(&A.x[(int64_t)j * K + q]), R.acc[q]);
+            }
+        }
+    }
+    if (MODE == ENUM_FILL) R.pos += cnt;
+}
+
+// Record this round's matches: count them, or queue them and evaluate full
+// rounds of 32.
+template <int W, int MODE, int K>
+__device__ __forceinline__ void emit(RowAcc<MODE, K> &R, const EnumArgs &A, const DevInts &I, WarpQueue<W> &Q,
+                                     const Str<W> &si, const Str<W> &other, bool match, int32_t j, const Str<W> &sj,
+                                     int ctx) {
+    const int lane = threadIdx.x & 31;
+    const unsigned mask = __ballot_sync(0xffffffffu, match);
+    const int nm = __popc(mask);
+    R.found += nm;
+    if (MODE == ENUM_COUNT || nm == 0) return;
+    if (match) {
+        const int slot = R.qn + __popc(mask & ((1u << lane) - 1u));
+        Q.j[slot] = j;
+        Q.ctx[slot] = ctx;
+#pragma unroll
+        for (int k = 0; k < W; k++) Q.s[slot * W + k] = sj.w[k];
+    }
+    R.qn += nm;
+    __syncwarp();
+    if (R.qn >= 32) {
+        flush<W, MODE, K>(R, A, I, Q, si, other, 32);
+        __syncwarp();
+        const int rest = R.qn - 32;
+        if (lane < rest) {
+            Q.j[lane] = Q.j[32 + lane];
+            Q.ctx[lane] = Q.ctx[32 + lane];
+#pragma unroll
+            for (int k = 0; k < W; k++) Q.s[lane * W + k] = Q.s[(32 + lane) * W + k];
+        }
+        R.qn = rest;
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------- tile staging
+
+template <int W>
+struct Tile {
+    uint64_t str[ENUM_TILE * W];
+    int32_t det[ENUM_TILE];
+};
+
+template <int W, bool NEED_DET>
+__device__ __forceinline__ void stage(Tile<W> &T, const uint64_t *__restrict__ mstr, const int32_t *__restrict__ mdet,
+                                      int64_t start, int cnt) {
+    for (int e = threadIdx.x; e < cnt * W; e += ENUM_THREADS) T.str[e] = __ldg(&mstr[start * W + e]);
+    if (NEED_DET)
+        for (int e = threadIdx.x; e < cnt; e += ENUM_THREADS) T.det[e] = __ldg(&mdet[start + e]);
+}
+
+template <int W>
+__device__ __forceinline__ Str<W> tile_str(const Tile<W> &T, int e) {
+    Str<W> s;
+#pragma unroll
+    for (int k = 0; k < W; k++) s.w[k] = T.str[e * W + k];
+    return s;
+}
+
+template <int MODE, int K>
+__device__ __forceinline__ void row_begin(RowAcc<MODE, K> &R, const EnumArgs &A, int64_t i, bool valid) {
+    R.found = 0;
+    R.qn = 0;
+#pragma unroll
+    for (int q = 0; q < (K > 0 ? K : 1); q++) R.acc[q] = 0.0;
+    if (MODE == ENUM_FILL && valid) R.pos = A.rowptr[i] + (A.part_off ? A.part_off[i] : 0);
+}
+
+template <int W, int MODE, int K>
+__device__ __forceinline__ void row_end(RowAcc<MODE, K> &R, const EnumArgs &A, const DevInts &I, WarpQueue<W> &Q,
+                                        const Str<W> &si, const Str<W> &other, int64_t i, bool valid) {
+    const int lane = threadIdx.x & 31;
+    if (MODE != ENUM_COUNT && R.qn > 0) {
+        flush<W, MODE, K>(R, A, I, Q, si, other, R.qn);
+        R.qn = 0;
+        __syncwarp();
+    }
+    if (MODE == ENUM_SIGMA) {
+#pragma unroll
+        for (int q = 0; q < K; q++) {
+#pragma unroll
+            for (int o = 16; o >= 1; o >>= 1) R.acc[q] += __shfl_xor_sync(0xffffffffu, R.acc[q], o);
+        }
+        if (valid && lane == 0) {
+#pragma unroll
+            for (int q = 0; q < K; q++) {
+                const int64_t xi = i * K + q;
+                if (A.accumulate) A.y[xi] += R.acc[q];
+                else A.y[xi] = fma(A.diag[i], A.x[xi], R.acc[q]);
+            }
+        }
+    } else if (MODE == ENUM_COUNT) {
+        if (valid && lane == 0) A.cnt[i] = R.found;
+    }
+}
+
+// ---------------------------------------------------------------- kernels
+
+// Rows grouped by alpha string: same-spin beta excitations (candidates in the
+// row's own alpha group) and opposite-spin doubles (candidates in the alpha
+// groups of the alpha singles of the row's alpha string).
+template <int W, int MODE, int K>
+__global__ void __launch_bounds__(ENUM_THREADS) k_enum_alpha(EnumArgs A, DevInts I) {
+    __shared__ Tile<W> T;
+    __shared__ WarpQueue<W> Qs[ENUM_NW];
+    __shared__ int item_sh;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    WarpQueue<W> &Q = Qs[warp];
+    constexpr bool NEED_DET = MODE != ENUM_COUNT;
+    unsigned long long cand_local = 0;
+    while (true) {
+        if (threadIdx.x == 0) item_sh = atomicAdd(A.work_counter, 1);
+        __syncthreads();
+        const int64_t item = item_sh;
+        __syncthreads();
+        if (item >= A.n_items) break;
+        const int a = A.item_group[item];
+        const int64_t g_beg = A.ga_off[a], g_len = A.ga_off[a + 1] - g_beg;
+        const int64_t r = A.item_first[item] + warp;            // this warp's member
+        const bool valid = r < g_len;
+        const int64_t i = valid ? A.ga_det[g_beg + r] : 0;
+        const Str<W> Ai = load_str<W>(A.astr, a);
+        const Str<W> Bi = valid ? load_str<W>(A.ga_str, g_beg + r) : Str<W>{};
+        RowAcc<MODE, K> R;
+        row_begin(R, A, i, valid);
+        // same-spin beta: candidates with the same alpha string
+        for (int64_t t0 = 0; t0 < g_len; t0 += ENUM_TILE) {
+            const int cnt = (int)min((int64_t)ENUM_TILE, g_len - t0);
+            stage<W, NEED_DET>(T, A.ga_str, A.ga_det, g_beg + t0, cnt);
+            __syncthreads();
+            if (valid) {
+                cand_local += lane == 0 ? cnt : 0;
+                for (int b0 = 0; b0 < cnt; b0 += 32) {
+                    const int e = b0 + lane;
+                    bool match = false;
+                    Str<W> Bj{};
+                    if (e < cnt) {
+                        Bj = tile_str<W>(T, e);
+                        const int d = xor_popc<W>(Bi, Bj);
+                        match = (d == 2) | (d == 4);
+                    }
+                    emit<W, MODE, K>(R, A, I, Q, Bi, Ai, match, match && NEED_DET ? T.det[e] : 0, Bj, 0);
+                }
+            }
+            __syncthreads();
+        }
+        // opposite-spin doubles: candidates in the groups of the alpha singles of a
+        const int64_t s_beg = A.as_off[a], s_end = A.as_off[a + 1];
+        for (int64_t s = s_beg; s < s_end; s++) {
+            const int k = A.as_idx[s];
+            const int64_t k_beg = A.ga_off[k], k_len = A.ga_off[k + 1] - k_beg;
+            int ctx = 1;
+            if (MODE != ENUM_COUNT) {
+                int pq_a, neg_a;
+                move_info<W>(Ai, load_str<W>(A.astr, k), pq_a, neg_a);
+                ctx = (pq_a << 2) | ((neg_a & 1) << 1) | 1;
+            }
+            for (int64_t t0 = 0; t0 < k_len; t0 += ENUM_TILE) {
+                const int cnt = (int)min((int64_t)ENUM_TILE, k_len - t0);
+                stage<W, NEED_DET>(T, A.ga_str, A.ga_det, k_beg + t0, cnt);
+                __syncthreads();
+                if (valid) {
+                    cand_local += lane == 0 ? cnt : 0;
+                    for (int b0 = 0; b0 < cnt; b0 += 32) {
+                        const int e = b0 + lane;
+                        bool match = false;
+                        Str<W> Bj{};
+                        if (e < cnt) {
+                            Bj = tile_str<W>(T, e);
+                            match = xor_popc<W>(Bi, Bj) == 2;
+                        }
+                        emit<W, MODE, K>(R, A, I, Q, Bi, Ai, match, match && NEED_DET ? T.det[e] : 0, Bj, ctx);
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        row_end<W, MODE, K>(R, A, I, Q, Bi, Ai, i, valid);
+    }
+    if (MODE == ENUM_COUNT && lane == 0 && cand_local) atomicAdd(A.cand, cand_local);
+}
+
+// Rows grouped by beta string: same-spin alpha excitations (candidates with
+// the same beta string).
+template <int W, int MODE, int K>
+__global__ void __launch_bounds__(ENUM_THREADS) k_enum_beta(EnumArgs A, DevInts I) {
+    __shared__ Tile<W> T;
+    __shared__ WarpQueue<W> Qs[ENUM_NW];
+    __shared__ int item_sh;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    WarpQueue<W> &Q = Qs[warp];
+    constexpr bool NEED_DET = MODE != ENUM_COUNT;
+    unsigned long long cand_local = 0;
+    while (true) {
+        if (threadIdx.x == 0) item_sh = atomicAdd(A.work_counter, 1);
+        __syncthreads();
+        const int64_t item = item_sh;
+        __syncthreads();
+        if (item >= A.n_items) break;
+        const int b = A.item_group[item];
+        const int64_t g_beg = A.gb_off[b], g_len = A.gb_off[b + 1] - g_beg;
+        const int64_t r = A.item_first[item] + warp;
+        const bool valid = r < g_len;
+        const int64_t i = valid ? A.gb_det[g_beg + r] : 0;
+        const Str<W> Bi = load_str<W>(A.bstr, b);
+        const Str<W> Ai = valid ? load_str<W>(A.gb_str, g_beg + r) : Str<W>{};
+        RowAcc<MODE, K> R;
+        row_begin(R, A, i, valid);
+        for (int64_t t0 = 0; t0 < g_len; t0 += ENUM_TILE) {
+            const int cnt = (int)min((int64_t)ENUM_TILE, g_len - t0);
+            stage<W, NEED_DET>(T, A.gb_str, A.gb_det, g_beg + t0, cnt);
+            __syncthreads();
+            if (valid) {
+                cand_local += lane == 0 ? cnt : 0;
+                for (int b0 = 0; b0 < cnt; b0 += 32) {
+                    const int e = b0 + lane;
+                    bool match = false;
+                    Str<W> Aj{};
+                    if (e < cnt) {
+                        Aj = tile_str<W>(T, e);
+                        const int d = xor_popc<W>(Ai, Aj);
+                        match = (d == 2) | (d == 4);
+                    }
+                    emit<W, MODE, K>(R, A, I, Q, Ai, Bi, match, match && NEED_DET ? T.det[e] : 0, Aj, 0);
+                }
+            }
+            __syncthreads();
+        }
+        row_end<W, MODE, K>(R, A, I, Q, Ai, Bi, i, valid);
+    }
+    if (MODE == ENUM_COUNT && lane == 0 && cand_local) atomicAdd(A.cand, cand_local);
+}
+
+// work items: one per chunk of ENUM_NW members of each group
+static __global__ void k_items_count(const int64_t *__restrict__ off, int64_t n_groups, int64_t *__restrict__ cnt) {
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n_groups; g += (int64_t)gridDim.x * blockDim.x)
+        cnt[g] = (off[g + 1] - off[g] + ENUM_NW - 1) / ENUM_NW;
+}
+
+static __global__ void k_items_fill(const int64_t *__restrict__ off, const int64_t *__restrict__ start, int64_t n_groups,
+                                    int32_t *__restrict__ item_group, int32_t *__restrict__ item_first) {
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n_groups; g += (int64_t)gridDim.x * blockDim.x) {
+        int64_t c = (off[g + 1] - off[g] + ENUM_NW - 1) / ENUM_NW;
+        for (int64_t t = 0; t < c; t++) {
+            item_group[start[g] + t] = (int32_t)g;
+            item_first[start[g] + t] = (int32_t)(t * ENUM_NW);
+        }
+    }
+}
+
+}  // namespace shci

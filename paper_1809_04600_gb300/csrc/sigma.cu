@@ -8,7 +8,7 @@
 #include <algorithm>
 #include <atomic>
 
-#include "context.cuh"
+#include "enum_launch.cuh"
 
 
 namespace shci {
@@ -108,9 +108,43 @@ void sigma(shci_ctx *c, int k, const double *x, double *y, bool inter) {
     }
 }
 
+// On-the-fly sigma (the "direct" method the paper proposes for larger spaces,
+// Sec. VI): every product re-enumerates the connected pairs with the helper
+// lists and recomputes H_ij, so H is never stored.  Pass 1 (rows grouped by
+// alpha string) writes y = diag * x + same-spin-beta and opposite-spin terms;
+// pass 2 (rows grouped by beta string) adds the same-spin-alpha terms.
+template <int W, int K>
+static void otf_k(shci_ctx *c, const double *x, double *y) {
+    EnumArgs A = enum_args(c);
+    A.x = x;
+    A.y = y;
+    A.diag = c->diag.p;
+    DevInts I = dev_ints(c);
+    A.accumulate = 0;
+    launch_enum<W, ENUM_SIGMA, K>(c, A, I, true);
+    A.accumulate = 1;
+    launch_enum<W, ENUM_SIGMA, K>(c, A, I, false);
+}
+
+template <int W>
+static void otf_w(shci_ctx *c, int k, const double *x, double *y) {
+    switch (k) {
+        case 1: otf_k<W, 1>(c, x, y); break;
+        case 2: otf_k<W, 2>(c, x, y); break;
+        case 3: otf_k<W, 3>(c, x, y); break;
+        case 4: otf_k<W, 4>(c, x, y); break;
+        case 5: otf_k<W, 5>(c, x, y); break;
+        case 6: otf_k<W, 6>(c, x, y); break;
+        case 7: otf_k<W, 7>(c, x, y); break;
+        case 8: otf_k<W, 8>(c, x, y); break;
+        default: throw ShciError{SHCI_ERR_INVALID, "k must be in [1, 8]"};
+    }
+}
+
 void sigma_otf(shci_ctx *c, int k, const double *x, double *y, bool inter) {
-    (void)k; (void)x; (void)y; (void)inter;
-    throw ShciError{SHCI_ERR_STATE, "on-the-fly sigma is not available in this build"};
+    if (!inter && k != 1) throw ShciError{SHCI_ERR_INVALID, "on-the-fly sigma takes interleaved vectors"};
+    if (c->W == 1) otf_w<1>(c, k, x, y);
+    else otf_w<2>(c, k, x, y);
 }
 
 }  // namespace shci

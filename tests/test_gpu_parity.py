@@ -93,6 +93,34 @@ def test_selected_space_pairs_values(P, oracle_mod, name, n_det):
     B.close()
 
 
+@pytest.mark.parametrize("name,n_det", [("fci_10o_4a4b", None), ("sel_24o_6a6b_1m", 20000),
+                                        ("sel_20o_5a5b_1m", 4099), ("sel_76o_14a14b_50m", 5003)])
+def test_on_the_fly_sigma_and_energy(P, oracle_mod, name, n_det):
+    """The direct (on-the-fly) product matches the oracle without storing H."""
+    cfg, h, eri, ec, dets = G.system(name, n_det)
+    O = oracle_mod.System(h, eri, ec)
+    ii, jj = oracle_mod.pairs_allpairs(dets)
+    B = G.Built(P, h, eri, ec, dets, cfg.n_alpha, cfg.n_beta, mode=P.SHCI_ON_THE_FLY)
+    assert B.stats()["mode"] == P.SHCI_ON_THE_FLY
+    assert B.nnz == ii.size
+    with pytest.raises(P.ShciError):
+        B.pairs()                                  # nothing stored
+    n = dets.shape[0]
+    c = S.random_vectors(n, 3, 13)
+    ref = oracle_mod.sigma_pairs(n, ii, jj, O.hij_list(dets, ii, jj), O.hdiag(dets), c)
+    rows = np.unique(np.linspace(0, n - 1, 64).astype(np.int64))
+    scale = G.row_scale(O, dets, c, rows)
+    for k in (1, 2, 3):
+        got = B.sigma(c[:k])
+        assert np.all(np.abs(got[:, rows] - ref[:k, rows]) <= SIGMA_REL * scale[:k] + 1e-300)
+        assert np.max(np.abs(got - ref[:k])) < 1e-10
+    if n <= 20000:
+        e_ref, _ = O.lowest_eigenpairs(dets, 1, tol=1e-12)
+        e, vecs, it = B.davidson(1, tol=1e-10)
+        assert abs(e[0] - e_ref[0]) < E_TOL
+    B.close()
+
+
 def test_selected_space_two_roots(P, oracle_mod):
     cfg, h, eri, ec, dets = G.system("sel_24o_6a6b_1m", 20000)
     O = oracle_mod.System(h, eri, ec)
