@@ -151,6 +151,22 @@ int shci_sigma_noalloc(shci_ctx *ctx, int k, const double *c, double *sigma);
 int shci_davidson(shci_ctx *ctx, int k_roots, double tol, int max_iter, const double *guess,
                   double *energies, double *vecs, int mem_space, int *iters_out);
 
+/* Adjoint of a variational eigenvalue (no counterpart in the paper, which
+ * has no derivatives): for a normalised real eigenvector c of H on V,
+ * E = c^T H c and, by Hellmann-Feynman, dE/dX = c^T (dH/dX) c.  Writes
+ *   dE_dh[p * n_orb + q]   = grad_out_scale * gamma_pq
+ *                            (gamma_pq = sum_s <a+_ps a_qs>; every entry of h
+ *                            is treated as an independent variable), and
+ *   dE_deri_packed[slot]   = grad_out_scale * 1/2 * sum of Gamma_pqrs over the
+ *                            (p,q,r,s) that the packed slot stores
+ *                            (Gamma_pqrs = sum_{s,t} <a+_ps a+_rt a_st a_qs>).
+ * The pairs of V are enumerated again and H_ij recomputed, never stored.
+ * c: [n_det]; outputs n_orb^2 and npair(npair+1)/2 doubles; all in mem_space.
+ * Needs a completed shci_build_connectivity (either mode).  The determinant
+ * set V is held fixed (no reselection). */
+int shci_energy_backward(shci_ctx *ctx, const double *c, double grad_out_scale, double *dE_dh,
+                         double *dE_deri_packed, int mem_space);
+
 /* Library-side measurements of the last build / Davidson run (for reports). */
 typedef struct {
     int64_t n_det;

@@ -357,6 +357,34 @@ def rdm2_full(dets, c, n):
     return rdm2_entries(dets, c, n, idx).reshape(n, n, n, n)
 
 
+def slot_members(n):
+    """For every packed slot, the list of (p, q, r, s) index tuples that map to it."""
+    members = {}
+    for p in range(n):
+        for q in range(n):
+            for r in range(n):
+                for s in range(n):
+                    a = max(p, q) * (max(p, q) + 1) // 2 + min(p, q)
+                    b = max(r, s) * (max(r, s) + 1) // 2 + min(r, s)
+                    slot = max(a, b) * (max(a, b) + 1) // 2 + min(a, b)
+                    members.setdefault(slot, []).append((p, q, r, s))
+    return members
+
+
+def packed_gradient_entries(dets, c, n_orb, slots, members=None):
+    """dE/d(packed slot) = 1/2 sum_{(p,q,r,s) -> slot} Gamma_pqrs for the listed slots."""
+    members = members or slot_members(n_orb)
+    idx, owner = [], []
+    for t, slot in enumerate(slots):
+        for tup in members[int(slot)]:
+            idx.append(tup)
+            owner.append(t)
+    vals = rdm2_entries(dets, c, n_orb, np.array(idx, dtype=np.int32))
+    out = np.zeros(len(slots))
+    np.add.at(out, np.array(owner), 0.5 * vals)
+    return out
+
+
 def fold_rdm2_to_packed(G, n):
     """dE/d(packed slot) = 1/2 * sum of Gamma_pqrs over every distinct (p,q,r,s) that the
     slot stores (its 8-fold symmetry orbit)."""

@@ -10,4 +10,13 @@ from .binding import (  # noqa: F401
     load_library, shci_build_connectivity, shci_create, shci_davidson, shci_destroy, shci_get_diag,
     shci_get_pairs, shci_get_row, shci_get_stats, shci_last_error, shci_load_integrals, shci_set_timing, shci_sigma,
 )
+from .binding import shci_energy_backward, shci_sigma_noalloc  # noqa: F401
 from .build_lib import build  # noqa: F401
+
+
+def __getattr__(name):
+    # the autograd wrapper needs torch; import it on first use only
+    if name == "Energy":
+        from .autograd import Energy
+        return Energy
+    raise AttributeError(name)

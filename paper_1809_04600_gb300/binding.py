@@ -35,7 +35,7 @@ _STATUS = {1: "INVALID", 2: "OOM", 3: "CUDA", 4: "NOT_CONVERGED", 5: "TIMEOUT", 
 # every symbol include/shci.h declares (checked by the tests)
 EXPORTED = [
     "shci_create", "shci_destroy", "shci_last_error", "shci_load_integrals", "shci_build_connectivity",
-    "shci_get_diag", "shci_get_pairs", "shci_get_row", "shci_sigma", "shci_sigma_noalloc", "shci_davidson", "shci_get_stats", "shci_set_timing",
+    "shci_get_diag", "shci_get_pairs", "shci_get_row", "shci_sigma", "shci_sigma_noalloc", "shci_energy_backward", "shci_davidson", "shci_get_stats", "shci_set_timing",
 ]
 
 
@@ -78,6 +78,7 @@ def load_library(path: str = LIB_PATH):
         "shci_get_row": (i32, [vp, i64, i64, vp, vp, ctypes.POINTER(i64)]),
         "shci_sigma": (i32, [vp, i32, vp, vp, i32]),
         "shci_sigma_noalloc": (i32, [vp, i32, vp, vp]),
+        "shci_energy_backward": (i32, [vp, vp, f64, vp, vp, i32]),
         "shci_davidson": (i32, [vp, i32, f64, i32, vp, vp, vp, i32, ctypes.POINTER(i32)]),
         "shci_get_stats": (i32, [vp, ctypes.POINTER(shci_stats_t)]),
         "shci_set_timing": (i32, [vp, i32]),
@@ -226,6 +227,17 @@ def shci_davidson(ctx, k_roots, tol=1e-10, max_iter=200, guess=None, vecs=None, 
     if check and rc not in (SHCI_OK,):
         _check(ctx, rc)
     return e, it.value, rc
+
+
+def shci_energy_backward(ctx, c, grad_out_scale, dE_dh, dE_deri_packed):
+    """dE/dh and packed dE/d(pq|rs) for the normalised root c (Hellmann-Feynman)."""
+    pc, mc, kc = _ptr(c, np.float64)
+    ph, mh, kh = _ptr(dE_dh, np.float64)
+    pe, me, ke = _ptr(dE_deri_packed, np.float64)
+    if not (mc == mh == me):
+        raise ValueError("c and the gradient buffers must live in the same memory space")
+    _check(ctx, load_library().shci_energy_backward(ctx, pc, float(grad_out_scale), ph, pe, mc))
+    return dE_dh, dE_deri_packed
 
 
 def shci_get_stats(ctx) -> dict:

@@ -27,7 +27,9 @@ constexpr int ENUM_THREADS = 32 * ENUM_NW;
 constexpr int ENUM_TILE = 1024;             // candidates staged per tile
 constexpr int ENUM_QCAP = 64;               // per-warp queue of found pairs
 
-enum { ENUM_COUNT = 0, ENUM_FILL = 1, ENUM_SIGMA = 2 };
+enum { ENUM_COUNT = 0, ENUM_FILL = 1, ENUM_SIGMA = 2, ENUM_GRAD = 3 };
+
+constexpr int GRAD_REPLICAS = 32;           // gradient copies that spread the atomics
 
 struct EnumArgs {
     const uint64_t *dets;
@@ -54,6 +56,10 @@ struct EnumArgs {
     double *y;                              // [n][K]
     const double *diag;
     int accumulate;                         // 0: y = diag x + part, 1: y += part
+    // gradient (x = the root c, [n])
+    double *gdh;                            // [GRAD_REPLICAS][n_orb * n_orb]
+    double *geri;                           // [GRAD_REPLICAS][packed length]
+    int64_t geri_len;
 };
 
 // ---------------------------------------------------------------- matrix element pieces
@@ -152,6 +158,76 @@ __device__ __forceinline__ double eval_pair(const DevInts &I, const Str<W> &si, 
     return xor_popc<W>(si, sj) == 2 ? single_exc<W>(I, si, sj, other) : same_double<W>(I, si, sj);
 }
 
+__device__ __forceinline__ int64_t eri_slot(int p, int q, int r, int s) {
+    int a = pair_idx(p, q), b = pair_idx(r, s);
+    int hi = a > b ? a : b, lo = a > b ? b : a;
+    return (int64_t)hi * (hi + 1) / 2 + lo;
+}
+
+// Adjoint of one connected pair i < j: add c_i c_j dH_ij/d(integral) for
+// both orders (i, j) and (j, i).  h entries are independent, so H_ij's h_pq
+// and H_ji's h_qp go to different slots (weight w = c_i c_j each); a packed
+// two-electron slot is shared by both orders (weight w2 = 2 c_i c_j).
+template <int W>
+__device__ __forceinline__ void grad_pair(const DevInts &I, double *__restrict__ gdh, double *__restrict__ geri,
+                                          const Str<W> &si, const Str<W> &other, const Str<W> &sj, int ctx,
+                                          double w) {
+    const double w2 = 2.0 * w;
+    if (ctx & 1) {
+        int pq_b, neg_b;
+        move_info<W>(si, sj, pq_b, neg_b);
+        const int pq_a = ctx >> 2;
+        const int hi = pq_a > pq_b ? pq_a : pq_b, lo = pq_a > pq_b ? pq_b : pq_a;
+        atomicAdd(&geri[(int64_t)hi * (hi + 1) / 2 + lo], flip_sign(w2, ((ctx >> 1) & 1) + neg_b));
+        return;
+    }
+    const int n = I.n;
+    Str<W> pm, qm;
+#pragma unroll
+    for (int k = 0; k < W; k++) {
+        uint64_t d = si.w[k] ^ sj.w[k];
+        pm.w[k] = si.w[k] & d;
+        qm.w[k] = sj.w[k] & d;
+    }
+    if (xor_popc<W>(si, sj) == 2) {
+        const int p = lowest_bit<W>(pm), q = lowest_bit<W>(qm);
+        Str<W> common;
+#pragma unroll
+        for (int k = 0; k < W; k++) common.w[k] = si.w[k] & sj.w[k];
+        const int neg = bits_between<W>(common, p < q ? p : q, p < q ? q : p);
+        const double sw = flip_sign(w, neg), sw2 = flip_sign(w2, neg);
+        atomicAdd(&gdh[p * n + q], sw);
+        atomicAdd(&gdh[q * n + p], sw);
+#pragma unroll
+        for (int k = 0; k < W; k++) {
+            uint64_t m = common.w[k];
+            while (m) {
+                const int b = 64 * k + __ffsll((long long)m) - 1;
+                m &= m - 1;
+                atomicAdd(&geri[eri_slot(p, q, b, b)], sw2);
+                atomicAdd(&geri[eri_slot(p, b, b, q)], -sw2);
+            }
+            uint64_t o = other.w[k];
+            while (o) {
+                const int b = 64 * k + __ffsll((long long)o) - 1;
+                o &= o - 1;
+                atomicAdd(&geri[eri_slot(p, q, b, b)], sw2);
+            }
+        }
+        return;
+    }
+    int p1 = lowest_bit<W>(pm); clear_bit<W>(pm, p1); int p2 = lowest_bit<W>(pm);
+    int q1 = lowest_bit<W>(qm); clear_bit<W>(qm, q1); int q2 = lowest_bit<W>(qm);
+    int neg = bits_between<W>(sj, p1 < q1 ? p1 : q1, p1 < q1 ? q1 : p1);
+    Str<W> x = sj;
+    flip_bit<W>(x, q1);
+    flip_bit<W>(x, p1);
+    neg += bits_between<W>(x, p2 < q2 ? p2 : q2, p2 < q2 ? q2 : p2);
+    const double sw2 = flip_sign(w2, neg);
+    atomicAdd(&geri[eri_slot(p1, q1, p2, q2)], sw2);
+    atomicAdd(&geri[eri_slot(p1, q2, p2, q1)], -sw2);
+}
+
 // ---------------------------------------------------------------- per-row state
 
 template <int W>
@@ -166,6 +242,8 @@ struct RowAcc {
     int64_t found = 0;
     int64_t pos = 0;
     int qn = 0;
+    int64_t i = 0;          // the row's determinant (gradient mode)
+    double ci = 0.0;        // its coefficient (gradient mode)
     double acc[K > 0 ? K : 1];
 };
 
@@ -174,6 +252,20 @@ template <int W, int MODE, int K>
 __device__ __forceinline__ void flush(RowAcc<MODE, K> &R, const EnumArgs &A, const DevInts &I, WarpQueue<W> &Q,
                                       const Str<W> &si, const Str<W> &other, int cnt) {
     const int lane = threadIdx.x & 31;
+    if (MODE == ENUM_GRAD) {
+        if (lane < cnt) {
+            const int32_t j = Q.j[lane];
+            if ((int64_t)j > R.i) {
+                Str<W> sj;
+#pragma unroll
+                for (int k = 0; k < W; k++) sj.w[k] = Q.s[lane * W + k];
+                const int rep = blockIdx.x % GRAD_REPLICAS;
+                grad_pair<W>(I, A.gdh + (int64_t)rep * I.n * I.n, A.geri + rep * A.geri_len, si, other, sj,
+                             Q.ctx[lane], R.ci * __ldg(&A.x[j]));
+            }
+        }
+        return;
+    }
     if (lane < cnt) {
         Str<W> sj;
 #pragma unroll
@@ -260,9 +352,11 @@ template <int MODE, int K>
 __device__ __forceinline__ void row_begin(RowAcc<MODE, K> &R, const EnumArgs &A, int64_t i, bool valid) {
     R.found = 0;
     R.qn = 0;
+    R.i = i;
 #pragma unroll
     for (int q = 0; q < (K > 0 ? K : 1); q++) R.acc[q] = 0.0;
     if (MODE == ENUM_FILL && valid) R.pos = A.rowptr[i] + (A.part_off ? A.part_off[i] : 0);
+    if (MODE == ENUM_GRAD) R.ci = valid ? A.x[i] : 0.0;
 }
 
 template <int W, int MODE, int K>
