@@ -167,6 +167,52 @@ int shci_davidson(shci_ctx *ctx, int k_roots, double tol, int max_iter, const do
 int shci_energy_backward(shci_ctx *ctx, const double *c, double grad_out_scale, double *dE_dh,
                          double *dE_deri_packed, int mem_space);
 
+/* ---------------------------------------------------------------- batches
+ * Many independent systems (each with its own integrals and determinant
+ * list) solved together (no counterpart in the paper, which treats one
+ * system at a time).  shci_batch_create builds every system's helper lists,
+ * diagonal and, while the total fits `stored_budget_bytes` (negative: no
+ * limit beyond free memory), its stored H -- the rest use the on-the-fly
+ * product.  shci_batch_davidson then runs the Davidson iterations of all
+ * systems (up to 4 roots each; same stopping rule as shci_davidson) inside
+ * one persistent cooperative kernel launch captured in a CUDA graph: each
+ * phase of an iteration covers every active system, with grid-wide barriers
+ * between phases.  The first call also runs the library's autotuner (rows
+ * per stored-sigma work item, CTAs per SM) on a few iterations of the real
+ * kernel.  Systems are limited to n_orb <= 64.  The batch keeps using the
+ * creating context's stream; destroy the batch before the context. */
+typedef struct shci_batch shci_batch;
+
+typedef struct {
+    int n_orb, n_alpha, n_beta;
+    int64_t n_det;
+    double e_core;
+    const double *h;           /* n_orb * n_orb */
+    const double *eri_packed;  /* packed as for shci_load_integrals */
+    const uint64_t *dets;      /* [n_det][2] (W = 1) */
+} shci_system_desc;
+
+typedef struct {
+    int n_sys, n_stored, n_on_the_fly;
+    int64_t total_det, total_nnz_upper;
+    int tuned_rows_per_item, tuned_ctas_per_sm;
+    double tune_ms;            /* best time of the tuning trials (3 iterations) */
+    double solve_ms;           /* last shci_batch_davidson, device time */
+    int max_iters;             /* iterations of the slowest system */
+    int graph;                 /* 1 if the solve ran as a captured CUDA graph */
+    int grid_ctas;
+} shci_batch_stats_t;
+
+int shci_batch_create(shci_ctx *ctx, int n_sys, const shci_system_desc *systems, int mem_space,
+                      double stored_budget_bytes, shci_batch **out);
+/* energies: host [n_sys][k_roots]; iters, converged: host [n_sys] or NULL.
+ * SHCI_ERR_NOT_CONVERGED if a system hit max_iter (its estimates are still
+ * written); SHCI_ERR_TIMEOUT if the grid barrier gave up. */
+int shci_batch_davidson(shci_batch *b, int k_roots, double tol, int max_iter, double *energies, int *iters,
+                        int *converged);
+int shci_batch_get_stats(shci_batch *b, shci_batch_stats_t *out);
+void shci_batch_destroy(shci_batch *b);
+
 /* Library-side measurements of the last build / Davidson run (for reports). */
 typedef struct {
     int64_t n_det;

@@ -35,7 +35,8 @@ _STATUS = {1: "INVALID", 2: "OOM", 3: "CUDA", 4: "NOT_CONVERGED", 5: "TIMEOUT", 
 # every symbol include/shci.h declares (checked by the tests)
 EXPORTED = [
     "shci_create", "shci_destroy", "shci_last_error", "shci_load_integrals", "shci_build_connectivity",
-    "shci_get_diag", "shci_get_pairs", "shci_get_row", "shci_sigma", "shci_sigma_noalloc", "shci_energy_backward", "shci_davidson", "shci_get_stats", "shci_set_timing",
+    "shci_get_diag", "shci_get_pairs", "shci_get_row", "shci_sigma", "shci_sigma_noalloc", "shci_energy_backward",
+    "shci_batch_create", "shci_batch_davidson", "shci_batch_get_stats", "shci_batch_destroy", "shci_davidson", "shci_get_stats", "shci_set_timing",
 ]
 
 
@@ -52,6 +53,24 @@ class shci_stats_t(ctypes.Structure):
         ("build_ms", ctypes.c_double), ("sigma_ms_total", ctypes.c_double), ("sigma_launches", ctypes.c_int64),
         ("sigma_vectors", ctypes.c_int64), ("kernel_launches", ctypes.c_int64), ("davidson_iters", ctypes.c_int),
         ("mode", ctypes.c_int), ("n_words", ctypes.c_int),
+    ]
+
+
+class shci_system_desc(ctypes.Structure):
+    _fields_ = [
+        ("n_orb", ctypes.c_int), ("n_alpha", ctypes.c_int), ("n_beta", ctypes.c_int), ("n_det", ctypes.c_int64),
+        ("e_core", ctypes.c_double), ("h", ctypes.c_void_p), ("eri_packed", ctypes.c_void_p),
+        ("dets", ctypes.c_void_p),
+    ]
+
+
+class shci_batch_stats_t(ctypes.Structure):
+    _fields_ = [
+        ("n_sys", ctypes.c_int), ("n_stored", ctypes.c_int), ("n_on_the_fly", ctypes.c_int),
+        ("total_det", ctypes.c_int64), ("total_nnz_upper", ctypes.c_int64),
+        ("tuned_rows_per_item", ctypes.c_int), ("tuned_ctas_per_sm", ctypes.c_int),
+        ("tune_ms", ctypes.c_double), ("solve_ms", ctypes.c_double), ("max_iters", ctypes.c_int),
+        ("graph", ctypes.c_int), ("grid_ctas", ctypes.c_int),
     ]
 
 
@@ -79,6 +98,10 @@ def load_library(path: str = LIB_PATH):
         "shci_sigma": (i32, [vp, i32, vp, vp, i32]),
         "shci_sigma_noalloc": (i32, [vp, i32, vp, vp]),
         "shci_energy_backward": (i32, [vp, vp, f64, vp, vp, i32]),
+        "shci_batch_create": (i32, [vp, i32, ctypes.POINTER(shci_system_desc), i32, f64, ctypes.POINTER(vp)]),
+        "shci_batch_davidson": (i32, [vp, i32, f64, i32, vp, vp, vp]),
+        "shci_batch_get_stats": (i32, [vp, ctypes.POINTER(shci_batch_stats_t)]),
+        "shci_batch_destroy": (None, [vp]),
         "shci_davidson": (i32, [vp, i32, f64, i32, vp, vp, vp, i32, ctypes.POINTER(i32)]),
         "shci_get_stats": (i32, [vp, ctypes.POINTER(shci_stats_t)]),
         "shci_set_timing": (i32, [vp, i32]),
@@ -238,6 +261,53 @@ def shci_energy_backward(ctx, c, grad_out_scale, dE_dh, dE_deri_packed):
         raise ValueError("c and the gradient buffers must live in the same memory space")
     _check(ctx, load_library().shci_energy_backward(ctx, pc, float(grad_out_scale), ph, pe, mc))
     return dE_dh, dE_deri_packed
+
+
+def shci_batch_create(ctx, systems, stored_budget_bytes=-1.0):
+    """systems: list of dicts with n_orb, n_alpha, n_beta, h, eri, dets (and optional e_core);
+    arrays all numpy (host) or all torch CUDA tensors.  Returns the batch handle."""
+    lib = load_library()
+    arr = (shci_system_desc * len(systems))()
+    keep = []
+    mem = None
+    for s, d in enumerate(systems):
+        ph, m1, k1 = _ptr(d["h"], np.float64)
+        pe, m2, k2 = _ptr(d["eri"], np.float64)
+        pd, m3, k3 = _ptr(d["dets"], np.uint64)
+        keep += [k1, k2, k3]
+        if not (m1 == m2 == m3) or (mem is not None and m1 != mem):
+            raise ValueError("all batch arrays must live in the same memory space")
+        mem = m1
+        arr[s] = shci_system_desc(int(d["n_orb"]), int(d["n_alpha"]), int(d["n_beta"]), int(d["dets"].shape[0]),
+                                  float(d.get("e_core", 0.0)), ph, pe, pd)
+    out = ctypes.c_void_p()
+    _check(ctx, lib.shci_batch_create(ctx, len(systems), arr, mem, float(stored_budget_bytes), ctypes.byref(out)))
+    return out
+
+
+def shci_batch_davidson(ctx, batch, n_sys, k_roots, tol=1e-10, max_iter=400):
+    """(energies [n_sys, k], iters [n_sys], converged [n_sys], status)."""
+    lib = load_library()
+    e = np.empty((n_sys, k_roots), np.float64)
+    it = np.empty(n_sys, np.int32)
+    cv = np.empty(n_sys, np.int32)
+    rc = lib.shci_batch_davidson(batch, int(k_roots), float(tol), int(max_iter), e.ctypes.data, it.ctypes.data,
+                                 cv.ctypes.data)
+    if rc not in (SHCI_OK, SHCI_ERR_NOT_CONVERGED):
+        _check(ctx, rc)
+    return e, it, cv, rc
+
+
+def shci_batch_get_stats(batch) -> dict:
+    s = shci_batch_stats_t()
+    rc = load_library().shci_batch_get_stats(batch, ctypes.byref(s))
+    if rc != SHCI_OK:
+        raise ShciError(rc, "shci_batch_get_stats failed")
+    return {name: getattr(s, name) for name, _ in shci_batch_stats_t._fields_}
+
+
+def shci_batch_destroy(batch):
+    load_library().shci_batch_destroy(batch)
 
 
 def shci_get_stats(ctx) -> dict:

@@ -434,7 +434,9 @@ static void build_w(shci_ctx *c, int mode) {
         size_t free_b = 0, total_b = 0;
         CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
         double need = (double)nnz * 12.0;
-        mode = need < 0.8 * (double)free_b ? SHCI_STORED : SHCI_ON_THE_FLY;
+        double cap = 0.8 * (double)free_b;
+        if (c->stored_budget >= 0.0) cap = std::min(cap, c->stored_budget);
+        mode = need < cap ? SHCI_STORED : SHCI_ON_THE_FLY;
     }
     c->mode = mode;
     if (mode == SHCI_STORED) {

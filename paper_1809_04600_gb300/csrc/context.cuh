@@ -68,6 +68,10 @@ struct shci_ctx {
 
     DavidsonWork dw;
 
+    // SHCI_AUTO stores H only if it fits this many bytes (negative: no limit
+    // beyond the device's free memory)
+    double stored_budget = -1.0;
+
     // measurements
     bool timing = false;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;

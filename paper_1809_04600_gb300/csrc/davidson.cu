@@ -13,6 +13,7 @@
 #include <cmath>
 
 #include "context.cuh"
+#include "jacobi.cuh"
 
 namespace shci {
 
@@ -149,36 +150,7 @@ __global__ void __launch_bounds__(DV_THREADS) k_project(const double *__restrict
 __global__ void k_cholqr_coef(const double *__restrict__ S, int kb, const double *__restrict__ ref, double rel,
                               double *__restrict__ M, int *__restrict__ count) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double R[SHCI_MAX_K][SHCI_MAX_K];
-    double Mi[SHCI_MAX_K][SHCI_MAX_K];   // Mi[j][l]: coefficient of t_j in q_l
-    int acc[SHCI_MAX_K];
-    int na = 0;
-    for (int l = 0; l < kb; l++)
-        for (int j = 0; j < kb; j++) { R[j][l] = 0.0; Mi[j][l] = 0.0; }
-    for (int l = 0; l < kb; l++) {
-        // R[j][l] for accepted j < l
-        for (int x = 0; x < na; x++) {
-            int j = acc[x];
-            double s = S[j * kb + l];
-            for (int y = 0; y < x; y++) s -= R[acc[y]][j] * R[acc[y]][l];
-            R[j][l] = s / R[j][j];
-        }
-        double d = S[l * kb + l];
-        for (int x = 0; x < na; x++) d -= R[acc[x]][l] * R[acc[x]][l];
-        double r0 = ref ? ref[l] : S[l * kb + l];
-        if (!(d > rel * r0) || !(d > 1e-300)) continue;      // numerically dependent: drop
-        R[l][l] = sqrt(d);
-        // q_l = (t_l - sum_{j acc} R[j][l] q_j) / R[l][l]
-        for (int j = 0; j < kb; j++) {
-            double v = (j == l) ? 1.0 : 0.0;
-            for (int x = 0; x < na; x++) v -= R[acc[x]][l] * Mi[j][acc[x]];
-            Mi[j][l] = v / R[l][l];
-        }
-        acc[na++] = l;
-    }
-    for (int j = 0; j < kb; j++)
-        for (int x = 0; x < kb; x++) M[j * kb + x] = x < na ? Mi[j][acc[x]] : 0.0;
-    *count = na;
+    *count = cholqr_coef(S, kb, ref, rel, M);
 }
 
 // out[l'] = sum_j M[j * KB + l'] T[j] for l' < KB; slots l' >= *count are
@@ -304,147 +276,12 @@ __global__ void k_sum_partials(const double *__restrict__ partial, int nblk, int
 
 // ---------------------------------------------------------------- subspace eigensolver
 
-// Eigen-decomposition of the symmetric m x m matrix G (row-major, leading
-// dimension ld) by cyclic Jacobi with Brent-Luk parallel ordering (m/2
-// disjoint rotations per round).
-//
-// Warm start: when m_prev > 0, evec holds the eigenvectors of G's leading
-// m_prev x m_prev block from the previous call (G only grew since), so in
-// the basis blockdiag(evec, I) the leading block is diag(eval) and only the
-// new border has to be transformed.  Rotations whose off-diagonal element is
-// below 1e-15 (|a_pp| + |a_qq|) are skipped, and only the active pairs are
-// applied; sweeps stop when one applies no rotation.  Output: eigenvalues
-// (the converged diagonal) ascending and
-// eigenvectors as columns, evec[l * ld + a] = component a of vector l.
+// one CTA: the eigen-decomposition of one projected matrix (see jacobi.cuh)
 __global__ void k_jacobi(const double *__restrict__ G, int ld, int m, int m_prev, double *__restrict__ eval,
                          double *__restrict__ evec) {
     extern __shared__ double jsm[];
-    double (*A)[SHCI_MAX_SUB + 1] = reinterpret_cast<double (*)[SHCI_MAX_SUB + 1]>(jsm);
-    double (*Q)[SHCI_MAX_SUB + 1] = reinterpret_cast<double (*)[SHCI_MAX_SUB + 1]>(jsm + SHCI_MAX_SUB * (SHCI_MAX_SUB + 1));
-    double *Gs = jsm + 2 * SHCI_MAX_SUB * (SHCI_MAX_SUB + 1);          // exact G, m x m (stride m)
-    __shared__ double cs[SHCI_MAX_SUB / 2], sn[SHCI_MAX_SUB / 2];
-    __shared__ int pp[SHCI_MAX_SUB / 2], qq[SHCI_MAX_SUB / 2];
-    __shared__ int n_active, any_rot;
-    __shared__ double lam[SHCI_MAX_SUB];
-    const int mm = (m + 1) & ~1;
-    const int tid = threadIdx.x, nt = blockDim.x;
-    const int mp = (m_prev > 0 && m_prev <= m) ? m_prev : 0;
-    for (int e = tid; e < m * m; e += nt) {
-        int r = e / m, c = e % m;
-        Gs[e] = 0.5 * (G[r * ld + c] + G[c * ld + r]);
-    }
-    // Q = blockdiag(previous eigenvectors, I)
-    for (int e = tid; e < mm * mm; e += nt) {
-        int r = e / mm, c = e % mm;
-        double q = (r == c) ? 1.0 : 0.0;
-        if (r < mp && c < mp) q = evec[c * ld + r];
-        Q[r][c] = q;
-    }
-    __syncthreads();
-    // A = Q^T G Q: leading block diag(previous eigenvalues), border transformed, trailing block copied
-    for (int e = tid; e < mm * mm; e += nt) {
-        int r = e / mm, c = e % mm;
-        double v = 0.0;
-        if (r < m && c < m) {
-            if (r < mp && c < mp) {
-                v = (r == c) ? eval[r] : 0.0;
-            } else if (r < mp) {          // (Q^T G)[r][c] for border column c
-                for (int s = 0; s < mp; s++) v = fma(Q[s][r], Gs[s * m + c], v);
-            } else if (c < mp) {
-                for (int s = 0; s < mp; s++) v = fma(Q[s][c], Gs[r * m + s], v);
-            } else {
-                v = Gs[r * m + c];
-            }
-        }
-        A[r][c] = v;
-    }
-    __syncthreads();
-    if (mm != m && tid == 0) {
-        // padding index: decoupled, with a diagonal value above every Gershgorin bound
-        double bound = 0.0;
-        for (int r = 0; r < m; r++) {
-            double s = 0.0;
-            for (int c = 0; c < m; c++) s += fabs(A[r][c]);
-            bound = fmax(bound, s);
-        }
-        A[m][m] = 2.0 * bound + 1.0;
-    }
-    __syncthreads();
-    for (int sweep = 0; sweep < 60; sweep++) {
-        if (tid == 0) any_rot = 0;
-        __syncthreads();
-        for (int round = 0; round < mm - 1; round++) {
-            if (tid == 0) n_active = 0;
-            __syncthreads();
-            if (tid < mm / 2) {
-                int x = tid, y = mm - 1 - tid;
-                int p = x == 0 ? 0 : ((x - 1 + round) % (mm - 1)) + 1;
-                int q = y == 0 ? 0 : ((y - 1 + round) % (mm - 1)) + 1;
-                if (p > q) { int t = p; p = q; q = t; }
-                const double apq = A[p][q];
-                if (fabs(apq) > 1e-15 * (fabs(A[p][p]) + fabs(A[q][q])) + 1e-300) {
-                    double tau = (A[q][q] - A[p][p]) / (2.0 * apq);
-                    double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-                    double c = 1.0 / sqrt(1.0 + t * t);
-                    int slot = atomicAdd(&n_active, 1);
-                    cs[slot] = c;
-                    sn[slot] = t * c;
-                    pp[slot] = p;
-                    qq[slot] = q;
-                }
-            }
-            __syncthreads();
-            const int na = n_active;
-            __syncthreads();             // every thread has read n_active before it is reset
-            if (na == 0) continue;       // uniform: every thread read the same count
-            if (tid == 0) any_rot = 1;
-            // rows: A <- J^T A
-            for (int e = tid; e < na * mm; e += nt) {
-                int t = e / mm, j = e % mm;
-                int p = pp[t], q = qq[t];
-                double c = cs[t], s = sn[t];
-                double ap = A[p][j], aq = A[q][j];
-                A[p][j] = c * ap - s * aq;
-                A[q][j] = s * ap + c * aq;
-            }
-            __syncthreads();
-            // columns: A <- A J, Q <- Q J
-            for (int e = tid; e < na * mm; e += nt) {
-                int t = e / mm, i = e % mm;
-                int p = pp[t], q = qq[t];
-                double c = cs[t], s = sn[t];
-                double ap = A[i][p], aq = A[i][q];
-                A[i][p] = c * ap - s * aq;
-                A[i][q] = s * ap + c * aq;
-                double qp = Q[i][p], qv = Q[i][q];
-                Q[i][p] = c * qp - s * qv;
-                Q[i][q] = s * qp + c * qv;
-            }
-            __syncthreads();
-        }
-        __syncthreads();
-        const int rot = any_rot;
-        __syncthreads();                 // every thread has read any_rot before it is reset
-        if (!rot) break;
-    }
-    for (int a = tid; a < mm; a += nt) lam[a] = A[a][a];
-    __syncthreads();
-    // sort ascending (rank by value, ties by index) and write out the first m
-    for (int a = tid; a < mm; a += nt) {
-        double va = lam[a];
-        int rank = 0;
-        for (int b = 0; b < mm; b++) {
-            double vb = lam[b];
-            rank += (vb < va) || (vb == va && b < a);
-        }
-        if (rank < m) {
-            eval[rank] = va;
-            for (int r = 0; r < m; r++) evec[rank * ld + r] = Q[r][a];
-        }
-    }
+    jacobi_solve(G, ld, m, m_prev, eval, evec, jsm);
 }
-
-constexpr size_t JACOBI_SMEM = sizeof(double) * (2 * SHCI_MAX_SUB * (SHCI_MAX_SUB + 1) + SHCI_MAX_SUB * SHCI_MAX_SUB);
 
 // ---------------------------------------------------------------- guesses
 

@@ -56,6 +56,7 @@ struct EnumArgs {
     double *y;                              // [n][K]
     const double *diag;
     int accumulate;                         // 0: y = diag x + part, 1: y += part
+    int k_active;                           // vectors in use (<= K; 0 means K)
     // gradient (x = the root c, [n])
     double *gdh;                            // [GRAD_REPLICAS][n_orb * n_orb]
     double *geri;                           // [GRAD_REPLICAS][packed length]
@@ -276,13 +277,17 @@ __device__ __forceinline__ void flush(RowAcc<MODE, K> &R, const EnumArgs &A, con
             A.col[R.pos + lane] = j;
             A.val[R.pos + lane] = v;
         } else if (MODE == ENUM_SIGMA) {
+            // x is read through L2 (ld.global.cg): the batched solver rewrites it
+            // between phases of one persistent launch
             if (K == 2) {
-                const double2 c2 = __ldg(reinterpret_cast<const double2 *>(A.x) + j);
+                const double2 c2 = __ldcg(reinterpret_cast<const double2 *>(A.x) + j);
                 R.acc[0] = fma(v, c2.x, R.acc[0]);
                 R.acc[K - 1] = fma(v, c2.y, R.acc[K - 1]);
             } else {
+                const int ka = A.k_active ? A.k_active : K;
 #pragma unroll
-                for (int q = 0; q < K; q++) R.acc[q] = fma(v, __ldg(&A.x[(int64_t)j * K + q]), R.acc[q]);
+                for (int q = 0; q < K; q++)
+                    if (q < ka) R.acc[q] = fma(v, __ldcg(&A.x[(int64_t)j * K + q]), R.acc[q]);
             }
         }
     }
@@ -378,8 +383,8 @@ __device__ __forceinline__ void row_end(RowAcc<MODE, K> &R, const EnumArgs &A, c
 #pragma unroll
             for (int q = 0; q < K; q++) {
                 const int64_t xi = i * K + q;
-                if (A.accumulate) A.y[xi] += R.acc[q];
-                else A.y[xi] = fma(A.diag[i], A.x[xi], R.acc[q]);
+                if (A.accumulate) A.y[xi] = __ldcg(&A.y[xi]) + R.acc[q];
+                else A.y[xi] = fma(A.diag[i], __ldcg(&A.x[xi]), R.acc[q]);
             }
         }
     } else if (MODE == ENUM_COUNT) {
@@ -391,35 +396,57 @@ __device__ __forceinline__ void row_end(RowAcc<MODE, K> &R, const EnumArgs &A, c
 
 // Rows grouped by alpha string: same-spin beta excitations (candidates in the
 // row's own alpha group) and opposite-spin doubles (candidates in the alpha
-// groups of the alpha singles of the row's alpha string).
+// groups of the alpha singles of the row's alpha string).  One work item:
+// up to ENUM_NW rows of one alpha group, one per warp; called by the whole CTA.
 template <int W, int MODE, int K>
-__global__ void __launch_bounds__(ENUM_THREADS) k_enum_alpha(EnumArgs A, DevInts I) {
-    __shared__ Tile<W> T;
-    __shared__ WarpQueue<W> Qs[ENUM_NW];
-    __shared__ int item_sh;
+__device__ __forceinline__ void enum_alpha_item(const EnumArgs &A, const DevInts &I, int64_t item, Tile<W> &T,
+                                                WarpQueue<W> &Q, unsigned long long &cand_local) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    WarpQueue<W> &Q = Qs[warp];
     constexpr bool NEED_DET = MODE != ENUM_COUNT;
-    unsigned long long cand_local = 0;
-    while (true) {
-        if (threadIdx.x == 0) item_sh = atomicAdd(A.work_counter, 1);
+    const int a = A.item_group[item];
+    const int64_t g_beg = A.ga_off[a], g_len = A.ga_off[a + 1] - g_beg;
+    const int64_t r = A.item_first[item] + warp;            // this warp's member
+    const bool valid = r < g_len;
+    const int64_t i = valid ? A.ga_det[g_beg + r] : 0;
+    const Str<W> Ai = load_str<W>(A.astr, a);
+    const Str<W> Bi = valid ? load_str<W>(A.ga_str, g_beg + r) : Str<W>{};
+    RowAcc<MODE, K> R;
+    row_begin(R, A, i, valid);
+    // same-spin beta: candidates with the same alpha string
+    for (int64_t t0 = 0; t0 < g_len; t0 += ENUM_TILE) {
+        const int cnt = (int)min((int64_t)ENUM_TILE, g_len - t0);
+        stage<W, NEED_DET>(T, A.ga_str, A.ga_det, g_beg + t0, cnt);
         __syncthreads();
-        const int64_t item = item_sh;
+        if (valid) {
+            cand_local += lane == 0 ? cnt : 0;
+            for (int b0 = 0; b0 < cnt; b0 += 32) {
+                const int e = b0 + lane;
+                bool match = false;
+                Str<W> Bj{};
+                if (e < cnt) {
+                    Bj = tile_str<W>(T, e);
+                    const int d = xor_popc<W>(Bi, Bj);
+                    match = (d == 2) | (d == 4);
+                }
+                emit<W, MODE, K>(R, A, I, Q, Bi, Ai, match, match && NEED_DET ? T.det[e] : 0, Bj, 0);
+            }
+        }
         __syncthreads();
-        if (item >= A.n_items) break;
-        const int a = A.item_group[item];
-        const int64_t g_beg = A.ga_off[a], g_len = A.ga_off[a + 1] - g_beg;
-        const int64_t r = A.item_first[item] + warp;            // this warp's member
-        const bool valid = r < g_len;
-        const int64_t i = valid ? A.ga_det[g_beg + r] : 0;
-        const Str<W> Ai = load_str<W>(A.astr, a);
-        const Str<W> Bi = valid ? load_str<W>(A.ga_str, g_beg + r) : Str<W>{};
-        RowAcc<MODE, K> R;
-        row_begin(R, A, i, valid);
-        // same-spin beta: candidates with the same alpha string
-        for (int64_t t0 = 0; t0 < g_len; t0 += ENUM_TILE) {
-            const int cnt = (int)min((int64_t)ENUM_TILE, g_len - t0);
-            stage<W, NEED_DET>(T, A.ga_str, A.ga_det, g_beg + t0, cnt);
+    }
+    // opposite-spin doubles: candidates in the groups of the alpha singles of a
+    const int64_t s_beg = A.as_off[a], s_end = A.as_off[a + 1];
+    for (int64_t s = s_beg; s < s_end; s++) {
+        const int k = A.as_idx[s];
+        const int64_t k_beg = A.ga_off[k], k_len = A.ga_off[k + 1] - k_beg;
+        int ctx = 1;
+        if (MODE != ENUM_COUNT) {
+            int pq_a, neg_a;
+            move_info<W>(Ai, load_str<W>(A.astr, k), pq_a, neg_a);
+            ctx = (pq_a << 2) | ((neg_a & 1) << 1) | 1;
+        }
+        for (int64_t t0 = 0; t0 < k_len; t0 += ENUM_TILE) {
+            const int cnt = (int)min((int64_t)ENUM_TILE, k_len - t0);
+            stage<W, NEED_DET>(T, A.ga_str, A.ga_det, k_beg + t0, cnt);
             __syncthreads();
             if (valid) {
                 cand_local += lane == 0 ? cnt : 0;
@@ -429,60 +456,67 @@ __global__ void __launch_bounds__(ENUM_THREADS) k_enum_alpha(EnumArgs A, DevInts
                     Str<W> Bj{};
                     if (e < cnt) {
                         Bj = tile_str<W>(T, e);
-                        const int d = xor_popc<W>(Bi, Bj);
-                        match = (d == 2) | (d == 4);
+                        match = xor_popc<W>(Bi, Bj) == 2;
                     }
-                    emit<W, MODE, K>(R, A, I, Q, Bi, Ai, match, match && NEED_DET ? T.det[e] : 0, Bj, 0);
+                    emit<W, MODE, K>(R, A, I, Q, Bi, Ai, match, match && NEED_DET ? T.det[e] : 0, Bj, ctx);
                 }
             }
             __syncthreads();
         }
-        // opposite-spin doubles: candidates in the groups of the alpha singles of a
-        const int64_t s_beg = A.as_off[a], s_end = A.as_off[a + 1];
-        for (int64_t s = s_beg; s < s_end; s++) {
-            const int k = A.as_idx[s];
-            const int64_t k_beg = A.ga_off[k], k_len = A.ga_off[k + 1] - k_beg;
-            int ctx = 1;
-            if (MODE != ENUM_COUNT) {
-                int pq_a, neg_a;
-                move_info<W>(Ai, load_str<W>(A.astr, k), pq_a, neg_a);
-                ctx = (pq_a << 2) | ((neg_a & 1) << 1) | 1;
-            }
-            for (int64_t t0 = 0; t0 < k_len; t0 += ENUM_TILE) {
-                const int cnt = (int)min((int64_t)ENUM_TILE, k_len - t0);
-                stage<W, NEED_DET>(T, A.ga_str, A.ga_det, k_beg + t0, cnt);
-                __syncthreads();
-                if (valid) {
-                    cand_local += lane == 0 ? cnt : 0;
-                    for (int b0 = 0; b0 < cnt; b0 += 32) {
-                        const int e = b0 + lane;
-                        bool match = false;
-                        Str<W> Bj{};
-                        if (e < cnt) {
-                            Bj = tile_str<W>(T, e);
-                            match = xor_popc<W>(Bi, Bj) == 2;
-                        }
-                        emit<W, MODE, K>(R, A, I, Q, Bi, Ai, match, match && NEED_DET ? T.det[e] : 0, Bj, ctx);
-                    }
-                }
-                __syncthreads();
-            }
-        }
-        row_end<W, MODE, K>(R, A, I, Q, Bi, Ai, i, valid);
     }
-    if (MODE == ENUM_COUNT && lane == 0 && cand_local) atomicAdd(A.cand, cand_local);
+    row_end<W, MODE, K>(R, A, I, Q, Bi, Ai, i, valid);
 }
 
 // Rows grouped by beta string: same-spin alpha excitations (candidates with
-// the same beta string).
+// the same beta string).  One work item, called by the whole CTA.
 template <int W, int MODE, int K>
-__global__ void __launch_bounds__(ENUM_THREADS) k_enum_beta(EnumArgs A, DevInts I) {
-    __shared__ Tile<W> T;
-    __shared__ WarpQueue<W> Qs[ENUM_NW];
-    __shared__ int item_sh;
+__device__ __forceinline__ void enum_beta_item(const EnumArgs &A, const DevInts &I, int64_t item, Tile<W> &T,
+                                               WarpQueue<W> &Q, unsigned long long &cand_local) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    WarpQueue<W> &Q = Qs[warp];
     constexpr bool NEED_DET = MODE != ENUM_COUNT;
+    const int b = A.item_group[item];
+    const int64_t g_beg = A.gb_off[b], g_len = A.gb_off[b + 1] - g_beg;
+    const int64_t r = A.item_first[item] + warp;
+    const bool valid = r < g_len;
+    const int64_t i = valid ? A.gb_det[g_beg + r] : 0;
+    const Str<W> Bi = load_str<W>(A.bstr, b);
+    const Str<W> Ai = valid ? load_str<W>(A.gb_str, g_beg + r) : Str<W>{};
+    RowAcc<MODE, K> R;
+    row_begin(R, A, i, valid);
+    for (int64_t t0 = 0; t0 < g_len; t0 += ENUM_TILE) {
+        const int cnt = (int)min((int64_t)ENUM_TILE, g_len - t0);
+        stage<W, NEED_DET>(T, A.gb_str, A.gb_det, g_beg + t0, cnt);
+        __syncthreads();
+        if (valid) {
+            cand_local += lane == 0 ? cnt : 0;
+            for (int b0 = 0; b0 < cnt; b0 += 32) {
+                const int e = b0 + lane;
+                bool match = false;
+                Str<W> Aj{};
+                if (e < cnt) {
+                    Aj = tile_str<W>(T, e);
+                    const int d = xor_popc<W>(Ai, Aj);
+                    match = (d == 2) | (d == 4);
+                }
+                emit<W, MODE, K>(R, A, I, Q, Ai, Bi, match, match && NEED_DET ? T.det[e] : 0, Aj, 0);
+            }
+        }
+        __syncthreads();
+    }
+    row_end<W, MODE, K>(R, A, I, Q, Ai, Bi, i, valid);
+}
+
+template <int W>
+struct EnumSmem {
+    Tile<W> T;
+    WarpQueue<W> Q[ENUM_NW];
+};
+
+// persistent grids: CTAs take work items from an atomic counter
+template <int W, int MODE, int K>
+__global__ void __launch_bounds__(ENUM_THREADS) k_enum_alpha(EnumArgs A, DevInts I) {
+    __shared__ EnumSmem<W> S;
+    __shared__ int item_sh;
     unsigned long long cand_local = 0;
     while (true) {
         if (threadIdx.x == 0) item_sh = atomicAdd(A.work_counter, 1);
@@ -490,38 +524,25 @@ __global__ void __launch_bounds__(ENUM_THREADS) k_enum_beta(EnumArgs A, DevInts 
         const int64_t item = item_sh;
         __syncthreads();
         if (item >= A.n_items) break;
-        const int b = A.item_group[item];
-        const int64_t g_beg = A.gb_off[b], g_len = A.gb_off[b + 1] - g_beg;
-        const int64_t r = A.item_first[item] + warp;
-        const bool valid = r < g_len;
-        const int64_t i = valid ? A.gb_det[g_beg + r] : 0;
-        const Str<W> Bi = load_str<W>(A.bstr, b);
-        const Str<W> Ai = valid ? load_str<W>(A.gb_str, g_beg + r) : Str<W>{};
-        RowAcc<MODE, K> R;
-        row_begin(R, A, i, valid);
-        for (int64_t t0 = 0; t0 < g_len; t0 += ENUM_TILE) {
-            const int cnt = (int)min((int64_t)ENUM_TILE, g_len - t0);
-            stage<W, NEED_DET>(T, A.gb_str, A.gb_det, g_beg + t0, cnt);
-            __syncthreads();
-            if (valid) {
-                cand_local += lane == 0 ? cnt : 0;
-                for (int b0 = 0; b0 < cnt; b0 += 32) {
-                    const int e = b0 + lane;
-                    bool match = false;
-                    Str<W> Aj{};
-                    if (e < cnt) {
-                        Aj = tile_str<W>(T, e);
-                        const int d = xor_popc<W>(Ai, Aj);
-                        match = (d == 2) | (d == 4);
-                    }
-                    emit<W, MODE, K>(R, A, I, Q, Ai, Bi, match, match && NEED_DET ? T.det[e] : 0, Aj, 0);
-                }
-            }
-            __syncthreads();
-        }
-        row_end<W, MODE, K>(R, A, I, Q, Ai, Bi, i, valid);
+        enum_alpha_item<W, MODE, K>(A, I, item, S.T, S.Q[threadIdx.x >> 5], cand_local);
     }
-    if (MODE == ENUM_COUNT && lane == 0 && cand_local) atomicAdd(A.cand, cand_local);
+    if (MODE == ENUM_COUNT && (threadIdx.x & 31) == 0 && cand_local) atomicAdd(A.cand, cand_local);
+}
+
+template <int W, int MODE, int K>
+__global__ void __launch_bounds__(ENUM_THREADS) k_enum_beta(EnumArgs A, DevInts I) {
+    __shared__ EnumSmem<W> S;
+    __shared__ int item_sh;
+    unsigned long long cand_local = 0;
+    while (true) {
+        if (threadIdx.x == 0) item_sh = atomicAdd(A.work_counter, 1);
+        __syncthreads();
+        const int64_t item = item_sh;
+        __syncthreads();
+        if (item >= A.n_items) break;
+        enum_beta_item<W, MODE, K>(A, I, item, S.T, S.Q[threadIdx.x >> 5], cand_local);
+    }
+    if (MODE == ENUM_COUNT && (threadIdx.x & 31) == 0 && cand_local) atomicAdd(A.cand, cand_local);
 }
 
 // work items: one per chunk of ENUM_NW members of each group

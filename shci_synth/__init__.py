@@ -278,6 +278,27 @@ def config(name: str) -> Config:
     return CONFIGS[name]
 
 
+def batch_configs(n_sys: int = 64, seed: int = 5000, n_det_max: int = 2_000_000, n_det_min: int = 10_000,
+                  roots: int = 4):
+    """The batched workload: n_sys independent systems of uneven size.
+
+    System s draws (from its own generator seeded seed + s) n_orb ~ U{12..30},
+    electrons per spin ~ U{3..8} (capped at n_orb - 2, alpha and beta drawn
+    separately) and |V| log-uniform in [n_det_min, n_det_max], capped at half
+    the full-CI dimension; integrals use rank 2 * n_orb and seed seed + s."""
+    out = []
+    for s in range(n_sys):
+        rng = np.random.default_rng(seed + s)
+        n_orb = int(rng.integers(12, 31))
+        na = int(min(rng.integers(3, 9), n_orb - 2))
+        nb = int(min(rng.integers(3, 9), n_orb - 2))
+        n_det = int(np.exp(rng.uniform(np.log(n_det_min), np.log(n_det_max))))
+        fci = math.comb(n_orb, na) * math.comb(n_orb, nb)
+        n_det = max(roots + 1, min(n_det, fci // 2))
+        out.append(Config("batch_%02d" % s, n_orb, na, nb, 2 * n_orb, seed + s, n_det, roots))
+    return out
+
+
 def make_system(cfg: Config, n_det: int | None = None):
     """(h, eri_packed, e_core, dets) for a workload; ``n_det`` overrides the
     space size (a smaller space of the same shape for parity runs)."""
