@@ -41,9 +41,11 @@ def metric_name():
     return "sigma H·c nonzeros/s and Davidson time-to-E (|ΔE|<1e-9 Ha) vs roofline, 1 GB300"
 
 
-def workload_desc(cfg):
-    return ("%s: %d orbitals, %da+%db electrons, |V|=%d selected determinants, %d roots, stored H, FP64"
-            % (cfg.name, cfg.n_orb, cfg.n_alpha, cfg.n_beta, cfg.n_det, cfg.roots))
+def workload_desc(cfg, n_det=None):
+    n = n_det if n_det is not None else cfg.n_det
+    return ("%s: %d orbitals, %da+%db electrons, |V|=%d %s determinants, %d roots, stored H, FP64"
+            % (cfg.name, cfg.n_orb, cfg.n_alpha, cfg.n_beta, n, "selected" if cfg.n_det else "full-CI",
+               cfg.roots))
 
 
 def load_peaks():
@@ -391,6 +393,226 @@ def run_sigma_only(args):
     ctx.close()
 
 
+# ------------------------------------------------------------------ other workloads
+# Each prints one JSON measurement line (not the default bench line).
+
+def _gpu_setup():
+    import torch
+    import paper_1809_04600_gb300 as P
+    P.build()
+    P.load_library()
+    return torch, P
+
+
+def _dev(torch, a):
+    a = np.ascontiguousarray(a)
+    if a.dtype == np.uint64:
+        a = a.view(np.int64)
+    return torch.from_numpy(a).cuda()
+
+
+def run_fci(args):
+    """Full-CI space, 10 orbitals, 4a4b (44,100 determinants): build + Davidson
+    (1 root, tol 1e-10) per step; energy against the oracle's."""
+    torch, P = _gpu_setup()
+    import oracle
+    cfg = S.config("fci_10o_4a4b")
+    h, eri, ec, dets = S.make_system(cfg)
+    n = dets.shape[0]
+    ctx = P.Context(0, torch.cuda.current_stream())
+    H = ctx.handle
+    dh, de, dd = _dev(torch, h), _dev(torch, eri), _dev(torch, dets)
+
+    def step():
+        P.shci_load_integrals(H, cfg.n_orb, ec, dh, de)
+        P.shci_build_connectivity(H, 4, 4, dd, P.SHCI_STORED)
+        return P.shci_davidson(H, 1, TOL, MAX_ITER)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    P.shci_set_timing(H, True)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        e, it, rc = step()
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t) / args.steps
+    st = P.shci_get_stats(H)
+    nnz_full = 2 * st["nnz_upper"] + n
+    O = oracle.System(h, eri, ec)
+    e_ref, _ = O.lowest_eigenpairs(dets, 1, tol=1e-12)
+    print(json.dumps({"workload": workload_desc(cfg, n),
+                      "metric": "sigma nnz/s over the step; time-to-E", "value": nnz_full * st["sigma_vectors"] /
+                      args.steps / dt, "unit": "nnz/s", "s_per_step": dt, "build_ms": st["build_ms"],
+                      "davidson_iters": it, "energy": float(e[0]), "energy_oracle": float(e_ref[0]),
+                      "abs_dE": abs(float(e[0]) - float(e_ref[0])), "nnz_upper": st["nnz_upper"],
+                      "sigma_kernel_ms": st["sigma_ms_total"] / max(1, st["sigma_launches"])}))
+    ctx.close()
+
+
+def run_large(args):
+    """76 orbitals, 14a14b, 12-orbital band, |V| = 5e7 (or --n-det): on-the-fly
+    sigma (no stored H).  Times the build (count pass) and sigma launches;
+    checks sampled rows against the oracle's brute-force rows."""
+    torch, P = _gpu_setup()
+    import oracle
+    cfg = S.config("sel_76o_14a14b_50m")
+    t = time.perf_counter()
+    h, eri, ec, dets = S.make_system(cfg, n_det=args.n_det)
+    t_gen = time.perf_counter() - t
+    n = dets.shape[0]
+    ctx = P.Context(0, torch.cuda.current_stream())
+    H = ctx.handle
+    P.shci_load_integrals(H, cfg.n_orb, ec, _dev(torch, h), _dev(torch, eri))
+    nnz = P.shci_build_connectivity(H, cfg.n_alpha, cfg.n_beta, _dev(torch, dets), P.SHCI_ON_THE_FLY)
+    st = P.shci_get_stats(H)
+    x = torch.from_numpy(S.random_vectors(n, 1, 3)).cuda()
+    y = torch.empty_like(x)
+    P.shci_sigma(H, x, y)                       # warm-up
+    P.shci_set_timing(H, True)
+    reps = max(1, min(args.steps, 3))
+    for _ in range(reps):
+        P.shci_sigma(H, x, y)
+    st2 = P.shci_get_stats(H)
+    ms = st2["sigma_ms_total"] / st2["sigma_launches"]
+    nnz_full = 2 * nnz + n
+    # algorithmic HBM bytes per product: determinants (32 B), x, y and diag (8 B each)
+    # per determinant, plus the helper lists read once (member strings and indices)
+    bytes_alg = n * (16.0 * S.n_words(cfg.n_orb) * 2 + 24.0) + n * (8.0 + 4.0) * 2
+    hbm_peak, kind = load_peaks()
+    O = oracle.System(h, eri, ec)
+    rng = np.random.default_rng(7)
+    rows = np.concatenate([[0], rng.choice(n, 7, replace=False)])
+    xr = x.cpu().numpy()
+    yr = y.cpu().numpy()
+    ref = O.sigma_rows(dets, xr, rows)
+    err = float(np.max(np.abs(yr[:, rows] - ref)))
+    print(json.dumps({"workload": workload_desc(cfg).replace("stored H", "on-the-fly sigma"),
+                      "n_det": n, "nnz_upper": nnz, "gen_s": t_gen, "build_count_ms": st["build_ms"],
+                      "candidates_per_pass": st["candidates"], "sigma_ms": ms,
+                      "value": nnz_full / (ms / 1e3), "unit": "full-matrix nnz/s (one vector)",
+                      "roofline": {"bound": "alu", "hbm_achieved_gbs": bytes_alg / (ms / 1e3) / 1e9,
+                                   "hbm_peak_gbs": hbm_peak, "hbm_frac": bytes_alg / (ms / 1e3) / 1e9 / hbm_peak,
+                                   "candidates_per_s": st["candidates"] / (ms / 1e3)},
+                      "sampled_rows": int(rows.size), "max_abs_err_sampled_rows": err}))
+    ctx.close()
+
+
+def run_adjoint(args):
+    """20 orbitals, 5a5b, |V| = 1e6: energy + hand-written backward; central
+    differences (step 1e-5) along 16 seeded directions at full size."""
+    torch, P = _gpu_setup()
+    cfg = S.config("sel_20o_5a5b_1m")
+    h, eri, ec, dets = S.make_system(cfg, n_det=args.n_det)
+    n = dets.shape[0]
+    ctx = P.Context(0, torch.cuda.current_stream())
+    H = ctx.handle
+    dd = _dev(torch, dets)
+
+    def energy(hh, ee, tol=1e-13):
+        P.shci_load_integrals(H, cfg.n_orb, ec, _dev(torch, hh), _dev(torch, ee))
+        P.shci_build_connectivity(H, 5, 5, dd, P.SHCI_STORED)
+        v = torch.empty((1, n), dtype=torch.float64, device="cuda")
+        e, it, rc = P.shci_davidson(H, 1, tol, 800, vecs=v)
+        return float(e[0]), v
+
+    e0, v = energy(h, eri)
+    gh = torch.empty((cfg.n_orb, cfg.n_orb), dtype=torch.float64, device="cuda")
+    ge = torch.empty(eri.size, dtype=torch.float64, device="cuda")
+    P.shci_energy_backward(H, v[0], 1.0, gh, ge)      # warm-up
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    reps = 3
+    for _ in range(reps):
+        P.shci_energy_backward(H, v[0], 1.0, gh, ge)
+    torch.cuda.synchronize()
+    t_bwd = (time.perf_counter() - t) / reps
+    ghn, gen = gh.cpu().numpy(), ge.cpu().numpy()
+    rng = np.random.default_rng(4004)
+    step = 1e-5
+    rel = []
+    ndir = 16 if args.n_det is None or args.n_det > 0 else 16
+    for _ in range(ndir):
+        dh = rng.normal(size=h.shape)
+        dh = 0.5 * (dh + dh.T)
+        de = rng.normal(size=eri.size)
+        ep, _ = energy(h + step * dh, eri + step * de)
+        em, _ = energy(h - step * dh, eri - step * de)
+        fd = (ep - em) / (2 * step)
+        an = float(np.sum(ghn * dh) + np.dot(gen, de))
+        rel.append(abs(fd - an) / max(1.0, abs(an)))
+    e_lin = ec + float(np.sum(h * ghn) + np.dot(eri, gen))
+    print(json.dumps({"workload": workload_desc(cfg), "n_det": n, "energy": e0,
+                      "backward_s": t_bwd, "fd_directions": ndir, "fd_step": step,
+                      "fd_max_rel_err": max(rel), "fd_rel_errs": rel, "trace_gamma": float(np.trace(ghn)),
+                      "energy_linear_identity_err": abs(e_lin - e0)}))
+    ctx.close()
+
+
+def run_batch(args):
+    """64 uneven systems x 4 roots: one batched persistent launch vs 64
+    sequential shci_davidson calls (same builds, same tolerance)."""
+    torch, P = _gpu_setup()
+    cfgs = S.batch_configs()
+    if args.n_det:
+        cfgs = [S.Config(c.name, c.n_orb, c.n_alpha, c.n_beta, c.rank, c.seed, min(c.n_det, args.n_det), c.roots)
+                for c in cfgs]
+    t = time.perf_counter()
+    systems = []
+    for c in cfgs:
+        h, eri, ec, dets = S.make_system(c)
+        systems.append(dict(n_orb=c.n_orb, n_alpha=c.n_alpha, n_beta=c.n_beta, h=_dev(torch, h),
+                            eri=_dev(torch, eri), e_core=ec, dets=_dev(torch, dets)))
+    t_gen = time.perf_counter() - t
+    ctx = P.Context(0, torch.cuda.current_stream())
+    budget = args.batch_budget_gb * 1e9
+    t = time.perf_counter()
+    b = P.shci_batch_create(ctx.handle, systems, stored_budget_bytes=budget)
+    torch.cuda.synchronize()
+    t_create = time.perf_counter() - t
+    k = 4
+    e, it, conv, rc = P.shci_batch_davidson(ctx.handle, b, len(systems), k, tol=TOL, max_iter=MAX_ITER)
+    st0 = P.shci_batch_get_stats(b)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    e, it, conv, rc = P.shci_batch_davidson(ctx.handle, b, len(systems), k, tol=TOL, max_iter=MAX_ITER)
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t
+    st = P.shci_batch_get_stats(b)
+    P.shci_batch_destroy(b)
+    # sequential: one context per system, same storage decisions, Davidson timed alone
+    seq_time, seq_e = 0.0, []
+    left = budget
+    for d in systems:
+        c2 = P.Context(0, torch.cuda.current_stream())
+        P.shci_load_integrals(c2.handle, d["n_orb"], d["e_core"], d["h"], d["eri"])
+        nnz = P.shci_build_connectivity(c2.handle, d["n_alpha"], d["n_beta"], d["dets"], P.SHCI_ON_THE_FLY)
+        mode = P.SHCI_STORED if 12.0 * (2 * nnz + 0) < left else P.SHCI_ON_THE_FLY
+        if mode == P.SHCI_STORED:
+            P.shci_build_connectivity(c2.handle, d["n_alpha"], d["n_beta"], d["dets"], P.SHCI_STORED)
+            left -= 12.0 * 2 * nnz
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        es, its, rcs = P.shci_davidson(c2.handle, k, TOL, MAX_ITER, check=False)
+        torch.cuda.synchronize()
+        seq_time += time.perf_counter() - t
+        seq_e.append(es)
+        c2.close()
+    seq_e = np.array(seq_e)
+    print(json.dumps({"workload": "64 systems: n_orb U{12..30}, 3-8 electrons per spin, |V| log-uniform "
+                                  "1e4..2e6 (capped at half the full-CI size), 4 roots each, FP64",
+                      "total_det": st["total_det"], "total_nnz_upper": st["total_nnz_upper"],
+                      "n_stored": st["n_stored"], "n_on_the_fly": st["n_on_the_fly"], "gen_s": t_gen,
+                      "create_s": t_create, "batched_s": t_batch, "batched_device_ms": st["solve_ms"],
+                      "sequential_s": seq_time, "speedup": seq_time / t_batch,
+                      "max_abs_dE_vs_sequential": float(np.max(np.abs(e - seq_e))),
+                      "graph": st["graph"], "grid_ctas": st["grid_ctas"],
+                      "tuned": {"rows_per_item": st["tuned_rows_per_item"], "ctas_per_sm": st["tuned_ctas_per_sm"],
+                                "trial_ms": st0["tune_ms"]},
+                      "max_iters": st["max_iters"], "all_converged": bool(conv.all())}))
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -405,8 +627,13 @@ def main():
                     help="profiling only: a smaller space of the same shape (not a bench line)")
     ap.add_argument("--sigma-only", type=int, default=0,
                     help="profiling only: build once, then launch the sigma kernel this many times")
+    ap.add_argument("--workload", default="main", choices=["main", "fci", "large", "adjoint", "batch"],
+                    help="main: the bench line; others print the measurement line of another workload")
+    ap.add_argument("--batch-budget-gb", type=float, default=180.0)
     args = ap.parse_args()
-    if args.sigma_only:
+    if args.workload != "main":
+        {"fci": run_fci, "large": run_large, "adjoint": run_adjoint, "batch": run_batch}[args.workload](args)
+    elif args.sigma_only:
         run_sigma_only(args)
     elif args.impl == "reference":
         run_reference(args)

@@ -4,6 +4,7 @@
 // Slater-Condon value, into both rows of a symmetric sparse matrix.
 #include <algorithm>
 #include <atomic>
+#include <cstdlib>
 #include <numeric>
 
 #include "enum_launch.cuh"
@@ -329,23 +330,25 @@ static void group_by(shci_ctx *c, const int32_t *major, const int32_t *minor, in
     LAUNCHED(2);
 }
 
+// Single-excitation lists (Table I's alpha-singles, and the beta mirror) over
+// the U unique strings `ustr` with ne electrons: keys are the strings with one
+// electron removed (alpha^(-1)); strings sharing a key are single excitations
+// of one another, and each such pair shares exactly one key (Sec. III).
 template <int W>
-static void alpha_singles(shci_ctx *c) {
+static int64_t string_singles(shci_ctx *c, const uint64_t *ustr, int64_t U, int ne, DevBuf<int64_t> &off,
+                              DevBuf<int32_t> &idx) {
     cudaStream_t st = c->st;
-    const int64_t Ua = c->Ua;
-    const int ne = c->n_alpha;
-    const int64_t nk = Ua * ne;
-    c->as_off.alloc((size_t)Ua + 1);
+    const int64_t nk = U * ne;
+    off.alloc((size_t)U + 1);
     if (ne == 0 || nk == 0) {
-        CUDA_TRY(cudaMemsetAsync(c->as_off.p, 0, sizeof(int64_t) * (Ua + 1), st));
-        c->as_idx.alloc(1);
-        c->n_alpha_singles = 0;
-        return;
+        CUDA_TRY(cudaMemsetAsync(off.p, 0, sizeof(int64_t) * (U + 1), st));
+        idx.alloc(1);
+        return 0;
     }
-    if (nk > 0x7FFFFFFFll) throw ShciError{SHCI_ERR_INVALID, "too many alpha strings"};
+    if (nk > 0x7FFFFFFFll) throw ShciError{SHCI_ERR_INVALID, "too many unique strings"};
     c->sort_keys.alloc((size_t)std::max<int64_t>(nk * W, c->n_det * W));
     c->sort_vals.alloc((size_t)std::max<int64_t>(nk, c->n_det));
-    k_minus_one_keys<W><<<grid_for(Ua), 256, 0, st>>>(c->astr.p, Ua, ne, c->sort_keys.p, c->sort_vals.p);
+    k_minus_one_keys<W><<<grid_for(U), 256, 0, st>>>(ustr, U, ne, c->sort_keys.p, c->sort_vals.p);
     KERNEL_CHECK();
     radix_sort<W>(c->sort_keys.p, c->sort_vals.p, nk, c->sw, st);
     DevBuf<int64_t> seg_start;
@@ -353,20 +356,107 @@ static void alpha_singles(shci_ctx *c) {
     seg_start.alloc((size_t)nk);
     seg_len.alloc((size_t)nk);
     k_segment_info<W><<<grid_for(nk), 256, 0, st>>>(c->sort_keys.p, c->sort_vals.p, nk, seg_start.p, seg_len.p);
-    c->i64a.alloc((size_t)std::max<int64_t>(Ua + 1, c->n_det + 1));
-    c->i64c.alloc((size_t)scan_tmp_len(std::max<int64_t>(Ua + 1, c->n_det + 1)));
-    k_singles_count<<<grid_for(Ua), 256, 0, st>>>(seg_len.p, Ua, ne, c->i64a.p);
-    exclusive_scan<int64_t>(c->i64a.p, c->as_off.p, Ua, c->i64c.p, st);
+    c->i64a.alloc((size_t)std::max<int64_t>(U + 1, c->n_det + 1));
+    c->i64c.alloc((size_t)scan_tmp_len(std::max<int64_t>(U + 1, c->n_det + 1)));
+    k_singles_count<<<grid_for(U), 256, 0, st>>>(seg_len.p, U, ne, c->i64a.p);
+    exclusive_scan<int64_t>(c->i64a.p, off.p, U, c->i64c.p, st);
     int64_t total = 0;
-    CUDA_TRY(cudaMemcpyAsync(&total, c->as_off.p + Ua, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(&total, off.p + U, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));
-    c->as_idx.alloc((size_t)std::max<int64_t>(total, 1));
-    k_singles_fill<<<grid_for(Ua), 256, 0, st>>>(seg_start.p, seg_len.p, c->sort_vals.p, Ua, ne, c->as_off.p,
-                                                 c->as_idx.p);
+    idx.alloc((size_t)std::max<int64_t>(total, 1));
+    k_singles_fill<<<grid_for(U), 256, 0, st>>>(seg_start.p, seg_len.p, c->sort_vals.p, U, ne, off.p, idx.p);
     KERNEL_CHECK();
     LAUNCHED(4);
     CUDA_TRY(cudaStreamSynchronize(st));
-    c->n_alpha_singles = total;
+    return total;
+}
+
+template <int W>
+static void alpha_singles(shci_ctx *c) {
+    c->n_alpha_singles = string_singles<W>(c, c->astr.p, c->Ua, c->n_alpha, c->as_off, c->as_idx);
+}
+
+// occupancy bitmap over (unique alpha, unique beta) and, per 64-bit word, the
+// number of set bits before it in its row: the rank of a present (a, b) among
+// the members of alpha group a (sorted by beta index) is its member offset
+__global__ void k_occ_set(const int32_t *__restrict__ ia, const int32_t *__restrict__ ib, int64_t n, int64_t ow,
+                          unsigned long long *__restrict__ occ) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = ib[i];
+        atomicOr(&occ[(int64_t)ia[i] * ow + (b >> 6)], 1ull << (b & 63));
+    }
+}
+
+__global__ void k_occ_prefix(const unsigned long long *__restrict__ occ, int64_t Ua, int64_t ow,
+                             int32_t *__restrict__ pref) {
+    for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < Ua; a += (int64_t)gridDim.x * blockDim.x) {
+        int32_t run = 0;
+        for (int64_t w = 0; w < ow; w++) {
+            pref[a * ow + w] = run;
+            run += __popcll(occ[a * ow + w]);
+        }
+    }
+}
+
+// estimates of the opposite-spin work: scanning whole alpha groups (per unique
+// alpha string: |G(a)| * sum_{k in singles(a)} |G(k)|) vs looking up every
+// (alpha single, beta single) pair (per determinant: |singles(a)| |singles(b)|)
+__global__ void k_opp_costs(const int64_t *__restrict__ ga_off, const int64_t *__restrict__ as_off,
+                            const int32_t *__restrict__ as_idx, int64_t Ua, const int32_t *__restrict__ ia,
+                            const int32_t *__restrict__ ib, const int64_t *__restrict__ bs_off, int64_t n,
+                            unsigned long long *__restrict__ cost) {
+    unsigned long long scan = 0, look = 0;
+    for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < Ua; a += (int64_t)gridDim.x * blockDim.x) {
+        unsigned long long s = 0;
+        for (int64_t t = as_off[a]; t < as_off[a + 1]; t++) {
+            const int k = as_idx[t];
+            s += ga_off[k + 1] - ga_off[k];
+        }
+        scan += s * (unsigned long long)(ga_off[a + 1] - ga_off[a]);
+    }
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        look += (unsigned long long)(as_off[ia[i] + 1] - as_off[ia[i]]) * (bs_off[ib[i] + 1] - bs_off[ib[i]]);
+    atomicAdd(&cost[0], scan);
+    atomicAdd(&cost[1], look);
+}
+
+// Beta-single lists and the occupancy bitmap, then the choice between
+// scanning and lookups for the opposite-spin doubles (SHCI_OPP_SPIN=scan,
+// lookup or auto overrides the estimate).
+template <int W>
+static void opposite_spin_setup(shci_ctx *c) {
+    cudaStream_t st = c->st;
+    c->n_beta_singles = string_singles<W>(c, c->bstr.p, c->Ub, c->n_beta, c->bs_off, c->bs_idx);
+    c->occ_words = (c->Ub + 63) / 64;
+    const double bytes = (double)c->Ua * c->occ_words * 12.0;
+    const char *env = getenv("SHCI_OPP_SPIN");
+    std::string pref = env ? env : "auto";
+    c->opp_lookup = false;
+    if (pref == "scan" || bytes > 4.0e9) {
+        c->occ.reset();
+        c->occ_pref.reset();
+        return;
+    }
+    c->occ.alloc((size_t)(c->Ua * c->occ_words));
+    c->occ_pref.alloc((size_t)(c->Ua * c->occ_words));
+    CUDA_TRY(cudaMemsetAsync(c->occ.p, 0, sizeof(unsigned long long) * c->Ua * c->occ_words, st));
+    k_occ_set<<<grid_for(c->n_det), 256, 0, st>>>(c->ia.p, c->ib.p, c->n_det, c->occ_words, c->occ.p);
+    k_occ_prefix<<<grid_for(c->Ua), 256, 0, st>>>(c->occ.p, c->Ua, c->occ_words, c->occ_pref.p);
+    DevBuf<unsigned long long> cost;
+    cost.alloc(2);
+    CUDA_TRY(cudaMemsetAsync(cost.p, 0, 2 * sizeof(unsigned long long), st));
+    k_opp_costs<<<grid_for(std::max(c->Ua, c->n_det)), 256, 0, st>>>(c->ga_off.p, c->as_off.p, c->as_idx.p, c->Ua,
+                                                                      c->ia.p, c->ib.p, c->bs_off.p, c->n_det,
+                                                                      cost.p);
+    KERNEL_CHECK();
+    LAUNCHED(3);
+    unsigned long long h[2];
+    CUDA_TRY(cudaMemcpyAsync(h, cost.p, sizeof(h), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    c->opp_scan_cost = (int64_t)h[0];
+    c->opp_lookup_cost = (int64_t)h[1];
+    // a lookup is a few dependent L2 loads; a scanned candidate is one shared-memory load
+    c->opp_lookup = pref == "lookup" || (pref == "auto" && 4.0 * (double)h[1] < (double)h[0]);
 }
 
 template <int W>
@@ -393,6 +483,7 @@ static void build_w(shci_ctx *c, int mode) {
     CUDA_TRY(cudaStreamSynchronize(st));
     if (flags & 8) throw ShciError{SHCI_ERR_INVALID, "duplicate determinants in V"};
     alpha_singles<W>(c);
+    opposite_spin_setup<W>(c);
 
     DevInts I = dev_ints(c);
     c->diag.alloc((size_t)n);

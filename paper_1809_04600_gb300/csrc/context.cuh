@@ -46,6 +46,14 @@ struct shci_ctx {
     DevBuf<int64_t> as_off;                // alpha-single lists over unique alpha strings
     DevBuf<int32_t> as_idx;
     DevBuf<double> diag;                   // H_ii
+    // beta-single lists and the (alpha, beta) occupancy bitmap for opposite-spin lookups
+    DevBuf<int64_t> bs_off;
+    DevBuf<int32_t> bs_idx;
+    DevBuf<unsigned long long> occ;
+    DevBuf<int32_t> occ_pref;
+    int64_t occ_words = 0, n_beta_singles = 0;
+    bool opp_lookup = false;
+    int64_t opp_scan_cost = 0, opp_lookup_cost = 0;
     // enumeration work items: chunks of rows of one alpha (beta) group
     DevBuf<int32_t> item_a_group, item_a_first, item_b_group, item_b_first;
     int64_t n_items_a = 0, n_items_b = 0;

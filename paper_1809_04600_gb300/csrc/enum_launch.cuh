@@ -19,6 +19,13 @@ inline EnumArgs enum_args(const shci_ctx *c) {
     A.as_off = c->as_off.p;
     A.as_idx = c->as_idx.p;
     A.work_counter = c->counter.p + 1;
+    A.opp_lookup = c->opp_lookup ? 1 : 0;
+    A.ib = c->ib.p;
+    A.bs_off = c->bs_off.p;
+    A.bs_idx = c->bs_idx.p;
+    A.occ = c->occ.p;
+    A.occ_pref = c->occ_pref.p;
+    A.occ_words = c->occ_words;
     return A;
 }
 

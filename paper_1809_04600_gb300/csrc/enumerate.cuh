@@ -39,6 +39,14 @@ struct EnumArgs {
     const uint64_t *ga_str, *gb_str;        // member's other string
     const int64_t *as_off;                  // alpha singles
     const int32_t *as_idx;
+    // opposite-spin lookups (used when opp_lookup != 0)
+    int opp_lookup;
+    const int32_t *ib;                      // beta string index of each determinant
+    const int64_t *bs_off;                  // beta singles
+    const int32_t *bs_idx;
+    const unsigned long long *occ;          // [Ua][occ_words] occupancy bitmap over (alpha, beta)
+    const int32_t *occ_pref;                // [Ua][occ_words] set bits before each word in its row
+    int64_t occ_words;
     const int32_t *item_group;              // work item -> group index
     const int32_t *item_first;              // work item -> first member offset within the group
     int64_t n_items;
@@ -435,6 +443,49 @@ __device__ __forceinline__ void enum_alpha_item(const EnumArgs &A, const DevInts
     }
     // opposite-spin doubles: candidates in the groups of the alpha singles of a
     const int64_t s_beg = A.as_off[a], s_end = A.as_off[a + 1];
+    if (A.opp_lookup) {
+        // look up every (alpha single k of a, beta single kb of the row's beta
+        // string) in the occupancy bitmap; a hit's rank within row k is its
+        // member offset in alpha group k (members sorted by beta index).  The
+        // warps of the CTA work independently here.
+        if (valid) {
+            const int b = A.ib[i];
+            const int64_t sb_beg = A.bs_off[b];
+            const int sb_len = (int)(A.bs_off[b + 1] - sb_beg);
+            for (int64_t s = s_beg; s < s_end; s++) {
+                const int k = A.as_idx[s];
+                int ctx = 1;
+                if (MODE != ENUM_COUNT) {
+                    int pq_a, neg_a;
+                    move_info<W>(Ai, load_str<W>(A.astr, k), pq_a, neg_a);
+                    ctx = (pq_a << 2) | ((neg_a & 1) << 1) | 1;
+                }
+                const unsigned long long *row = A.occ + (int64_t)k * A.occ_words;
+                cand_local += lane == 0 ? sb_len : 0;
+                for (int y0 = 0; y0 < sb_len; y0 += 32) {
+                    const int y = y0 + lane;
+                    bool match = false;
+                    int32_t j = 0;
+                    Str<W> Bj{};
+                    if (y < sb_len) {
+                        const int kb = A.bs_idx[sb_beg + y];
+                        const unsigned long long word = __ldg(&row[kb >> 6]);
+                        const unsigned long long below = word & ((1ull << (kb & 63)) - 1ull);
+                        match = (word >> (kb & 63)) & 1ull;
+                        if (match && NEED_DET) {
+                            const int64_t m = A.ga_off[k] + __ldg(&A.occ_pref[(int64_t)k * A.occ_words + (kb >> 6)]) +
+                                              __popcll(below);
+                            j = A.ga_det[m];
+                            Bj = load_str<W>(A.ga_str, m);
+                        }
+                    }
+                    emit<W, MODE, K>(R, A, I, Q, Bi, Ai, match, j, Bj, ctx);
+                }
+            }
+        }
+        row_end<W, MODE, K>(R, A, I, Q, Bi, Ai, i, valid);
+        return;
+    }
     for (int64_t s = s_beg; s < s_end; s++) {
         const int k = A.as_idx[s];
         const int64_t k_beg = A.ga_off[k], k_len = A.ga_off[k + 1] - k_beg;

@@ -51,7 +51,7 @@ __device__ __forceinline__ int cholqr_coef(const double *S, int kb, const double
 // m_prev x m_prev block from the previous call (G only grew since), so in
 // the basis blockdiag(evec, I) the leading block is diag(eval) and only the
 // new border has to be transformed.  Rotations whose off-diagonal element is
-// below 1e-15 (|a_pp| + |a_qq|) are skipped, and only the active pairs are
+// below 1e-14 (|a_pp| + |a_qq|) are skipped, and only the active pairs are
 // applied; sweeps stop when one applies no rotation.  Output: eigenvalues
 // (the converged diagonal) ascending and
 // eigenvectors as columns, evec[l * ld + a] = component a of vector l.
@@ -108,7 +108,7 @@ __device__ __forceinline__ void jacobi_solve(const double *__restrict__ G, int l
         A[m][m] = 2.0 * bound + 1.0;
     }
     __syncthreads();
-    for (int sweep = 0; sweep < 60; sweep++) {
+    for (int sweep = 0; sweep < 30; sweep++) {
         if (tid == 0) any_rot = 0;
         __syncthreads();
         for (int round = 0; round < mm - 1; round++) {
@@ -120,7 +120,7 @@ __device__ __forceinline__ void jacobi_solve(const double *__restrict__ G, int l
                 int q = y == 0 ? 0 : ((y - 1 + round) % (mm - 1)) + 1;
                 if (p > q) { int t = p; p = q; q = t; }
                 const double apq = A[p][q];
-                if (fabs(apq) > 1e-15 * (fabs(A[p][p]) + fabs(A[q][q])) + 1e-300) {
+                if (fabs(apq) > 1e-14 * (fabs(A[p][p]) + fabs(A[q][q])) + 1e-300) {
                     double tau = (A[q][q] - A[p][p]) / (2.0 * apq);
                     double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
                     double c = 1.0 / sqrt(1.0 + t * t);

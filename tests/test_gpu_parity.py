@@ -121,6 +121,29 @@ def test_on_the_fly_sigma_and_energy(P, oracle_mod, name, n_det):
     B.close()
 
 
+@pytest.mark.parametrize("opp", ["scan", "lookup"])
+@pytest.mark.parametrize("name,n_det", [("sel_24o_6a6b_1m", 20000), ("sel_76o_14a14b_50m", 3001),
+                                        ("fci_10o_4a4b", None)])
+def test_opposite_spin_strategies(P, oracle_mod, monkeypatch, opp, name, n_det):
+    """Both opposite-spin strategies (scanning alpha groups; looking up
+    (alpha single, beta single) pairs in the occupancy bitmap) give the same
+    pairs, values and on-the-fly sigma."""
+    monkeypatch.setenv("SHCI_OPP_SPIN", opp)
+    cfg, h, eri, ec, dets = G.system(name, n_det)
+    O = oracle_mod.System(h, eri, ec)
+    ii, jj = oracle_mod.pairs_allpairs(dets)
+    B = G.Built(P, h, eri, ec, dets, cfg.n_alpha, cfg.n_beta)
+    _check_pairs_and_values(B, O, dets, ii, jj)
+    B.close()
+    B = G.Built(P, h, eri, ec, dets, cfg.n_alpha, cfg.n_beta, mode=P.SHCI_ON_THE_FLY)
+    n = dets.shape[0]
+    c = S.random_vectors(n, 2, 17)
+    ref = oracle_mod.sigma_pairs(n, ii, jj, O.hij_list(dets, ii, jj), O.hdiag(dets), c)
+    got = B.sigma(c)
+    assert np.max(np.abs(got - ref)) < 1e-10
+    B.close()
+
+
 def test_selected_space_two_roots(P, oracle_mod):
     cfg, h, eri, ec, dets = G.system("sel_24o_6a6b_1m", 20000)
     O = oracle_mod.System(h, eri, ec)
