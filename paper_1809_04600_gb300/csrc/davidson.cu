@@ -32,7 +32,8 @@ struct GramShape {
 template <int NB>
 __global__ void __launch_bounds__(DV_THREADS) k_gram(const double *__restrict__ A, int na,
                                                     const double *__restrict__ B, int64_t n,
-                                                    double *__restrict__ partial) {
+                                                    double *__restrict__ partial, const int *__restrict__ skip) {
+    if (skip && *skip) return;              // device-side decision: this product is not needed
     constexpr int NA = GramShape<NB>::NA;
     const int a0 = blockIdx.y * NA;
     const int cnt = min(NA, na - a0);
@@ -111,7 +112,8 @@ __global__ void k_unpack(const double *__restrict__ X, int k, int64_t n, double 
 template <int KB>
 __global__ void __launch_bounds__(DV_THREADS) k_project(const double *__restrict__ V, int m,
                                                        const double *__restrict__ C, int64_t n,
-                                                       double *__restrict__ T) {
+                                                       double *__restrict__ T, const int *__restrict__ skip) {
+    if (skip && *skip) return;
     __shared__ double cs[SHCI_MAX_SUB * KB];
     for (int e = threadIdx.x; e < m * KB; e += blockDim.x) cs[e] = C[e];
     __syncthreads();
@@ -339,6 +341,16 @@ __global__ void k_diag_copy(const double *__restrict__ S, int kb, double *__rest
     if (l < kb) out[l] = S[l * kb + l];
 }
 
+// "twice is enough": a second Gram-Schmidt pass is needed only if the first
+// removed more than half of some vector's norm (squared norm below a quarter)
+__global__ void k_second_pass_flag(const double *__restrict__ S, int kb, const double *__restrict__ pre,
+                                   int *__restrict__ skip) {
+    if (threadIdx.x != 0) return;
+    int need = 0;
+    for (int l = 0; l < kb; l++) need |= S[l * kb + l] < 0.25 * pre[l];
+    *skip = need ? 0 : 1;
+}
+
 #define DISPATCH_K(kval, F)                         \
     switch (kval) {                                 \
         case 1: F(1); break;                        \
@@ -360,39 +372,44 @@ struct Dav {
     cudaStream_t st;
     double *coef, *gram_s, *pre, *mcoef;   // device small buffers
     int *d_count;
+    int *d_skip;            // device flag: 1 = second Gram-Schmidt pass not needed
 
     double *Vr(int a) { return c->dw.V.p + (int64_t)a * n; }
     double *AVr(int a) { return c->dw.AV.p + (int64_t)a * n; }
 
     template <int NB>
-    void gram_nb(const double *A, int na, const double *B, double *out, int ld, int a0, int b0, bool sym) {
+    void gram_nb(const double *A, int na, const double *B, double *out, int ld, int a0, int b0, bool sym,
+                 const int *skip) {
         constexpr int NA = GramShape<NB>::NA;
         const int groups = (na + NA - 1) / NA;
         const int slices = std::max(1, std::min<int>((int)ceil_div(n, DV_THREADS * 4), n_slots / groups));
         dim3 grid(slices, groups);
-        k_gram<NB><<<grid, DV_THREADS, 0, st>>>(A, na, B, n, c->dw.partial.p);
+        k_gram<NB><<<grid, DV_THREADS, 0, st>>>(A, na, B, n, c->dw.partial.p, skip);
         const int outs = na * NB;
         k_gram_reduce<<<(outs + 7) / 8, 256, 0, st>>>(c->dw.partial.p, slices, na, NB, out, ld, a0, b0, sym ? 1 : 0);
         KERNEL_CHECK();
         g_kernel_launches += 2;
     }
 
-    // out[a0 + a][b0 + b] (leading dimension ld) = A[a] . B[b], a < na, b < nb; mirrored if sym
-    void gram(const double *A, int na, const double *B, int nb, double *out, int ld, int a0, int b0, bool sym) {
+    // out[a0 + a][b0 + b] (leading dimension ld) = A[a] . B[b], a < na, b < nb; mirrored if sym.
+    // With a non-null `skip` the products are not computed when *skip != 0 (and out
+    // then holds unused values).
+    void gram(const double *A, int na, const double *B, int nb, double *out, int ld, int a0, int b0, bool sym,
+              const int *skip = nullptr) {
         if (na <= 0 || nb <= 0) return;
         int b = 0;
         while (b < nb) {
             int left = nb - b;
             const double *Bb = B + (int64_t)b * n;
-            if (left >= 8) { gram_nb<8>(A, na, Bb, out, ld, a0, b0 + b, sym); b += 8; }
-            else if (left >= 4) { gram_nb<4>(A, na, Bb, out, ld, a0, b0 + b, sym); b += 4; }
-            else if (left >= 2) { gram_nb<2>(A, na, Bb, out, ld, a0, b0 + b, sym); b += 2; }
-            else { gram_nb<1>(A, na, Bb, out, ld, a0, b0 + b, sym); b += 1; }
+            if (left >= 8) { gram_nb<8>(A, na, Bb, out, ld, a0, b0 + b, sym, skip); b += 8; }
+            else if (left >= 4) { gram_nb<4>(A, na, Bb, out, ld, a0, b0 + b, sym, skip); b += 4; }
+            else if (left >= 2) { gram_nb<2>(A, na, Bb, out, ld, a0, b0 + b, sym, skip); b += 2; }
+            else { gram_nb<1>(A, na, Bb, out, ld, a0, b0 + b, sym, skip); b += 1; }
         }
     }
 
-    void project(const double *C, int m, int kb, double *T) {
-#define F(KB) k_project<KB><<<vec_blocks, DV_THREADS, 0, st>>>(c->dw.V.p, m, C, n, T)
+    void project(const double *C, int m, int kb, double *T, const int *skip = nullptr) {
+#define F(KB) k_project<KB><<<vec_blocks, DV_THREADS, 0, st>>>(c->dw.V.p, m, C, n, T, skip)
         DISPATCH_K(kb, F)
 #undef F
         KERNEL_CHECK();
@@ -408,17 +425,24 @@ struct Dav {
     }
 
     // Orthonormalise the kb vectors T[0..kb) against V[0..m) (classical
-    // Gram-Schmidt, twice) and among themselves (Cholesky-QR, twice), writing
-    // the accepted ones to V[m ..); returns how many were accepted.
+    // Gram-Schmidt; the second pass runs only when the first removed more
+    // than half of some vector's norm, decided on the device) and among
+    // themselves (Cholesky-QR, twice), writing the accepted ones to V[m ..);
+    // returns how many were accepted.
     int orthonormalize_append(double *T, int kb, int m) {
         double *T2 = c->dw.T.p + (int64_t)SHCI_MAX_K * n;
         // squared norms before projection: reference for the dependence test
         gram(T, kb, T, kb, gram_s, kb, 0, 0, false);
         k_diag_copy<<<1, 32, 0, st>>>(gram_s, kb, pre);
         g_kernel_launches += 1;
-        for (int pass = 0; pass < 2 && m > 0; pass++) {
+        if (m > 0) {
             gram(c->dw.V.p, m, T, kb, coef, kb, 0, 0, false);
             project(coef, m, kb, T);
+            gram(T, kb, T, kb, gram_s, kb, 0, 0, false);
+            k_second_pass_flag<<<1, 32, 0, st>>>(gram_s, kb, pre, d_skip);
+            gram(c->dw.V.p, m, T, kb, coef, kb, 0, 0, false, d_skip);
+            project(coef, m, kb, T, d_skip);
+            g_kernel_launches += 1;
         }
         gram(T, kb, T, kb, gram_s, kb, 0, 0, false);
         k_cholqr_coef<<<1, 1, 0, st>>>(gram_s, kb, pre, 1e-20, mcoef, d_count);
@@ -516,6 +540,7 @@ int davidson(shci_ctx *c, int k, double tol, int max_iter, const double *guess, 
     double *d_rn = w.small.p + 3 * SHCI_MAX_SUB * SHCI_MAX_K;  // [k]
     c->counter.alloc(4);
     d.d_count = c->counter.p + 3;
+    d.d_skip = c->counter.p + 2;
     DevBuf<int64_t> idx;
     idx.alloc(SHCI_MAX_K);
     cudaStream_t st = c->st;

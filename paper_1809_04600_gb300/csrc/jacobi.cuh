@@ -121,12 +121,34 @@ __device__ __forceinline__ void jacobi_solve(const double *__restrict__ G, int l
                 if (p > q) { int t = p; p = q; q = t; }
                 const double apq = A[p][q];
                 if (fabs(apq) > 1e-14 * (fabs(A[p][p]) + fabs(A[q][q])) + 1e-300) {
-                    double tau = (A[q][q] - A[p][p]) / (2.0 * apq);
-                    double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-                    double c = 1.0 / sqrt(1.0 + t * t);
+                    const double diff = A[q][q] - A[p][p];
+                    double c, s;
+                    const float tauf = (float)diff / (2.0f * (float)apq);
+                    if (fabs(apq) > 1e-30 && isfinite(tauf)) {
+                        // rotation angle in FP32 (the FP64 divide and square root are
+                        // long dependent chains on this part), then (c, s) renormalised
+                        // in FP64 so that c^2 + s^2 = 1 to FP64 precision: the rotation
+                        // stays exactly orthogonal and zeroes a_pq to ~1e-7 relative,
+                        // which the next sweep finishes
+                        const float tf = copysignf(1.0f, tauf) / (fabsf(tauf) + sqrtf(1.0f + tauf * tauf));
+                        const float cf = rsqrtf(1.0f + tf * tf);
+                        c = (double)cf;
+                        s = (double)(tf * cf);
+                        double f = 1.5 - 0.5 * (c * c + s * s);
+                        c *= f;
+                        s *= f;
+                        f = 1.5 - 0.5 * (c * c + s * s);
+                        c *= f;
+                        s *= f;
+                    } else {
+                        const double tau = diff / (2.0 * apq);
+                        const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+                        c = 1.0 / sqrt(1.0 + t * t);
+                        s = t * c;
+                    }
                     int slot = atomicAdd(&n_active, 1);
                     cs[slot] = c;
-                    sn[slot] = t * c;
+                    sn[slot] = s;
                     pp[slot] = p;
                     qq[slot] = q;
                 }
