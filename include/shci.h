@@ -141,7 +141,9 @@ int shci_sigma_noalloc(shci_ctx *ctx, int k, const double *c, double *sigma);
 /* Lowest k_roots (in [1, 8]) eigenpairs of H on V by diagonally
  * preconditioned Davidson (Sec. II.A).  Converged when, for every root, the
  * Ritz value moved by less than `tol` since the previous iteration and the
- * residual norm ||H x - theta x|| is below 0.1 * sqrt(tol).
+ * residual norm ||H x - theta x|| is below 0.1 * sqrt(tol).  A root that meets
+ * both conditions adds no further correction vector while the others
+ * converge (its Ritz value and residual are still checked every iteration).
  * guess: NULL (start from the unit vectors of the k_roots lowest H_ii) or
  * [k_roots][n_det] starting vectors (orthonormalised by the call), in
  * mem_space.  energies: host [k_roots], ascending.  vecs: [k_roots][n_det]
@@ -150,6 +152,17 @@ int shci_sigma_noalloc(shci_ctx *ctx, int k, const double *c, double *sigma);
  * max_iter iterations. */
 int shci_davidson(shci_ctx *ctx, int k_roots, double tol, int max_iter, const double *guess,
                   double *energies, double *vecs, int mem_space, int *iters_out);
+
+/* Convergence history of the last shci_davidson on this context (no paper
+ * counterpart; for reports such as the time to reach a given accuracy).
+ * Iteration it (0-based, < the returned count) has Ritz values
+ * theta[it * k_roots + l], residual norms rnorm[it * k_roots + l] and t_s[it],
+ * the host wall time in seconds from the call's entry to the moment those
+ * values were known on the host.  Host arrays of at least cap iterations; any
+ * may be NULL.  Writes min(cap, iterations) rows and *n_out = the number of
+ * iterations recorded (0 before any Davidson run).  SHCI_ERR_INVALID if
+ * cap < 0 or n_out is NULL. */
+int shci_davidson_history(shci_ctx *ctx, int cap, double *theta, double *rnorm, double *t_s, int *n_out);
 
 /* Adjoint of a variational eigenvalue (no counterpart in the paper, which
  * has no derivatives): for a normalised real eigenvector c of H on V,
@@ -201,6 +214,13 @@ typedef struct {
     int max_iters;             /* iterations of the slowest system */
     int graph;                 /* 1 if the solve ran as a captured CUDA graph */
     int grid_ctas;
+    /* last shci_batch_davidson: device time between consecutive grid barriers,
+     * summed over iterations, per phase: 0 start, 1 sigma (stored rows and
+     * alpha-grouped items), 2 sigma (beta-grouped items), 3 Gram columns,
+     * 4 eigensolver, 5 Ritz vectors and residuals, 6 convergence and restart
+     * decision, 7 basis rotation, 8 second-pass coefficients, 9 second
+     * projection, 10-12 Cholesky-QR, 13 next block, 14 bookkeeping */
+    double phase_ms[16];
 } shci_batch_stats_t;
 
 int shci_batch_create(shci_ctx *ctx, int n_sys, const shci_system_desc *systems, int mem_space,
@@ -229,13 +249,21 @@ typedef struct {
     int davidson_iters;
     int mode;                   /* SHCI_STORED or SHCI_ON_THE_FLY after a build */
     int n_words;                /* W */
+    /* last shci_davidson with phase timing on: device-timeline time per part
+     * (gaps while the host decides included in the part that follows):
+     * 0 start (guess, first product), 1 eigensolver, 2 Ritz vectors and
+     * residuals (with the read of the Ritz values), 3 restarts,
+     * 4 orthonormalisation, 5 sigma (with layout changes), 6 new Gram columns */
+    double davidson_phase_ms[8];
 } shci_stats_t;
 
 /* Fill *out.  Kernel times are recorded only while timing is enabled. */
 int shci_get_stats(shci_ctx *ctx, shci_stats_t *out);
 
-/* Enable (1) or disable (0) per-launch CUDA-event timing of the sigma
- * kernels, and reset the accumulated counters. */
+/* Timing switches (bit mask), and reset of the accumulated counters:
+ * bit 0: CUDA-event timing of every sigma launch (synchronises after each);
+ * bit 1: per-part timing of shci_davidson (events only, no extra
+ * synchronisation).  0 turns both off. */
 int shci_set_timing(shci_ctx *ctx, int enable);
 
 #ifdef __cplusplus

@@ -7,7 +7,8 @@ the library; the first call does, and fails loudly if it was not built.
 """
 from .binding import (  # noqa: F401
     EXPORTED, SHCI_AUTO, SHCI_MEM_DEVICE, SHCI_MEM_HOST, SHCI_ON_THE_FLY, SHCI_STORED, Context, ShciError,
-    load_library, shci_build_connectivity, shci_create, shci_davidson, shci_destroy, shci_get_diag,
+    load_library, shci_build_connectivity, shci_create, shci_davidson, shci_davidson_history, shci_destroy,
+    shci_get_diag,
     shci_get_pairs, shci_get_row, shci_get_stats, shci_last_error, shci_load_integrals, shci_set_timing, shci_sigma,
 )
 from .binding import shci_energy_backward, shci_sigma_noalloc  # noqa: F401

@@ -36,7 +36,8 @@ _STATUS = {1: "INVALID", 2: "OOM", 3: "CUDA", 4: "NOT_CONVERGED", 5: "TIMEOUT", 
 EXPORTED = [
     "shci_create", "shci_destroy", "shci_last_error", "shci_load_integrals", "shci_build_connectivity",
     "shci_get_diag", "shci_get_pairs", "shci_get_row", "shci_sigma", "shci_sigma_noalloc", "shci_energy_backward",
-    "shci_batch_create", "shci_batch_davidson", "shci_batch_get_stats", "shci_batch_destroy", "shci_davidson", "shci_get_stats", "shci_set_timing",
+    "shci_batch_create", "shci_batch_davidson", "shci_batch_get_stats", "shci_batch_destroy", "shci_davidson",
+    "shci_davidson_history", "shci_get_stats", "shci_set_timing",
 ]
 
 
@@ -52,7 +53,7 @@ class shci_stats_t(ctypes.Structure):
         ("n_beta_strings", ctypes.c_int64), ("n_alpha_singles", ctypes.c_int64), ("candidates", ctypes.c_int64),
         ("build_ms", ctypes.c_double), ("sigma_ms_total", ctypes.c_double), ("sigma_launches", ctypes.c_int64),
         ("sigma_vectors", ctypes.c_int64), ("kernel_launches", ctypes.c_int64), ("davidson_iters", ctypes.c_int),
-        ("mode", ctypes.c_int), ("n_words", ctypes.c_int),
+        ("mode", ctypes.c_int), ("n_words", ctypes.c_int), ("davidson_phase_ms", ctypes.c_double * 8),
     ]
 
 
@@ -70,7 +71,7 @@ class shci_batch_stats_t(ctypes.Structure):
         ("total_det", ctypes.c_int64), ("total_nnz_upper", ctypes.c_int64),
         ("tuned_rows_per_item", ctypes.c_int), ("tuned_ctas_per_sm", ctypes.c_int),
         ("tune_ms", ctypes.c_double), ("solve_ms", ctypes.c_double), ("max_iters", ctypes.c_int),
-        ("graph", ctypes.c_int), ("grid_ctas", ctypes.c_int),
+        ("graph", ctypes.c_int), ("grid_ctas", ctypes.c_int), ("phase_ms", ctypes.c_double * 16),
     ]
 
 
@@ -103,6 +104,7 @@ def load_library(path: str = LIB_PATH):
         "shci_batch_get_stats": (i32, [vp, ctypes.POINTER(shci_batch_stats_t)]),
         "shci_batch_destroy": (None, [vp]),
         "shci_davidson": (i32, [vp, i32, f64, i32, vp, vp, vp, i32, ctypes.POINTER(i32)]),
+        "shci_davidson_history": (i32, [vp, i32, vp, vp, vp, ctypes.POINTER(i32)]),
         "shci_get_stats": (i32, [vp, ctypes.POINTER(shci_stats_t)]),
         "shci_set_timing": (i32, [vp, i32]),
     }
@@ -252,6 +254,19 @@ def shci_davidson(ctx, k_roots, tol=1e-10, max_iter=200, guess=None, vecs=None, 
     return e, it.value, rc
 
 
+def shci_davidson_history(ctx, k_roots):
+    """Last Davidson run: (theta [iters, k], rnorm [iters, k], t_s [iters])."""
+    lib = load_library()
+    n = ctypes.c_int(0)
+    _check(ctx, lib.shci_davidson_history(ctx, 0, None, None, None, ctypes.byref(n)))
+    th = np.empty((n.value, k_roots), np.float64)
+    rn = np.empty((n.value, k_roots), np.float64)
+    ts = np.empty(n.value, np.float64)
+    _check(ctx, lib.shci_davidson_history(ctx, n.value, th.ctypes.data, rn.ctypes.data, ts.ctypes.data,
+                                          ctypes.byref(n)))
+    return th, rn, ts
+
+
 def shci_energy_backward(ctx, c, grad_out_scale, dE_dh, dE_deri_packed):
     """dE/dh and packed dE/d(pq|rs) for the normalised root c (Hellmann-Feynman)."""
     pc, mc, kc = _ptr(c, np.float64)
@@ -303,7 +318,9 @@ def shci_batch_get_stats(batch) -> dict:
     rc = load_library().shci_batch_get_stats(batch, ctypes.byref(s))
     if rc != SHCI_OK:
         raise ShciError(rc, "shci_batch_get_stats failed")
-    return {name: getattr(s, name) for name, _ in shci_batch_stats_t._fields_}
+    out = {name: getattr(s, name) for name, _ in shci_batch_stats_t._fields_}
+    out["phase_ms"] = list(s.phase_ms)
+    return out
 
 
 def shci_batch_destroy(batch):
@@ -313,11 +330,14 @@ def shci_batch_destroy(batch):
 def shci_get_stats(ctx) -> dict:
     s = shci_stats_t()
     _check(ctx, load_library().shci_get_stats(ctx, ctypes.byref(s)))
-    return {name: getattr(s, name) for name, _ in shci_stats_t._fields_}
+    out = {name: getattr(s, name) for name, _ in shci_stats_t._fields_}
+    out["davidson_phase_ms"] = list(s.davidson_phase_ms)
+    return out
 
 
-def shci_set_timing(ctx, enable: bool):
-    _check(ctx, load_library().shci_set_timing(ctx, 1 if enable else 0))
+def shci_set_timing(ctx, enable, davidson_phases=False):
+    """Bit 0: time every sigma launch; bit 1 (davidson_phases): time the parts of shci_davidson."""
+    _check(ctx, load_library().shci_set_timing(ctx, (1 if enable else 0) | (2 if davidson_phases else 0)))
 
 
 class Context:

@@ -198,6 +198,23 @@ int shci_davidson(shci_ctx *c, int k, double tol, int max_iter, const double *gu
     return guarded(c, [&] { return shci::davidson(c, k, tol, max_iter, guess, energies, vecs, mem, iters_out); });
 }
 
+int shci_davidson_history(shci_ctx *c, int cap, double *theta, double *rnorm, double *t_s, int *n_out) {
+    return guarded(c, [&] {
+        if (cap < 0 || !n_out) throw ShciError{SHCI_ERR_INVALID, "cap must be >= 0 and n_out non-null"};
+        const int n = (int)c->hist_t.size(), k = c->hist_k;
+        const int w = std::min(cap, n);
+        for (int it = 0; it < w; it++) {
+            if (t_s) t_s[it] = c->hist_t[it];
+            for (int l = 0; l < k; l++) {
+                if (theta) theta[it * k + l] = c->hist_theta[(size_t)it * k + l];
+                if (rnorm) rnorm[it * k + l] = c->hist_rn[(size_t)it * k + l];
+            }
+        }
+        *n_out = n;
+        return SHCI_OK;
+    });
+}
+
 int shci_get_stats(shci_ctx *c, shci_stats_t *out) {
     return guarded(c, [&] {
         if (!out) throw ShciError{SHCI_ERR_INVALID, "null pointer"};
@@ -218,7 +235,8 @@ int shci_get_stats(shci_ctx *c, shci_stats_t *out) {
 
 int shci_set_timing(shci_ctx *c, int enable) {
     return guarded(c, [&] {
-        c->timing = enable != 0;
+        c->timing = (enable & 1) != 0;
+        c->timing_dav = (enable & 2) != 0;
         c->stats.sigma_ms_total = 0.0;
         c->stats.sigma_launches = 0;
         c->stats.sigma_vectors = 0;

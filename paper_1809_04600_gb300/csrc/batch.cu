@@ -65,11 +65,15 @@ struct BState {
     double theta[BK], theta_old[BK], rn[BK];
 };
 
+constexpr int N_PHASES = 16;
+
 struct BarrierState {
     unsigned count;
     unsigned gen;
     int err;
     int work;
+    unsigned long long t_last;             // block 0: global time at the last barrier exit
+    unsigned long long phase_ns[N_PHASES]; // block 0: time between barriers, per phase
 };
 
 struct BatchArgs {
@@ -93,7 +97,15 @@ struct BatchArgs {
 
 // ---------------------------------------------------------------- barrier and helpers
 
-__device__ bool grid_sync(BarrierState *b) {
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Grid-wide barrier; `phase` names the phase that ends here (block 0 adds
+// the time since the previous barrier to that phase's total).
+__device__ bool grid_sync(BarrierState *b, int phase) {
     __shared__ int ok;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -121,6 +133,11 @@ __device__ bool grid_sync(BarrierState *b) {
                 }
             }
             __threadfence();
+        }
+        if (blockIdx.x == 0) {
+            const unsigned long long now = global_ns();
+            b->phase_ns[phase] += now - b->t_last;
+            b->t_last = now;
         }
         ok = good;
     }
@@ -197,16 +214,36 @@ __device__ void sigma_rows(const BSys &S, int nb, int64_t r0, int cnt) {
     for (int64_t i = r0 + warp; i < r0 + cnt && i < S.n; i += BT / 32) {
         double acc[BK] = {0.0, 0.0, 0.0, 0.0};
         const int64_t beg = S.rowptr[i], end = S.rowptr[i + 1];
-        for (int64_t p = beg + lane; p < end; p += 32) {
-            const int64_t j = __ldg(&S.col[p]);
-            const double v = __ldg(&S.val[p]);
-            const double2 x01 = __ldcg(reinterpret_cast<const double2 *>(S.X) + 2 * j);
-            acc[0] = fma(v, x01.x, acc[0]);
-            if (nb > 1) acc[1] = fma(v, x01.y, acc[1]);
-            if (nb > 2) {
-                const double2 x23 = __ldcg(reinterpret_cast<const double2 *>(S.X) + 2 * j + 1);
-                acc[2] = fma(v, x23.x, acc[2]);
-                if (nb > 3) acc[3] = fma(v, x23.y, acc[3]);
+        // SR nonzeros per lane per step, all loads issued before the FMAs: the
+        // persistent grid has few warps per SM, so each warp keeps several
+        // gathers of X in flight
+        constexpr int SR = 4;
+        for (int64_t p0 = beg + lane; p0 < end; p0 += 32 * SR) {
+            int32_t j[SR];
+            double v[SR];
+            double2 x01[SR], x23[SR];
+#pragma unroll
+            for (int u = 0; u < SR; u++) {
+                const int64_t p = p0 + 32 * u;
+                j[u] = p < end ? __ldg(&S.col[p]) : -1;
+                v[u] = p < end ? __ldg(&S.val[p]) : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < SR; u++) {
+                x01[u] = j[u] >= 0 ? __ldcg(reinterpret_cast<const double2 *>(S.X) + 2 * (int64_t)j[u])
+                                   : make_double2(0.0, 0.0);
+                x23[u] = (nb > 2 && j[u] >= 0)
+                             ? __ldcg(reinterpret_cast<const double2 *>(S.X) + 2 * (int64_t)j[u] + 1)
+                             : make_double2(0.0, 0.0);
+            }
+#pragma unroll
+            for (int u = 0; u < SR; u++) {
+                acc[0] = fma(v[u], x01[u].x, acc[0]);
+                if (nb > 1) acc[1] = fma(v[u], x01[u].y, acc[1]);
+                if (nb > 2) {
+                    acc[2] = fma(v[u], x23[u].x, acc[2]);
+                    if (nb > 3) acc[3] = fma(v[u], x23[u].y, acc[3]);
+                }
             }
         }
 #pragma unroll
@@ -225,7 +262,7 @@ __device__ void sigma_rows(const BSys &S, int nb, int64_t r0, int cnt) {
 
 // ---------------------------------------------------------------- the persistent kernel
 
-__global__ void __launch_bounds__(BT, 2) k_batch_davidson(BatchArgs B) {
+__global__ void __launch_bounds__(BT, 3) k_batch_davidson(BatchArgs B) {
     extern __shared__ double smem[];
     EnumSmem<1> &es = *reinterpret_cast<EnumSmem<1> *>(smem);
     double *sh = smem;                       // small-matrix scratch (phases never overlap)
@@ -236,6 +273,7 @@ __global__ void __launch_bounds__(BT, 2) k_batch_davidson(BatchArgs B) {
     __shared__ int64_t bi[BT / 32];
     const int tid = threadIdx.x;
 
+    if (blockIdx.x == 0 && tid == 0) B.bar->t_last = global_ns();
     // ---- init: unit vectors on the k lowest diagonal entries of each system
     for (int s = blockIdx.x; s < B.S; s += gridDim.x) {
         const BSys &S = B.sys[s];
@@ -287,7 +325,7 @@ __global__ void __launch_bounds__(BT, 2) k_batch_davidson(BatchArgs B) {
         }
         __syncthreads();
     }
-    if (!grid_sync(B.bar)) return;
+    if (!grid_sync(B.bar, 0)) return;
 
     for (int it = 0; it < B.max_iter; it++) {
         // ---- A1: sigma for stored rows and alpha-grouped on-the-fly items
@@ -311,7 +349,7 @@ __global__ void __launch_bounds__(BT, 2) k_batch_davidson(BatchArgs B) {
                 enum_alpha_item<1, ENUM_SIGMA, BK>(A, S.I, B.a1_local[item], es.T, es.Q[tid >> 5], cand);
             }
         }
-        if (!grid_sync(B.bar)) return;
+        if (!grid_sync(B.bar, 1)) return;
         // ---- A2: beta-grouped on-the-fly items (adds the same-spin-alpha part)
         while (true) {
             const int item = next_item(B.bar);
@@ -332,7 +370,7 @@ __global__ void __launch_bounds__(BT, 2) k_batch_davidson(BatchArgs B) {
             unsigned long long cand = 0;
             enum_beta_item<1, ENUM_SIGMA, BK>(A, S.I, B.a2_local[item], es.T, es.Q[tid >> 5], cand);
         }
-        if (!grid_sync(B.bar)) return;
+        if (!grid_sync(B.bar, 2)) return;
 
         // ---- B: AV[m + q] = Y[:, q]; partial Gram columns V[a] . Y[:, q], a < m + nb
         for (int64_t item = blockIdx.x; item < B.n_v; item += gridDim.x) {
@@ -353,7 +391,7 @@ __global__ void __launch_bounds__(BT, 2) k_batch_davidson(BatchArgs B) {
             };
             slice_gram(B.partial + item * PSTRIDE, V, S.n, m + nb, i0, i1, loadY, red);
         }
-        if (!grid_sync(B.bar)) return;
+        if (!grid_sync(B.bar, 3)) return;
 
         // ---- C: per system: new G columns, subspace eigen-decomposition
         for (int s = blockIdx.x; s < B.S; s += gridDim.x) {
@@ -377,7 +415,7 @@ __global__ void __launch_bounds__(BT, 2) k_batch_davidson(BatchArgs B) {
             }
             __syncthreads();
         }
-        if (!grid_sync(B.bar)) return;
+        if (!grid_sync(B.bar, 4)) return;
 
         // ---- D: Ritz vectors, residuals and corrections T[l] = r_l / (theta_l - H_ii);
         //         partials |r_l|^2, S0 = T^T T, C = V^T T
@@ -436,7 +474,7 @@ __global__ void __launch_bounds__(BT, 2) k_batch_davidson(BatchArgs B) {
             };
             slice_gram(part, V, S.n, m, i0, i1, loadT, red);
         }
-        if (!grid_sync(B.bar)) return;
+        if (!grid_sync(B.bar, 5)) return;
 
         // ---- E: per system: convergence, restart decision, coefficients of the kept corrections
         for (int s = blockIdx.x; s < B.S; s += gridDim.x) {
@@ -458,7 +496,8 @@ __global__ void __launch_bounds__(BT, 2) k_batch_davidson(BatchArgs B) {
                     st.rn[l] = sqrt(fmax(0.0, rn2[l]));
                     const bool cl = fabs(st.theta[l] - st.theta_old[l]) < S.tol && st.rn[l] < S.res_tol;
                     conv = conv && cl;
-                    if (st.rn[l] >= S.res_tol * 1e-3) st.todo[ntodo++] = l;
+                    // a converged root is locked: no new direction for it
+                    if (!cl && st.rn[l] >= S.res_tol * 1e-3) st.todo[ntodo++] = l;
                 }
                 for (int l = 0; l < k; l++) st.theta_old[l] = st.theta[l];
                 st.it = st.it + 1;
@@ -510,7 +549,7 @@ __global__ void __launch_bounds__(BT, 2) k_batch_davidson(BatchArgs B) {
             if (tid < BK) S.coefS0[tid] = tid < ntodo ? S0[st.todo[tid] * BK + st.todo[tid]] : 1.0;
             __syncthreads();
         }
-        if (!grid_sync(B.bar)) return;
+        if (!grid_sync(B.bar, 6)) return;
         {
             int any = 0;
             for (int s = 0; s < B.S; s++) any |= ldi(&B.st[s].active);
@@ -574,7 +613,7 @@ __global__ void __launch_bounds__(BT, 2) k_batch_davidson(BatchArgs B) {
             };
             slice_gram(B.partial + item * PSTRIDE, Vp, S.n, m, i0, i1, loadT2, red);
         }
-        if (!grid_sync(B.bar)) return;
+        if (!grid_sync(B.bar, 7)) return;
 
         // ---- G: per system: switch to the rotated buffers; second-pass coefficients
         for (int s = blockIdx.x; s < B.S; s += gridDim.x) {
@@ -590,7 +629,7 @@ __global__ void __launch_bounds__(BT, 2) k_batch_davidson(BatchArgs B) {
             }
             __syncthreads();
         }
-        if (!grid_sync(B.bar)) return;
+        if (!grid_sync(B.bar, 8)) return;
 
         // ---- H: second projection T2 -= V C2; partial S = T2^T T2
         for (int64_t item = blockIdx.x; item < B.n_v; item += gridDim.x) {
@@ -625,7 +664,7 @@ __global__ void __launch_bounds__(BT, 2) k_batch_davidson(BatchArgs B) {
             }
             item_reduce<BK * BK>(B.partial + item * PSTRIDE, s2, BK * BK, red);
         }
-        if (!grid_sync(B.bar)) return;
+        if (!grid_sync(B.bar, 9)) return;
 
         // ---- I: per system: Cholesky-QR coefficients, pass 1 (dependence test
         //         against the norms before projection)
@@ -639,7 +678,7 @@ __global__ void __launch_bounds__(BT, 2) k_batch_davidson(BatchArgs B) {
             if (tid == 0) st.cnt1 = cholqr_coef(S.coefS, nt, S.coefS0, 1e-20, S.coefM);
             __syncthreads();
         }
-        if (!grid_sync(B.bar)) return;
+        if (!grid_sync(B.bar, 10)) return;
 
         // ---- J: T = T2 M (zero past cnt1); partial S = T^T T
         for (int64_t item = blockIdx.x; item < B.n_v; item += gridDim.x) {
@@ -674,7 +713,7 @@ __global__ void __launch_bounds__(BT, 2) k_batch_davidson(BatchArgs B) {
             }
             item_reduce<BK * BK>(B.partial + item * PSTRIDE, s2, BK * BK, red);
         }
-        if (!grid_sync(B.bar)) return;
+        if (!grid_sync(B.bar, 11)) return;
 
         // ---- K: per system: Cholesky-QR coefficients, pass 2
         for (int s = blockIdx.x; s < B.S; s += gridDim.x) {
@@ -690,7 +729,7 @@ __global__ void __launch_bounds__(BT, 2) k_batch_davidson(BatchArgs B) {
             }
             __syncthreads();
         }
-        if (!grid_sync(B.bar)) return;
+        if (!grid_sync(B.bar, 12)) return;
 
         // ---- L: new basis vectors V[m + l] = T M2 (l < cnt2) and the next sigma input X
         for (int64_t item = blockIdx.x; item < B.n_v; item += gridDim.x) {
@@ -721,7 +760,7 @@ __global__ void __launch_bounds__(BT, 2) k_batch_davidson(BatchArgs B) {
             }
             __syncthreads();
         }
-        if (!grid_sync(B.bar)) return;
+        if (!grid_sync(B.bar, 13)) return;
 
         // ---- M: per system: the new block is ready for the next sigma
         if (tid == 0)
@@ -731,7 +770,7 @@ __global__ void __launch_bounds__(BT, 2) k_batch_davidson(BatchArgs B) {
                 st.nb = st.cnt2;
                 if (st.cnt2 == 0) st.active = 0;     // no new direction: this system stops here
             }
-        if (!grid_sync(B.bar)) return;
+        if (!grid_sync(B.bar, 14)) return;
     }
 }
 
@@ -973,7 +1012,7 @@ void prepare_davidson(shci_batch *b, int k, double tol) {
 // timing a few iterations of the real kernel for each candidate
 void autotune(shci_batch *b) {
     const int rows_c[3] = {64, 256, 1024};
-    const int bps_c[2] = {1, 2};
+    const int bps_c[3] = {1, 2, 3};
     double best = INFINITY;
     int best_rows = b->srows, best_bps = b->blocks_per_sm;
     for (int r : rows_c)
@@ -1118,6 +1157,7 @@ int shci_batch_davidson(shci_batch *b, int k_roots, double tol, int max_iter, do
             max_it = std::max(max_it, hs[s].it);
         }
         b->stats.solve_ms = ms;
+        for (int ph = 0; ph < 16; ph++) b->stats.phase_ms[ph] = ph < shci::N_PHASES ? bar.phase_ns[ph] * 1e-6 : 0.0;
         b->stats.max_iters = max_it;
         b->stats.graph = b->graph_ok ? 1 : 0;
         b->stats.grid_ctas = b->grid;

@@ -81,9 +81,12 @@ struct shci_ctx {
     double stored_budget = -1.0;
 
     // measurements
-    bool timing = false;
+    bool timing = false;                   // sigma launches
+    bool timing_dav = false;               // parts of shci_davidson
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     shci_stats_t stats{};
+    std::vector<double> hist_theta, hist_rn, hist_t;   // last Davidson: per iteration
+    int hist_k = 0;
     int64_t candidates = 0;
     int64_t n_alpha_singles = 0;
 };

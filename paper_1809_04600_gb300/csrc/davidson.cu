@@ -10,6 +10,7 @@
 // the number of accepted new vectors).
 #include <algorithm>
 #include <atomic>
+#include <chrono>
 #include <cmath>
 
 #include "context.cuh"
@@ -364,8 +365,44 @@ __global__ void k_second_pass_flag(const double *__restrict__ S, int kb, const d
         default: throw ShciError{SHCI_ERR_INVALID, "block size out of range"}; \
     }
 
+// Per-part device timeline of one Davidson run: an event after each part;
+// the time between consecutive events goes to the part that ended.
+struct PartTimer {
+    bool on = false;
+    cudaStream_t st = nullptr;
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> part;
+    void mark(int p) {
+        if (!on) return;
+        cudaEvent_t e;
+        CUDA_TRY(cudaEventCreate(&e));
+        CUDA_TRY(cudaEventRecord(e, st));
+        ev.push_back(e);
+        part.push_back(p);
+    }
+    void finish(double *out, int n_parts) {
+        if (!on || ev.empty()) return;
+        for (int p = 0; p < n_parts; p++) out[p] = 0.0;
+        CUDA_TRY(cudaEventSynchronize(ev.back()));
+        for (size_t x = 1; x < ev.size(); x++) {
+            float ms = 0.f;
+            CUDA_TRY(cudaEventElapsedTime(&ms, ev[x - 1], ev[x]));
+            if (part[x] >= 0 && part[x] < n_parts) out[part[x]] += ms;
+        }
+        for (auto e : ev) cudaEventDestroy(e);
+        ev.clear();
+        part.clear();
+    }
+    ~PartTimer() {
+        for (auto e : ev) cudaEventDestroy(e);
+    }
+};
+
+enum { DP_START = 0, DP_EIG = 1, DP_RITZ = 2, DP_RESTART = 3, DP_ORTHO = 4, DP_SIGMA = 5, DP_GRAM = 6 };
+
 struct Dav {
     shci_ctx *c;
+    PartTimer *pt = nullptr;
     int64_t n;
     int k, m_max, keep;
     int vec_blocks, n_slots;
@@ -466,7 +503,9 @@ struct Dav {
         k_unpack<<<vec_blocks, DV_THREADS, 0, st>>>(c->dw.Y.p, kb, n, AVr(m0));
         KERNEL_CHECK();
         g_kernel_launches += 2;
+        if (pt) pt->mark(m0 == 0 ? DP_START : DP_SIGMA);
         gram(c->dw.V.p, m0 + kb, AVr(m0), kb, c->dw.G.p, m_max, 0, m0, true);
+        if (pt) pt->mark(m0 == 0 ? DP_START : DP_GRAM);
     }
 
     void ritz_residuals(int m, double *T, double *d_rn) {
@@ -503,12 +542,18 @@ int davidson(shci_ctx *c, int k, double tol, int max_iter, const double *guess, 
     if (max_iter < 1) throw ShciError{SHCI_ERR_INVALID, "max_iter must be >= 1"};
     if (!energies) throw ShciError{SHCI_ERR_INVALID, "energies must not be NULL"};
     if (mem != SHCI_MEM_HOST && mem != SHCI_MEM_DEVICE) throw ShciError{SHCI_ERR_INVALID, "unknown mem_space"};
+    const auto t_entry = std::chrono::steady_clock::now();
     static bool jacobi_attr = false;
     if (!jacobi_attr) {
         CUDA_TRY(cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)JACOBI_SMEM));
         jacobi_attr = true;
     }
     Dav d;
+    PartTimer timer;
+    timer.on = c->timing_dav;
+    timer.st = c->st;
+    timer.mark(-1);
+    d.pt = &timer;
     d.c = c;
     d.n = c->n_det;
     d.k = k;
@@ -574,6 +619,10 @@ int davidson(shci_ctx *c, int k, double tol, int max_iter, const double *guess, 
     d.expand(0, m);
 
     std::vector<double> theta_old(k, INFINITY), status(2 * SHCI_MAX_K);
+    c->hist_theta.clear();
+    c->hist_rn.clear();
+    c->hist_t.clear();
+    c->hist_k = k;
     int it = 0;
     int m_eig = 0;          // size of the leading block whose eigenvectors are in evec
     bool conv = false;
@@ -582,19 +631,25 @@ int davidson(shci_ctx *c, int k, double tol, int max_iter, const double *guess, 
         k_jacobi<<<1, 256, JACOBI_SMEM, st>>>(w.G.p, d.m_max, m, m_eig, w.eval.p, w.evec.p);
         KERNEL_CHECK();
         g_kernel_launches += 1;
+        timer.mark(DP_EIG);
         m_eig = m;
         d.ritz_residuals(m, T, d_rn);
         CUDA_TRY(cudaMemcpyAsync(status.data(), w.eval.p, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
         CUDA_TRY(cudaMemcpyAsync(status.data() + SHCI_MAX_K, d_rn, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
         CUDA_TRY(cudaStreamSynchronize(st));
+        timer.mark(DP_RITZ);
+        c->hist_t.push_back(std::chrono::duration<double>(std::chrono::steady_clock::now() - t_entry).count());
         conv = true;
         std::vector<int> todo;
         for (int l = 0; l < k; l++) {
             theta[l] = status[l];
             rnorm[l] = std::sqrt(std::max(0.0, status[SHCI_MAX_K + l]));
+            c->hist_theta.push_back(theta[l]);
+            c->hist_rn.push_back(rnorm[l]);
             bool cl = std::fabs(theta[l] - theta_old[l]) < tol && rnorm[l] < res_tol;
             conv = conv && cl;
-            if (rnorm[l] >= res_tol * 1e-3) todo.push_back(l);
+            // a converged root is locked: no new direction for it
+            if (!cl && rnorm[l] >= res_tol * 1e-3) todo.push_back(l);
         }
         theta_old = theta;
         if (conv || it == max_iter) break;
@@ -613,6 +668,7 @@ int davidson(shci_ctx *c, int k, double tol, int max_iter, const double *guess, 
             m = keep;
             m_eig = 0;
             // the residual corrections in T[0..k) are still valid: they depend only on the Ritz pairs
+            timer.mark(DP_RESTART);
         }
         // corrections for the roots that are not yet converged
         int kb = 0;
@@ -625,6 +681,7 @@ int davidson(shci_ctx *c, int k, double tol, int max_iter, const double *guess, 
         kb = std::min(kb, d.m_max - m);              // never grow past the subspace buffers
         if (kb <= 0) break;
         int added = d.orthonormalize_append(T, kb, m);
+        timer.mark(DP_ORTHO);
         if (added == 0) break;
         d.expand(m, added);
         m += added;
@@ -640,6 +697,7 @@ int davidson(shci_ctx *c, int k, double tol, int max_iter, const double *guess, 
                                  mem == SHCI_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
     }
     CUDA_TRY(cudaStreamSynchronize(st));
+    timer.finish(c->stats.davidson_phase_ms, 8);
     return conv ? SHCI_OK : SHCI_ERR_NOT_CONVERGED;
 }
 

@@ -461,25 +461,46 @@ __device__ __forceinline__ void enum_alpha_item(const EnumArgs &A, const DevInts
                     ctx = (pq_a << 2) | ((neg_a & 1) << 1) | 1;
                 }
                 const unsigned long long *row = A.occ + (int64_t)k * A.occ_words;
+                const int64_t k_off = A.ga_off[k];
                 cand_local += lane == 0 ? sb_len : 0;
-                for (int y0 = 0; y0 < sb_len; y0 += 32) {
-                    const int y = y0 + lane;
-                    bool match = false;
-                    int32_t j = 0;
-                    Str<W> Bj{};
-                    if (y < sb_len) {
-                        const int kb = A.bs_idx[sb_beg + y];
-                        const unsigned long long word = __ldg(&row[kb >> 6]);
-                        const unsigned long long below = word & ((1ull << (kb & 63)) - 1ull);
-                        match = (word >> (kb & 63)) & 1ull;
-                        if (match && NEED_DET) {
-                            const int64_t m = A.ga_off[k] + __ldg(&A.occ_pref[(int64_t)k * A.occ_words + (kb >> 6)]) +
-                                              __popcll(below);
-                            j = A.ga_det[m];
-                            Bj = load_str<W>(A.ga_str, m);
+                // LU lookups per lane per step, each stage's loads issued together
+                // (independent L2 gathers in flight instead of one dependent chain)
+                constexpr int LU = W == 1 ? 4 : 2;
+                for (int y0 = 0; y0 < sb_len; y0 += 32 * LU) {
+                    int kb[LU];
+                    unsigned long long word[LU];
+                    bool match[LU];
+                    int32_t j[LU];
+                    Str<W> Bj[LU];
+#pragma unroll
+                    for (int u = 0; u < LU; u++) {
+                        const int y = y0 + 32 * u + lane;
+                        kb[u] = y < sb_len ? __ldg(&A.bs_idx[sb_beg + y]) : -1;
+                    }
+#pragma unroll
+                    for (int u = 0; u < LU; u++) word[u] = kb[u] >= 0 ? __ldg(&row[kb[u] >> 6]) : 0ull;
+#pragma unroll
+                    for (int u = 0; u < LU; u++) {
+                        match[u] = kb[u] >= 0 && ((word[u] >> (kb[u] & 63)) & 1ull);
+                        j[u] = 0;
+                        Bj[u] = Str<W>{};
+                    }
+                    if (NEED_DET) {
+                        int64_t m[LU];
+#pragma unroll
+                        for (int u = 0; u < LU; u++)
+                            m[u] = match[u] ? __ldg(&A.occ_pref[(int64_t)k * A.occ_words + (kb[u] >> 6)]) : 0;
+#pragma unroll
+                        for (int u = 0; u < LU; u++) {
+                            if (match[u]) {
+                                m[u] += k_off + __popcll(word[u] & ((1ull << (kb[u] & 63)) - 1ull));
+                                j[u] = __ldg(&A.ga_det[m[u]]);
+                                Bj[u] = load_str<W>(A.ga_str, m[u]);
+                            }
                         }
                     }
-                    emit<W, MODE, K>(R, A, I, Q, Bi, Ai, match, j, Bj, ctx);
+#pragma unroll
+                    for (int u = 0; u < LU; u++) emit<W, MODE, K>(R, A, I, Q, Bi, Ai, match[u], j[u], Bj[u], ctx);
                 }
             }
         }

@@ -51,26 +51,24 @@ __device__ __forceinline__ int cholqr_coef(const double *S, int kb, const double
 // m_prev x m_prev block from the previous call (G only grew since), so in
 // the basis blockdiag(evec, I) the leading block is diag(eval) and only the
 // new border has to be transformed.  Rotations whose off-diagonal element is
-// below 1e-14 (|a_pp| + |a_qq|) are skipped, and only the active pairs are
-// applied; sweeps stop when one applies no rotation.  Output: eigenvalues
-// (the converged diagonal) ascending and
-// eigenvectors as columns, evec[l * ld + a] = component a of vector l.
-__device__ __forceinline__ void jacobi_solve(const double *__restrict__ G, int ld, int m, int m_prev,
+// below 1e-14 (|a_pp| + |a_qq|) become the identity, a round with none active
+// is skipped, and sweeps stop when one applies no rotation.  A round applies
+// all of its rotations in one pass (two barriers per round).  Output:
+// eigenvalues (the converged diagonal) ascending and eigenvectors as columns,
+// evec[l * ld + a] = component a of vector l.
+__device__ __forceinline__ void jacobi_solve(const double *G, int ld, int m, int m_prev,
                                              double *__restrict__ eval, double *__restrict__ evec, double *jsm) {
     double (*A)[SHCI_MAX_SUB + 1] = reinterpret_cast<double (*)[SHCI_MAX_SUB + 1]>(jsm);
     double (*Q)[SHCI_MAX_SUB + 1] = reinterpret_cast<double (*)[SHCI_MAX_SUB + 1]>(jsm + SHCI_MAX_SUB * (SHCI_MAX_SUB + 1));
-    double *Gs = jsm + 2 * SHCI_MAX_SUB * (SHCI_MAX_SUB + 1);          // exact G, m x m (stride m)
     __shared__ double cs[SHCI_MAX_SUB / 2], sn[SHCI_MAX_SUB / 2];
     __shared__ int pp[SHCI_MAX_SUB / 2], qq[SHCI_MAX_SUB / 2];
-    __shared__ int n_active, any_rot;
     __shared__ double lam[SHCI_MAX_SUB];
     const int mm = (m + 1) & ~1;
     const int tid = threadIdx.x, nt = blockDim.x;
     const int mp = (m_prev > 0 && m_prev <= m) ? m_prev : 0;
-    for (int e = tid; e < m * m; e += nt) {
-        int r = e / m, c = e % m;
-        Gs[e] = 0.5 * (G[r * ld + c] + G[c * ld + r]);
-    }
+    // G is read symmetrised, (G + G^T) / 2, from L2 (ld.global.cg: the caller may
+    // have written it earlier in the same kernel)
+    auto gs = [&](int r, int c) { return 0.5 * (__ldcg(&G[r * ld + c]) + __ldcg(&G[c * ld + r])); };
     // Q = blockdiag(previous eigenvectors, I)
     for (int e = tid; e < mm * mm; e += nt) {
         int r = e / mm, c = e % mm;
@@ -87,11 +85,11 @@ __device__ __forceinline__ void jacobi_solve(const double *__restrict__ G, int l
             if (r < mp && c < mp) {
                 v = (r == c) ? eval[r] : 0.0;
             } else if (r < mp) {          // (Q^T G)[r][c] for border column c
-                for (int s = 0; s < mp; s++) v = fma(Q[s][r], Gs[s * m + c], v);
+                for (int s = 0; s < mp; s++) v = fma(Q[s][r], gs(s, c), v);
             } else if (c < mp) {
-                for (int s = 0; s < mp; s++) v = fma(Q[s][c], Gs[r * m + s], v);
+                for (int s = 0; s < mp; s++) v = fma(Q[s][c], gs(r, s), v);
             } else {
-                v = Gs[r * m + c];
+                v = gs(r, c);
             }
         }
         A[r][c] = v;
@@ -108,21 +106,22 @@ __device__ __forceinline__ void jacobi_solve(const double *__restrict__ G, int l
         A[m][m] = 2.0 * bound + 1.0;
     }
     __syncthreads();
+    const int half = mm / 2;
     for (int sweep = 0; sweep < 30; sweep++) {
-        if (tid == 0) any_rot = 0;
-        __syncthreads();
+        int swept = 0;
         for (int round = 0; round < mm - 1; round++) {
-            if (tid == 0) n_active = 0;
-            __syncthreads();
-            if (tid < mm / 2) {
+            // the round's mm/2 disjoint pairs; an inactive pair gets the identity
+            int active = 0;
+            if (tid < half) {
                 int x = tid, y = mm - 1 - tid;
                 int p = x == 0 ? 0 : ((x - 1 + round) % (mm - 1)) + 1;
                 int q = y == 0 ? 0 : ((y - 1 + round) % (mm - 1)) + 1;
                 if (p > q) { int t = p; p = q; q = t; }
                 const double apq = A[p][q];
+                double c = 1.0, s = 0.0;
                 if (fabs(apq) > 1e-14 * (fabs(A[p][p]) + fabs(A[q][q])) + 1e-300) {
+                    active = 1;
                     const double diff = A[q][q] - A[p][p];
-                    double c, s;
                     const float tauf = (float)diff / (2.0f * (float)apq);
                     if (fabs(apq) > 1e-30 && isfinite(tauf)) {
                         // rotation angle in FP32 (the FP64 divide and square root are
@@ -146,46 +145,41 @@ __device__ __forceinline__ void jacobi_solve(const double *__restrict__ G, int l
                         c = 1.0 / sqrt(1.0 + t * t);
                         s = t * c;
                     }
-                    int slot = atomicAdd(&n_active, 1);
-                    cs[slot] = c;
-                    sn[slot] = s;
-                    pp[slot] = p;
-                    qq[slot] = q;
                 }
+                cs[tid] = c;
+                sn[tid] = s;
+                pp[tid] = p;
+                qq[tid] = q;
             }
-            __syncthreads();
-            const int na = n_active;
-            __syncthreads();             // every thread has read n_active before it is reset
-            if (na == 0) continue;       // uniform: every thread read the same count
-            if (tid == 0) any_rot = 1;
-            // rows: A <- J^T A
-            for (int e = tid; e < na * mm; e += nt) {
-                int t = e / mm, j = e % mm;
-                int p = pp[t], q = qq[t];
-                double c = cs[t], s = sn[t];
-                double ap = A[p][j], aq = A[q][j];
-                A[p][j] = c * ap - s * aq;
-                A[q][j] = s * ap + c * aq;
+            if (!__syncthreads_or(active)) continue;     // uniform: every thread got the same answer
+            swept = 1;
+            // A <- J^T A J in one pass: the rotations are disjoint, so the 2 x 2 block
+            // of rows {p_t, q_t} and columns {p_u, q_u} depends only on itself and on
+            // rotations t and u
+            for (int e = tid; e < half * half; e += nt) {
+                const int t = e / half, u = e - t * half;
+                const int p = pp[t], q = qq[t], r = pp[u], v = qq[u];
+                const double ct = cs[t], st = sn[t], cu = cs[u], su = sn[u];
+                const double apr = A[p][r], apv = A[p][v], aqr = A[q][r], aqv = A[q][v];
+                const double bpr = ct * apr - st * aqr, bpv = ct * apv - st * aqv;   // rows
+                const double bqr = st * apr + ct * aqr, bqv = st * apv + ct * aqv;
+                A[p][r] = cu * bpr - su * bpv;                                      // columns
+                A[p][v] = su * bpr + cu * bpv;
+                A[q][r] = cu * bqr - su * bqv;
+                A[q][v] = su * bqr + cu * bqv;
             }
-            __syncthreads();
-            // columns: A <- A J, Q <- Q J
-            for (int e = tid; e < na * mm; e += nt) {
-                int t = e / mm, i = e % mm;
-                int p = pp[t], q = qq[t];
-                double c = cs[t], s = sn[t];
-                double ap = A[i][p], aq = A[i][q];
-                A[i][p] = c * ap - s * aq;
-                A[i][q] = s * ap + c * aq;
-                double qp = Q[i][p], qv = Q[i][q];
+            // Q <- Q J
+            for (int e = tid; e < mm * half; e += nt) {
+                const int i = e / half, t = e - i * half;
+                const int p = pp[t], q = qq[t];
+                const double c = cs[t], s = sn[t];
+                const double qp = Q[i][p], qv = Q[i][q];
                 Q[i][p] = c * qp - s * qv;
                 Q[i][q] = s * qp + c * qv;
             }
             __syncthreads();
         }
-        __syncthreads();
-        const int rot = any_rot;
-        __syncthreads();                 // every thread has read any_rot before it is reset
-        if (!rot) break;
+        if (!swept) break;               // uniform
     }
     for (int a = tid; a < mm; a += nt) lam[a] = A[a][a];
     __syncthreads();
@@ -204,6 +198,6 @@ __device__ __forceinline__ void jacobi_solve(const double *__restrict__ G, int l
     }
 }
 
-constexpr size_t JACOBI_SMEM = sizeof(double) * (2 * SHCI_MAX_SUB * (SHCI_MAX_SUB + 1) + SHCI_MAX_SUB * SHCI_MAX_SUB);
+constexpr size_t JACOBI_SMEM = sizeof(double) * (2 * SHCI_MAX_SUB * (SHCI_MAX_SUB + 1));
 
 }  // namespace shci

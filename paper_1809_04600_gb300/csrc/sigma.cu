@@ -15,13 +15,17 @@ namespace shci {
 
 constexpr int SIGMA_THREADS = 256;
 
-// One warp per row.  x and y are [n][K] (INTER) or [K][n].
+// One warp per row.  x and y are [n][K] (INTER) or [K][n].  Each lane takes
+// SR nonzeros per step and issues all their loads before the FMAs (more
+// gathers of x in flight per warp); a lane still accumulates its nonzeros in
+// ascending order.
 template <int K, bool INTER>
 __global__ void __launch_bounds__(SIGMA_THREADS) k_sigma_stored(int64_t n, const int64_t *__restrict__ rowptr,
                                                                 const int32_t *__restrict__ col,
                                                                 const double *__restrict__ val,
                                                                 const double *__restrict__ diag,
                                                                 const double *__restrict__ x, double *__restrict__ y) {
+    constexpr int SR = K <= 2 ? 4 : 2;
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (SIGMA_THREADS / 32);
     for (int64_t i = ((int64_t)blockIdx.x * SIGMA_THREADS + threadIdx.x) >> 5; i < n; i += warps) {
@@ -29,21 +33,38 @@ __global__ void __launch_bounds__(SIGMA_THREADS) k_sigma_stored(int64_t n, const
 #pragma unroll
         for (int q = 0; q < K; q++) acc[q] = 0.0;
         const int64_t beg = rowptr[i], end = rowptr[i + 1];
-        for (int64_t p = beg + lane; p < end; p += 32) {
-            const int64_t j = __ldg(&col[p]);
-            const double v = __ldg(&val[p]);
-            if (INTER) {
-                if (K == 2) {
-                    const double2 c2 = __ldg(reinterpret_cast<const double2 *>(x) + j);
-                    acc[0] = fma(v, c2.x, acc[0]);
-                    acc[K - 1] = fma(v, c2.y, acc[K - 1]);
+        for (int64_t p0 = beg + lane; p0 < end; p0 += 32 * SR) {
+            int64_t j[SR];
+            double v[SR], xv[SR][K];
+#pragma unroll
+            for (int u = 0; u < SR; u++) {
+                const int64_t p = p0 + 32 * u;
+                const bool in = p < end;
+                j[u] = in ? (int64_t)__ldg(&col[p]) : -1;
+                v[u] = in ? __ldg(&val[p]) : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < SR; u++) {
+                if (j[u] >= 0) {
+                    if (INTER && K == 2) {
+                        const double2 c2 = __ldg(reinterpret_cast<const double2 *>(x) + j[u]);
+                        xv[u][0] = c2.x;
+                        xv[u][K - 1] = c2.y;
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < K; q++) xv[u][q] = INTER ? __ldg(&x[j[u] * K + q]) : __ldg(&x[q * n + j[u]]);
+                    }
                 } else {
 #pragma unroll
-                    for (int q = 0; q < K; q++) acc[q] = fma(v, __ldg(&x[j * K + q]), acc[q]);
+                    for (int q = 0; q < K; q++) xv[u][q] = 0.0;
                 }
-            } else {
+            }
 #pragma unroll
-                for (int q = 0; q < K; q++) acc[q] = fma(v, __ldg(&x[q * n + j]), acc[q]);
+            for (int u = 0; u < SR; u++) {
+                if (j[u] >= 0) {
+#pragma unroll
+                    for (int q = 0; q < K; q++) acc[q] = fma(v[u], xv[u][q], acc[q]);
+                }
             }
         }
 #pragma unroll

@@ -43,8 +43,12 @@ def test_batch_matches_oracle(P, oracle_mod, budget, k):
         w = np.linalg.eigvalsh(O.dense_h(d["dets"]))[:k]
         np.testing.assert_allclose(e[s], w, atol=E_TOL, rtol=0)
     st = P.shci_batch_get_stats(b)
-    assert st["tuned_rows_per_item"] in (64, 256, 1024) and st["tuned_ctas_per_sm"] in (1, 2)
+    assert st["tuned_rows_per_item"] in (64, 256, 1024) and st["tuned_ctas_per_sm"] in (1, 2, 3)
     assert st["graph"] in (0, 1) and st["max_iters"] >= 1
+    # the per-phase times cover the solve: they add up to at most its device time
+    ph = st["phase_ms"]
+    assert all(x >= 0.0 for x in ph) and ph[1] > 0.0 and ph[4] > 0.0
+    assert 0.5 * st["solve_ms"] < sum(ph) <= st["solve_ms"] * 1.01 + 0.1
     P.shci_batch_destroy(b)
     ctx.close()
 

@@ -152,6 +152,13 @@ def test_selected_space_two_roots(P, oracle_mod):
     e, vecs, it = B.davidson(2, tol=1e-10)
     np.testing.assert_allclose(e, e_ref, atol=E_TOL, rtol=0)
     np.testing.assert_allclose(vecs @ vecs.T, np.eye(2), atol=1e-10)
+    # the convergence history: one row per iteration, ending on the returned energies
+    th, rn, ts = P.shci_davidson_history(B.ctx.handle, 2)
+    assert th.shape == (it, 2) and rn.shape == (it, 2) and ts.shape == (it,)
+    np.testing.assert_array_equal(th[-1], e)
+    assert np.all(np.diff(ts) >= 0.0) and ts[0] >= 0.0
+    assert np.all(rn[-1] < 0.1 * np.sqrt(1e-10))
+    assert np.all(np.diff(th[:, 0]) <= 1e-10)        # Ritz values never rise (thick restart keeps them)
     # restarting from the converged vectors converges at once to the same roots
     e2, _, it2 = B.davidson(2, tol=1e-10, guess=vecs)
     np.testing.assert_allclose(e2, e_ref, atol=E_TOL, rtol=0)
