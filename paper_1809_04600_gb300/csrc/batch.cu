@@ -53,6 +53,7 @@ struct BSys {
     double *Vb[2], *AVb[2];                // current / rotation target (swapped by index)
     double *T, *T2, *X, *Y;
     double *G, *evec, *erot, *eval;
+    double *jq;                            // the eigensolver's rotation accumulator (global scratch)
     double *coefC, *coefS0, *coefS, *coefM, *coefM2;
     double tol, res_tol;
 };
@@ -262,7 +263,10 @@ __device__ void sigma_rows(const BSys &S, int nb, int64_t r0, int cnt) {
 
 // ---------------------------------------------------------------- the persistent kernel
 
-__global__ void __launch_bounds__(BT, 3) k_batch_davidson(BatchArgs B) {
+// MINB: CTAs per SM the kernel is compiled for (its register budget); the
+// autotuner picks among the compiled variants.
+template <int MINB>
+__global__ void __launch_bounds__(BT, MINB) k_batch_davidson(BatchArgs B) {
     extern __shared__ double smem[];
     EnumSmem<1> &es = *reinterpret_cast<EnumSmem<1> *>(smem);
     double *sh = smem;                       // small-matrix scratch (phases never overlap)
@@ -406,7 +410,7 @@ __global__ void __launch_bounds__(BT, 3) k_batch_davidson(BatchArgs B) {
                 S.G[(m + q) * S.m_max + a] = v;
             }
             __syncthreads();
-            jacobi_solve(S.G, S.m_max, mt, st.m_eig, S.eval, S.evec, sh);
+            jacobi_solve<false>(S.G, S.m_max, mt, st.m_eig, S.eval, S.evec, sh, S.jq);
             __syncthreads();
             if (tid == 0) {
                 st.m = mt;
@@ -774,7 +778,24 @@ __global__ void __launch_bounds__(BT, 3) k_batch_davidson(BatchArgs B) {
     }
 }
 
-constexpr size_t BATCH_SMEM = JACOBI_SMEM;
+// dynamic shared memory: the eigensolver's working matrix (its rotations are
+// accumulated in global scratch), the enumeration's tiles and queues, or the
+// small-matrix scratch of the vector phases, whichever is largest
+constexpr size_t BATCH_SCRATCH = sizeof(double) * (SHCI_MAX_SUB * BK + 24 * SHCI_MAX_SUB);
+constexpr size_t BATCH_SMEM = JACOBI_SMEM_A > sizeof(EnumSmem<1>)
+                                  ? (JACOBI_SMEM_A > BATCH_SCRATCH ? JACOBI_SMEM_A : BATCH_SCRATCH)
+                                  : (sizeof(EnumSmem<1>) > BATCH_SCRATCH ? sizeof(EnumSmem<1>) : BATCH_SCRATCH);
+
+// the compiled variants of the persistent kernel (CTAs per SM)
+constexpr int BATCH_MINB_LO = 2, BATCH_MINB_HI = 4;
+
+inline void (*batch_kernel(int minb))(BatchArgs) {
+    switch (minb) {
+        case 2: return k_batch_davidson<2>;
+        case 3: return k_batch_davidson<3>;
+        default: return k_batch_davidson<4>;
+    }
+}
 
 }  // namespace shci
 
@@ -794,7 +815,7 @@ struct shci_batch {
     DevBuf<int64_t> a1_local, a2_local, v_start;
     DevBuf<double> partial;
     int64_t n_a1 = 0, n_a2 = 0, n_v = 0;
-    int srows = 256, blocks_per_sm = 2, grid = 0;
+    int srows = 256, blocks_per_sm = 3, grid = 0;
     bool tuned = false;
     cudaGraphExec_t gexec = nullptr;
     int graph_max_iter = -1;
@@ -856,7 +877,7 @@ void launch_batch(shci_batch *b, int max_iter, bool capture_ok) {
     auto enqueue = [&]() -> cudaError_t {
         cudaError_t e = cudaMemsetAsync(b->d_bar.p, 0, sizeof(BarrierState), st);
         if (e != cudaSuccess) return e;
-        return cudaLaunchKernelEx(&cfg, k_batch_davidson, A);
+        return cudaLaunchKernelEx(&cfg, batch_kernel(b->blocks_per_sm), A);
     };
     if (capture_ok) {
         // one persistent launch captured in a CUDA graph, re-instantiated when its parameters change
@@ -943,10 +964,11 @@ void build_worklists(shci_batch *b) {
 }
 
 void set_grid(shci_batch *b) {
-    CUDA_TRY(cudaFuncSetAttribute(shci::k_batch_davidson, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    CUDA_TRY(cudaFuncSetAttribute(shci::batch_kernel(b->blocks_per_sm), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)shci::BATCH_SMEM));
     int occ = 0;
-    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, shci::k_batch_davidson, shci::BT, shci::BATCH_SMEM));
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, shci::batch_kernel(b->blocks_per_sm), shci::BT,
+                                                           shci::BATCH_SMEM));
     if (occ < 1) throw ShciError{SHCI_ERR_CUDA, "the batched solver does not fit on one SM"};
     b->grid = b->parent->n_sm * std::min(occ, b->blocks_per_sm);
 }
@@ -968,6 +990,7 @@ void prepare_davidson(shci_batch *b, int k, double tol) {
             S.m_max = (int)std::min<int64_t>(std::min(SHCI_MAX_SUB, 16 + 16 * k), n);
             if (S.m_max < k) S.m_max = k;
             S.keep = std::max(k, std::min(S.m_max - k, std::max(2 * k, S.m_max / 3)));
+            if (S.keep > 24) throw ShciError{SHCI_ERR_INVALID, "restart block exceeds the batch scratch"};
             for (int x = 0; x < 2; x++) {
                 S.Vb[x] = b->alloc((size_t)S.m_max * n);
                 S.AVb[x] = b->alloc((size_t)S.m_max * n);
@@ -979,6 +1002,7 @@ void prepare_davidson(shci_batch *b, int k, double tol) {
             S.G = b->alloc((size_t)S.m_max * S.m_max);
             S.evec = b->alloc((size_t)S.m_max * S.m_max);
             S.erot = b->alloc((size_t)S.m_max * S.m_max);
+            S.jq = b->alloc((size_t)JACOBI_Q_DOUBLES);
             S.eval = b->alloc((size_t)S.m_max);
             S.coefC = b->alloc((size_t)SHCI_MAX_SUB * BK);
             S.coefS0 = b->alloc(BK);
@@ -1011,26 +1035,30 @@ void prepare_davidson(shci_batch *b, int k, double tol) {
 // project autotuner: rows per stored-sigma work item and CTAs per SM, chosen by
 // timing a few iterations of the real kernel for each candidate
 void autotune(shci_batch *b) {
+    // rows per stored-sigma item with the middle variant, then the variant
+    // (register budget / CTAs per SM) with the best rows
     const int rows_c[3] = {64, 256, 1024};
-    const int bps_c[3] = {1, 2, 3};
     double best = INFINITY;
-    int best_rows = b->srows, best_bps = b->blocks_per_sm;
-    for (int r : rows_c)
-        for (int p : bps_c) {
-            b->srows = r;
-            b->blocks_per_sm = p;
-            build_worklists(b);
-            set_grid(b);
-            const double ms = time_batch(b, 3);
-            shci::BarrierState bar{};
-            CUDA_TRY(cudaMemcpy(&bar, b->d_bar.p, sizeof(bar), cudaMemcpyDeviceToHost));
-            if (bar.err) throw ShciError{SHCI_ERR_TIMEOUT, "batched solver: grid barrier timed out while tuning"};
-            if (ms < best) {
-                best = ms;
-                best_rows = r;
-                best_bps = p;
-            }
+    int best_rows = b->srows, best_bps = 3;
+    auto trial = [&](int r, int p) {
+        b->srows = r;
+        b->blocks_per_sm = p;
+        build_worklists(b);
+        set_grid(b);
+        const double ms = time_batch(b, 3);
+        shci::BarrierState bar{};
+        CUDA_TRY(cudaMemcpy(&bar, b->d_bar.p, sizeof(bar), cudaMemcpyDeviceToHost));
+        if (bar.err) throw ShciError{SHCI_ERR_TIMEOUT, "batched solver: grid barrier timed out while tuning"};
+        if (ms < best) {
+            best = ms;
+            best_rows = r;
+            best_bps = p;
         }
+    };
+    for (int r : rows_c) trial(r, 3);
+    const int rows_best = best_rows;
+    for (int p = shci::BATCH_MINB_LO; p <= shci::BATCH_MINB_HI; p++)
+        if (p != 3) trial(rows_best, p);
     b->srows = best_rows;
     b->blocks_per_sm = best_bps;
     build_worklists(b);

@@ -14,6 +14,7 @@ struct DavidsonWork {
     DevBuf<double> eval;         // [m_max]
     DevBuf<double> partial;      // block partial sums for dot products
     DevBuf<double> small;        // small device scalars (norms, coefficients)
+    DevBuf<unsigned> ctr;        // last-block reduction counters
     DevBuf<double> host_pinned_dummy;
     double *h_status = nullptr;  // pinned host mirror of the status block
 };

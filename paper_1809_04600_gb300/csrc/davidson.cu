@@ -4,10 +4,12 @@
 // Everything runs on the device in FP64: the block sigma product, the
 // projected matrix V^T H V, its eigen-decomposition (warm-started threshold
 // Jacobi in one CTA), Ritz vectors, residuals, the preconditioner and the
-// block orthonormalisation (classical Gram-Schmidt twice against the basis,
-// then Cholesky-QR twice within the block).  The host only sequences launches
-// and reads a few scalars twice per iteration (Ritz values and residual norms;
-// the number of accepted new vectors).
+// block orthonormalisation (classical Gram-Schmidt against the basis, a second
+// pass only when the first removed most of a vector, Cholesky-QR within the
+// block).  Reductions finish in the last block of each launch (no separate
+// reduction kernels).  The host only sequences launches and reads a few
+// scalars twice per iteration (Ritz values and residual norms; the number of
+// accepted new vectors).
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -19,6 +21,8 @@
 namespace shci {
 
 constexpr int DV_THREADS = 256;
+constexpr int N_CTR = 128;                 // reduction counters: Gram row groups, last group, Ritz
+constexpr int RITZ_CTR = N_CTR - 1;
 
 // ---------------------------------------------------------------- block Gram products
 
@@ -28,71 +32,173 @@ struct GramShape {
     static constexpr int NA = NB >= 16 ? 1 : 16 / NB;
 };
 
-// partial[(slice * na + a) * NB + b] = sum over this slice of A[a][i] * B[b][i];
-// blockIdx.x = slice, blockIdx.y = group of NA rows of A
+// What the last block does with a finished Gram product R = A^T B (A: the
+// rows V[0..mv) then T[0..mt), B: NB vectors).
+enum { EP_STORE = 0, EP_ORTHO = 1, EP_CHOL = 2 };
+
+struct GramOut {
+    int mode;
+    double *R;              // [mv + mt][NB]: the product, always written
+    double *dst;            // EP_STORE: dst[(a0 + a) * ld + b0 + b] (and mirrored when sym)
+    int ld, a0, b0, sym;
+    // EP_ORTHO (A = [V; T], B = T, mt = NB) and EP_CHOL (A = T, B = T)
+    int pass;               // EP_ORTHO: 1 (decides on a second pass) or 2
+    double *pre;            // [NB] squared norms before projection (pass 1 writes them)
+    double *M;              // [NB][NB] coefficients of the new block
+    double *CM;             // [mv][NB] = C M (EP_ORTHO)
+    int *count;             // accepted vectors
+    int *skip2;             // EP_ORTHO pass 1: 1 when the second pass is not needed
+};
+
+// Parallel reduction over slices, in a fixed order: out[e] for this group's
+// outputs, one warp per output.
+__device__ __forceinline__ double slice_sum(const double *partial, int64_t base, int stride, int nslices, int lane) {
+    double s = 0.0;
+    for (int x = lane; x < nslices; x += 32) s += __ldcg(&partial[base + (int64_t)x * stride]);
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+}
+
+// R = A^T B with A = [V[0..mv); T[0..mt)] (rows of n) and B = NB vectors.
+// blockIdx.x = slice of the vectors, blockIdx.y = group of NA rows of A.  Each
+// block writes its partial sums; the last block of a group (atomic counter
+// ctr[y]) sums the group's partials in slice order; for EP_ORTHO / EP_CHOL the
+// last group (ctr[gridDim.y]) then computes the small-matrix coefficients.
+// Counters are reset by the blocks that finish with them.
 template <int NB>
-__global__ void __launch_bounds__(DV_THREADS) k_gram(const double *__restrict__ A, int na,
-                                                    const double *__restrict__ B, int64_t n,
-                                                    double *__restrict__ partial, const int *__restrict__ skip) {
+__global__ void __launch_bounds__(DV_THREADS) k_gram_f(const double *__restrict__ V, int mv,
+                                                      const double *__restrict__ T, int mt,
+                                                      const double *__restrict__ B, int64_t n,
+                                                      double *__restrict__ partial, unsigned *__restrict__ ctr,
+                                                      GramOut o, const int *__restrict__ skip) {
     if (skip && *skip) return;              // device-side decision: this product is not needed
     constexpr int NA = GramShape<NB>::NA;
+    constexpr int NE = NA * NB;
+    const int na = mv + mt;
     const int a0 = blockIdx.y * NA;
     const int cnt = min(NA, na - a0);
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const double *rowp[NA];
+#pragma unroll
+    for (int a = 0; a < NA; a++) {
+        const int r = min(a0 + a, na - 1);
+        rowp[a] = r < mv ? V + (int64_t)r * n : T + (int64_t)(r - mv) * n;
+    }
     double acc[NA][NB];
 #pragma unroll
     for (int a = 0; a < NA; a++)
 #pragma unroll
         for (int b = 0; b < NB; b++) acc[a][b] = 0.0;
     const int64_t stride = (int64_t)gridDim.x * DV_THREADS;
-    for (int64_t i = blockIdx.x * (int64_t)DV_THREADS + threadIdx.x; i < n; i += stride) {
+    for (int64_t i = blockIdx.x * (int64_t)DV_THREADS + tid; i < n; i += stride) {
         double bv[NB];
 #pragma unroll
         for (int b = 0; b < NB; b++) bv[b] = B[b * n + i];
 #pragma unroll
         for (int a = 0; a < NA; a++) {
             if (a < cnt) {
-                const double av = A[(int64_t)(a0 + a) * n + i];
+                const double av = rowp[a][i];
 #pragma unroll
                 for (int b = 0; b < NB; b++) acc[a][b] = fma(av, bv[b], acc[a][b]);
             }
         }
     }
-    __shared__ double red[NA * NB][DV_THREADS / 32];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __shared__ double red[NE][DV_THREADS / 32];
 #pragma unroll
     for (int a = 0; a < NA; a++) {
 #pragma unroll
         for (int b = 0; b < NB; b++) {
             double v = acc[a][b];
 #pragma unroll
-            for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            for (int o2 = 16; o2 >= 1; o2 >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o2);
             if (lane == 0) red[a * NB + b][w] = v;
         }
     }
     __syncthreads();
-    const int e = threadIdx.x;
-    if (e < cnt * NB) {
+    const int64_t gbase = (int64_t)blockIdx.y * gridDim.x * NE;
+    if (tid < cnt * NB) {
         double s = 0.0;
 #pragma unroll
-        for (int x = 0; x < DV_THREADS / 32; x++) s += red[e][x];
-        partial[((int64_t)blockIdx.x * na + a0 + e / NB) * NB + (e % NB)] = s;
+        for (int x = 0; x < DV_THREADS / 32; x++) s += red[tid][x];
+        partial[gbase + (int64_t)blockIdx.x * NE + tid] = s;
     }
-}
-
-// out[(a0 + a) * ld + b0 + b] = sum_slice partial[(slice * na + a) * nb + b]; one warp per entry
-__global__ void k_gram_reduce(const double *__restrict__ partial, int nslices, int na, int nb, double *out, int ld,
-                              int a0, int b0, int sym) {
-    const int e = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    if (e >= na * nb) return;
-    const int a = e / nb, b = e % nb;
-    double s = 0.0;
-    for (int x = lane; x < nslices; x += 32) s += partial[((int64_t)x * na + a) * nb + b];
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) {
-        out[(a0 + a) * ld + b0 + b] = s;
-        if (sym) out[(b0 + b) * ld + a0 + a] = s;
+    // last block of this group: the group's outputs
+    __shared__ int last;
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) last = atomicAdd(&ctr[blockIdx.y], 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (int e = w; e < cnt * NB; e += DV_THREADS / 32) {
+        const double v = slice_sum(partial, gbase + e, NE, gridDim.x, lane);
+        if (lane == 0) {
+            const int a = a0 + e / NB, b = e % NB;
+            o.R[a * NB + b] = v;
+            if (o.mode == EP_STORE) {
+                o.dst[(o.a0 + a) * o.ld + o.b0 + b] = v;
+                if (o.sym) o.dst[(o.b0 + b) * o.ld + o.a0 + a] = v;
+            }
+        }
+    }
+    if (tid == 0) ctr[blockIdx.y] = 0u;
+    if (o.mode == EP_STORE) return;
+    // last group: the small-matrix step
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) last = atomicAdd(&ctr[gridDim.y], 1u) == gridDim.y - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    if (tid == 0) ctr[gridDim.y] = 0u;
+    __shared__ double Ss[NB * NB], Ms[NB * NB], pres[NB];
+    __shared__ int cnt_s;
+    if (o.mode == EP_CHOL) {
+        if (tid == 0) {
+            for (int e = 0; e < NB * NB; e++) Ss[e] = __ldcg(&o.R[e]);
+            *o.count = cholqr_coef(Ss, NB, nullptr, 1e-12, o.M);
+        }
+        return;
+    }
+    // EP_ORTHO: C = R[0..mv), S = R[mv..mv + NB); projected Gram S' = S - C^T C
+    // (V orthonormal), then Cholesky-QR coefficients M of (T - V C) and C M
+    for (int e = tid; e < NB * NB; e += DV_THREADS) {
+        const int j = e / NB, l = e % NB;
+        double v = __ldcg(&o.R[(mv + j) * NB + l]);
+        for (int a = 0; a < mv; a++) v -= __ldcg(&o.R[a * NB + j]) * __ldcg(&o.R[a * NB + l]);
+        Ss[e] = v;
+    }
+    if (o.pass == 1 && tid < NB) {
+        pres[tid] = __ldcg(&o.R[(mv + tid) * NB + tid]);
+        o.pre[tid] = pres[tid];
+    } else if (tid < NB) {
+        pres[tid] = __ldcg(&o.pre[tid]);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        // "twice is enough": a second projection is needed only when the first
+        // removed more than half of some vector's norm (squared norm below a
+        // quarter); S' is then too inexact to orthonormalise from
+        int need2 = 0;
+        if (o.pass == 1)
+            for (int l = 0; l < NB; l++) need2 |= Ss[l * NB + l] < 0.25 * pres[l];
+        if (need2) {
+            for (int e = 0; e < NB * NB; e++) Ms[e] = (e / NB == e % NB) ? 1.0 : 0.0;
+            cnt_s = NB;
+        } else {
+            cnt_s = cholqr_coef(Ss, NB, pres, 1e-20, Ms);
+        }
+        if (o.pass == 1) *o.skip2 = need2 ? 0 : 1;
+        *o.count = cnt_s;
+    }
+    __syncthreads();
+    for (int e = tid; e < NB * NB; e += DV_THREADS) o.M[e] = Ms[e];
+    for (int e = tid; e < mv * NB; e += DV_THREADS) {
+        const int a = e / NB, l = e % NB;
+        double v = 0.0;
+        for (int j = 0; j < NB; j++) v = fma(__ldcg(&o.R[a * NB + j]), Ms[j * NB + l], v);
+        o.CM[e] = v;
     }
 }
 
@@ -109,51 +215,52 @@ __global__ void k_unpack(const double *__restrict__ X, int k, int64_t n, double 
         for (int b = 0; b < k; b++) V[b * n + i] = X[i * k + b];
 }
 
-// T[l] -= sum_a C[a * KB + l] * V[a]   for a < m, l < KB
+// In place: T[l] <- sum_j M[j][l] T[j] - sum_a CM[a][l] V[a] for l < *count,
+// zero for l >= *count (the projection T - V C followed by the block's
+// coefficients M, with CM = C M).
 template <int KB>
-__global__ void __launch_bounds__(DV_THREADS) k_project(const double *__restrict__ V, int m,
-                                                       const double *__restrict__ C, int64_t n,
+__global__ void __launch_bounds__(DV_THREADS) k_combine(const double *__restrict__ V, int m,
+                                                       const double *__restrict__ CM, const double *__restrict__ M,
+                                                       const int *__restrict__ count, int64_t n,
                                                        double *__restrict__ T, const int *__restrict__ skip) {
     if (skip && *skip) return;
     __shared__ double cs[SHCI_MAX_SUB * KB];
-    for (int e = threadIdx.x; e < m * KB; e += blockDim.x) cs[e] = C[e];
+    __shared__ double ms[KB * KB];
+    for (int e = threadIdx.x; e < m * KB; e += blockDim.x) cs[e] = CM[e];
+    for (int e = threadIdx.x; e < KB * KB; e += blockDim.x) ms[e] = M[e];
     __syncthreads();
+    const int na = *count;
     for (int64_t i = blockIdx.x * (int64_t)DV_THREADS + threadIdx.x; i < n; i += (int64_t)gridDim.x * DV_THREADS) {
-        double t[KB];
+        double t[KB], o[KB];
 #pragma unroll
         for (int l = 0; l < KB; l++) t[l] = T[l * n + i];
+#pragma unroll
+        for (int l = 0; l < KB; l++) {
+            double v = 0.0;
+#pragma unroll
+            for (int j = 0; j < KB; j++) v = fma(ms[j * KB + l], t[j], v);
+            o[l] = v;
+        }
         int a = 0;
         for (; a + 4 <= m; a += 4) {
             const double v0 = V[(int64_t)a * n + i], v1 = V[(int64_t)(a + 1) * n + i];
             const double v2 = V[(int64_t)(a + 2) * n + i], v3 = V[(int64_t)(a + 3) * n + i];
 #pragma unroll
             for (int l = 0; l < KB; l++) {
-                t[l] = fma(-cs[a * KB + l], v0, t[l]);
-                t[l] = fma(-cs[(a + 1) * KB + l], v1, t[l]);
-                t[l] = fma(-cs[(a + 2) * KB + l], v2, t[l]);
-                t[l] = fma(-cs[(a + 3) * KB + l], v3, t[l]);
+                o[l] = fma(-cs[a * KB + l], v0, o[l]);
+                o[l] = fma(-cs[(a + 1) * KB + l], v1, o[l]);
+                o[l] = fma(-cs[(a + 2) * KB + l], v2, o[l]);
+                o[l] = fma(-cs[(a + 3) * KB + l], v3, o[l]);
             }
         }
         for (; a < m; a++) {
             const double v = V[(int64_t)a * n + i];
 #pragma unroll
-            for (int l = 0; l < KB; l++) t[l] = fma(-cs[a * KB + l], v, t[l]);
+            for (int l = 0; l < KB; l++) o[l] = fma(-cs[a * KB + l], v, o[l]);
         }
 #pragma unroll
-        for (int l = 0; l < KB; l++) T[l * n + i] = t[l];
+        for (int l = 0; l < KB; l++) T[l * n + i] = l < na ? o[l] : 0.0;
     }
-}
-
-// Cholesky-QR coefficients for kb vectors with Gram matrix S (kb x kb).
-// Column l is dropped when its component outside the span of the accepted
-// earlier columns has squared norm below rel * ref[l] (ref: S's diagonal, or
-// the squared norms before projection when given).  Writes M (kb x kb,
-// column l' of the accepted set) such that q_l' = sum_j M[j * kb + l'] t_j is
-// orthonormal, and *count = number accepted.  One thread; kb <= 8.
-__global__ void k_cholqr_coef(const double *__restrict__ S, int kb, const double *__restrict__ ref, double rel,
-                              double *__restrict__ M, int *__restrict__ count) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    *count = cholqr_coef(S, kb, ref, rel, M);
 }
 
 // out[l'] = sum_j M[j * KB + l'] T[j] for l' < KB; slots l' >= *count are
@@ -195,7 +302,8 @@ __global__ void __launch_bounds__(DV_THREADS) k_ritz(const double *__restrict__ 
                                                      const double *__restrict__ eval, int64_t n,
                                                      const double *__restrict__ diag, double *__restrict__ T,
                                                      double *__restrict__ Xo, double *__restrict__ Ho,
-                                                     double *__restrict__ partial) {
+                                                     double *__restrict__ partial, unsigned *__restrict__ ctr,
+                                                     double *__restrict__ rn_out) {
     __shared__ double ys[SHCI_MAX_SUB * K];
     __shared__ double th[K];
     for (int e = threadIdx.x; e < m * K; e += blockDim.x) ys[e] = evec[(e % K) * ld + (e / K)];   // ys[a*K+l]
@@ -263,18 +371,23 @@ __global__ void __launch_bounds__(DV_THREADS) k_ritz(const double *__restrict__ 
             for (int x = 0; x < DV_THREADS / 32; x++) s += red[threadIdx.x][x];
             partial[(int64_t)blockIdx.x * K + threadIdx.x] = s;
         }
-    }
-}
-
-// out[l] = sum_blk partial[blk * k + l]; one warp per root
-__global__ void k_sum_partials(const double *__restrict__ partial, int nblk, int k, double *__restrict__ out) {
-    const int l = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (l >= k) return;
-    double s = 0.0;
-    for (int b = lane; b < nblk; b += 32) s += partial[(int64_t)b * k + l];
+        // the last block sums the partial squared norms in block order
+        __shared__ int last;
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) last = atomicAdd(ctr, 1u) == gridDim.x - 1;
+        __syncthreads();
+        if (!last) return;
+        __threadfence();
+        if (w < K) {
+            double s = 0.0;
+            for (int b = lane; b < (int)gridDim.x; b += 32) s += __ldcg(&partial[(int64_t)b * K + w]);
 #pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) out[l] = s;
+            for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) rn_out[w] = s;
+        }
+        if (threadIdx.x == 0) *ctr = 0u;
+    }
 }
 
 // ---------------------------------------------------------------- subspace eigensolver
@@ -337,21 +450,6 @@ __global__ void k_unit_vectors(const int64_t *__restrict__ idx, int k, int64_t n
 
 // ---------------------------------------------------------------- host driver
 
-__global__ void k_diag_copy(const double *__restrict__ S, int kb, double *__restrict__ out) {
-    int l = threadIdx.x;
-    if (l < kb) out[l] = S[l * kb + l];
-}
-
-// "twice is enough": a second Gram-Schmidt pass is needed only if the first
-// removed more than half of some vector's norm (squared norm below a quarter)
-__global__ void k_second_pass_flag(const double *__restrict__ S, int kb, const double *__restrict__ pre,
-                                   int *__restrict__ skip) {
-    if (threadIdx.x != 0) return;
-    int need = 0;
-    for (int l = 0; l < kb; l++) need |= S[l * kb + l] < 0.25 * pre[l];
-    *skip = need ? 0 : 1;
-}
-
 #define DISPATCH_K(kval, F)                         \
     switch (kval) {                                 \
         case 1: F(1); break;                        \
@@ -407,46 +505,53 @@ struct Dav {
     int k, m_max, keep;
     int vec_blocks, n_slots;
     cudaStream_t st;
-    double *coef, *gram_s, *pre, *mcoef;   // device small buffers
+    double *R, *CM, *M, *pre;   // device small buffers: Gram result, coefficients, norms
+    unsigned *ctr;              // reduction counters (zero between launches)
     int *d_count;
-    int *d_skip;            // device flag: 1 = second Gram-Schmidt pass not needed
+    int *d_skip;                // device flag: 1 = second Gram-Schmidt pass not needed
 
     double *Vr(int a) { return c->dw.V.p + (int64_t)a * n; }
     double *AVr(int a) { return c->dw.AV.p + (int64_t)a * n; }
 
     template <int NB>
-    void gram_nb(const double *A, int na, const double *B, double *out, int ld, int a0, int b0, bool sym,
+    void gram_nb(const double *V, int mv, const double *T, int mt, const double *B, const GramOut &o,
                  const int *skip) {
         constexpr int NA = GramShape<NB>::NA;
+        const int na = mv + mt;
         const int groups = (na + NA - 1) / NA;
         const int slices = std::max(1, std::min<int>((int)ceil_div(n, DV_THREADS * 4), n_slots / groups));
         dim3 grid(slices, groups);
-        k_gram<NB><<<grid, DV_THREADS, 0, st>>>(A, na, B, n, c->dw.partial.p, skip);
-        const int outs = na * NB;
-        k_gram_reduce<<<(outs + 7) / 8, 256, 0, st>>>(c->dw.partial.p, slices, na, NB, out, ld, a0, b0, sym ? 1 : 0);
+        k_gram_f<NB><<<grid, DV_THREADS, 0, st>>>(V, mv, T, mt, B, n, c->dw.partial.p, ctr, o, skip);
         KERNEL_CHECK();
-        g_kernel_launches += 2;
+        g_kernel_launches += 1;
+    }
+
+    void gram_dispatch(int nb, const double *V, int mv, const double *T, int mt, const double *B, const GramOut &o,
+                       const int *skip) {
+#define F(NB) gram_nb<NB>(V, mv, T, mt, B, o, skip)
+        DISPATCH_K(nb, F)
+#undef F
     }
 
     // out[a0 + a][b0 + b] (leading dimension ld) = A[a] . B[b], a < na, b < nb; mirrored if sym.
-    // With a non-null `skip` the products are not computed when *skip != 0 (and out
-    // then holds unused values).
-    void gram(const double *A, int na, const double *B, int nb, double *out, int ld, int a0, int b0, bool sym,
-              const int *skip = nullptr) {
+    void gram(const double *A, int na, const double *B, int nb, double *out, int ld, int a0, int b0, bool sym) {
         if (na <= 0 || nb <= 0) return;
-        int b = 0;
-        while (b < nb) {
-            int left = nb - b;
-            const double *Bb = B + (int64_t)b * n;
-            if (left >= 8) { gram_nb<8>(A, na, Bb, out, ld, a0, b0 + b, sym, skip); b += 8; }
-            else if (left >= 4) { gram_nb<4>(A, na, Bb, out, ld, a0, b0 + b, sym, skip); b += 4; }
-            else if (left >= 2) { gram_nb<2>(A, na, Bb, out, ld, a0, b0 + b, sym, skip); b += 2; }
-            else { gram_nb<1>(A, na, Bb, out, ld, a0, b0 + b, sym, skip); b += 1; }
+        for (int b = 0; b < nb; b += SHCI_MAX_K) {
+            const int cnt = std::min(SHCI_MAX_K, nb - b);
+            GramOut o{};
+            o.mode = EP_STORE;
+            o.R = R;
+            o.dst = out;
+            o.ld = ld;
+            o.a0 = a0;
+            o.b0 = b0 + b;
+            o.sym = sym ? 1 : 0;
+            gram_dispatch(cnt, A, na, nullptr, 0, B + (int64_t)b * n, o, nullptr);
         }
     }
 
-    void project(const double *C, int m, int kb, double *T, const int *skip = nullptr) {
-#define F(KB) k_project<KB><<<vec_blocks, DV_THREADS, 0, st>>>(c->dw.V.p, m, C, n, T, skip)
+    void combine(double *T, int kb, int m, const int *skip) {
+#define F(KB) k_combine<KB><<<vec_blocks, DV_THREADS, 0, st>>>(c->dw.V.p, m, CM, M, d_count, n, T, skip)
         DISPATCH_K(kb, F)
 #undef F
         KERNEL_CHECK();
@@ -454,41 +559,42 @@ struct Dav {
     }
 
     void apply_coef(const double *T, int kb, double *out, bool zero_fill) {
-#define F(KB) k_apply_coef<KB><<<vec_blocks, DV_THREADS, 0, st>>>(T, mcoef, d_count, zero_fill ? 1 : 0, n, out)
+#define F(KB) k_apply_coef<KB><<<vec_blocks, DV_THREADS, 0, st>>>(T, M, d_count, zero_fill ? 1 : 0, n, out)
         DISPATCH_K(kb, F)
 #undef F
         KERNEL_CHECK();
         g_kernel_launches += 1;
     }
 
-    // Orthonormalise the kb vectors T[0..kb) against V[0..m) (classical
-    // Gram-Schmidt; the second pass runs only when the first removed more
-    // than half of some vector's norm, decided on the device) and among
-    // themselves (Cholesky-QR, twice), writing the accepted ones to V[m ..);
-    // returns how many were accepted.
+    // Orthonormalise the kb vectors T[0..kb) against V[0..m) and among
+    // themselves, writing the accepted ones to V[m ..); returns how many were
+    // accepted.  Pass 1 forms C = V^T T and S = T^T T in one sweep, and the last
+    // block derives the coefficients of (T - V C) M from S - C^T C; when the
+    // projection removed more than half of some vector's norm the device asks
+    // for a second projection pass ("twice is enough"), otherwise that pass's
+    // kernels return at once.  A last Cholesky-QR pass within the block follows.
     int orthonormalize_append(double *T, int kb, int m) {
-        double *T2 = c->dw.T.p + (int64_t)SHCI_MAX_K * n;
-        // squared norms before projection: reference for the dependence test
-        gram(T, kb, T, kb, gram_s, kb, 0, 0, false);
-        k_diag_copy<<<1, 32, 0, st>>>(gram_s, kb, pre);
-        g_kernel_launches += 1;
-        if (m > 0) {
-            gram(c->dw.V.p, m, T, kb, coef, kb, 0, 0, false);
-            project(coef, m, kb, T);
-            gram(T, kb, T, kb, gram_s, kb, 0, 0, false);
-            k_second_pass_flag<<<1, 32, 0, st>>>(gram_s, kb, pre, d_skip);
-            gram(c->dw.V.p, m, T, kb, coef, kb, 0, 0, false, d_skip);
-            project(coef, m, kb, T, d_skip);
-            g_kernel_launches += 1;
-        }
-        gram(T, kb, T, kb, gram_s, kb, 0, 0, false);
-        k_cholqr_coef<<<1, 1, 0, st>>>(gram_s, kb, pre, 1e-20, mcoef, d_count);
-        apply_coef(T, kb, T2, true);
-        gram(T2, kb, T2, kb, gram_s, kb, 0, 0, false);
-        k_cholqr_coef<<<1, 1, 0, st>>>(gram_s, kb, nullptr, 1e-12, mcoef, d_count);
-        apply_coef(T2, kb, Vr(m), false);
-        KERNEL_CHECK();
-        g_kernel_launches += 2;
+        GramOut o{};
+        o.mode = EP_ORTHO;
+        o.R = R;
+        o.pre = pre;
+        o.M = M;
+        o.CM = CM;
+        o.count = d_count;
+        o.skip2 = d_skip;
+        o.pass = 1;
+        gram_dispatch(kb, c->dw.V.p, m, T, kb, T, o, nullptr);
+        combine(T, kb, m, nullptr);
+        o.pass = 2;
+        gram_dispatch(kb, c->dw.V.p, m, T, kb, T, o, d_skip);
+        combine(T, kb, m, d_skip);
+        GramOut q{};
+        q.mode = EP_CHOL;
+        q.R = R;
+        q.M = M;
+        q.count = d_count;
+        gram_dispatch(kb, nullptr, 0, T, kb, T, q, nullptr);
+        apply_coef(T, kb, Vr(m), false);
         int added = 0;
         CUDA_TRY(cudaMemcpyAsync(&added, d_count, sizeof(int), cudaMemcpyDeviceToHost, st));
         CUDA_TRY(cudaStreamSynchronize(st));
@@ -512,12 +618,11 @@ struct Dav {
 #define F(K)                                                                                                 \
     k_ritz<K, 0><<<vec_blocks, DV_THREADS, 0, st>>>(c->dw.V.p, c->dw.AV.p, m, c->dw.evec.p, m_max,          \
                                                     c->dw.eval.p, n, c->diag.p, T, nullptr, nullptr,         \
-                                                    c->dw.partial.p)
+                                                    c->dw.partial.p, ctr + RITZ_CTR, d_rn)
         DISPATCH_K(k, F)
 #undef F
-        k_sum_partials<<<1, 32 * k, 0, st>>>(c->dw.partial.p, vec_blocks, k, d_rn);
         KERNEL_CHECK();
-        g_kernel_launches += 2;
+        g_kernel_launches += 1;
     }
 
     // x_l = V y_l and h_l = AV y_l for l in [j0, j0 + cnt)
@@ -525,7 +630,7 @@ struct Dav {
 #define F(K)                                                                                                 \
     k_ritz<K, 1><<<vec_blocks, DV_THREADS, 0, st>>>(c->dw.V.p, c->dw.AV.p, m, c->dw.evec.p + (int64_t)j0 * m_max, \
                                                     m_max, c->dw.eval.p + j0, n, c->diag.p, nullptr, Xo, Ho, \
-                                                    nullptr)
+                                                    nullptr, nullptr, nullptr)
         DISPATCH_K(cnt, F)
 #undef F
         KERNEL_CHECK();
@@ -578,11 +683,14 @@ int davidson(shci_ctx *c, int k, double tol, int max_iter, const double *guess, 
     w.eval.alloc((size_t)d.m_max);
     w.partial.alloc((size_t)std::max(d.n_slots, d.vec_blocks) * SHCI_MAX_SUB * SHCI_MAX_K);
     w.small.alloc((size_t)4 * SHCI_MAX_SUB * SHCI_MAX_K + 64);
-    d.coef = w.small.p;                                        // [m_max][kb]
-    d.gram_s = w.small.p + SHCI_MAX_SUB * SHCI_MAX_K;          // [kb][kb]
-    d.pre = w.small.p + 2 * SHCI_MAX_SUB * SHCI_MAX_K;         // [kb]
-    d.mcoef = w.small.p + 2 * SHCI_MAX_SUB * SHCI_MAX_K + 16;  // [kb][kb]
-    double *d_rn = w.small.p + 3 * SHCI_MAX_SUB * SHCI_MAX_K;  // [k]
+    d.R = w.small.p;                                                    // [m_max + 8][kb]
+    d.CM = w.small.p + (SHCI_MAX_SUB + SHCI_MAX_K) * SHCI_MAX_K;        // [m_max][kb]
+    d.M = d.CM + SHCI_MAX_SUB * SHCI_MAX_K;                             // [kb][kb]
+    d.pre = d.M + SHCI_MAX_K * SHCI_MAX_K;                              // [kb]
+    double *d_rn = d.pre + SHCI_MAX_K;                                  // [k]
+    w.ctr.alloc(N_CTR);
+    CUDA_TRY(cudaMemsetAsync(w.ctr.p, 0, sizeof(unsigned) * N_CTR, c->st));
+    d.ctr = w.ctr.p;
     c->counter.alloc(4);
     d.d_count = c->counter.p + 3;
     d.d_skip = c->counter.p + 2;

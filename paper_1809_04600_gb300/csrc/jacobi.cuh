@@ -53,13 +53,29 @@ __device__ __forceinline__ int cholqr_coef(const double *S, int kb, const double
 // new border has to be transformed.  Rotations whose off-diagonal element is
 // below 1e-14 (|a_pp| + |a_qq|) become the identity, a round with none active
 // is skipped, and sweeps stop when one applies no rotation.  A round applies
-// all of its rotations in one pass (two barriers per round).  Output:
+// its active rotations in one pass over the 2 x 2 blocks they touch (two
+// barriers per round).  One SM issues few FP64 instructions (a warp-wide FP64
+// instruction occupies its FP64 pipe for many cycles), so no FP64 work is
+// spent on identity blocks and the work is packed into few warps.  Output:
 // eigenvalues (the converged diagonal) ascending and eigenvectors as columns,
 // evec[l * ld + a] = component a of vector l.
+//
+// The working matrix A lives in shared memory (jsm).  The accumulated
+// rotation Q lives there too (QSHARED, JACOBI_SMEM bytes in all), or in the
+// global scratch qg of JACOBI_Q_DOUBLES doubles owned by the calling CTA
+// (JACOBI_SMEM_A bytes of shared memory), accessed through L2.
+template <bool QSHARED = true>
 __device__ __forceinline__ void jacobi_solve(const double *G, int ld, int m, int m_prev,
-                                             double *__restrict__ eval, double *__restrict__ evec, double *jsm) {
-    double (*A)[SHCI_MAX_SUB + 1] = reinterpret_cast<double (*)[SHCI_MAX_SUB + 1]>(jsm);
-    double (*Q)[SHCI_MAX_SUB + 1] = reinterpret_cast<double (*)[SHCI_MAX_SUB + 1]>(jsm + SHCI_MAX_SUB * (SHCI_MAX_SUB + 1));
+                                             double *__restrict__ eval, double *__restrict__ evec, double *jsm,
+                                             double *qg = nullptr) {
+    constexpr int QL = SHCI_MAX_SUB + 1;
+    double (*A)[QL] = reinterpret_cast<double (*)[QL]>(jsm);
+    double *Qp = QSHARED ? jsm + SHCI_MAX_SUB * QL : qg;
+    auto qget = [&](int r, int c) { return QSHARED ? Qp[r * QL + c] : __ldcg(&Qp[r * QL + c]); };
+    auto qset = [&](int r, int c, double v) {
+        if (QSHARED) Qp[r * QL + c] = v;
+        else __stcg(&Qp[r * QL + c], v);
+    };
     __shared__ double cs[SHCI_MAX_SUB / 2], sn[SHCI_MAX_SUB / 2];
     __shared__ int pp[SHCI_MAX_SUB / 2], qq[SHCI_MAX_SUB / 2];
     __shared__ double lam[SHCI_MAX_SUB];
@@ -73,8 +89,8 @@ __device__ __forceinline__ void jacobi_solve(const double *G, int ld, int m, int
     for (int e = tid; e < mm * mm; e += nt) {
         int r = e / mm, c = e % mm;
         double q = (r == c) ? 1.0 : 0.0;
-        if (r < mp && c < mp) q = evec[c * ld + r];
-        Q[r][c] = q;
+        if (r < mp && c < mp) q = __ldcg(&evec[c * ld + r]);
+        qset(r, c, q);
     }
     __syncthreads();
     // A = Q^T G Q: leading block diag(previous eigenvalues), border transformed, trailing block copied
@@ -83,11 +99,11 @@ __device__ __forceinline__ void jacobi_solve(const double *G, int ld, int m, int
         double v = 0.0;
         if (r < m && c < m) {
             if (r < mp && c < mp) {
-                v = (r == c) ? eval[r] : 0.0;
+                v = (r == c) ? __ldcg(&eval[r]) : 0.0;
             } else if (r < mp) {          // (Q^T G)[r][c] for border column c
-                for (int s = 0; s < mp; s++) v = fma(Q[s][r], gs(s, c), v);
+                for (int s = 0; s < mp; s++) v = fma(qget(s, r), gs(s, c), v);
             } else if (c < mp) {
-                for (int s = 0; s < mp; s++) v = fma(Q[s][c], gs(r, s), v);
+                for (int s = 0; s < mp; s++) v = fma(qget(s, c), gs(r, s), v);
             } else {
                 v = gs(r, c);
             }
@@ -106,76 +122,108 @@ __device__ __forceinline__ void jacobi_solve(const double *G, int ld, int m, int
         A[m][m] = 2.0 * bound + 1.0;
     }
     __syncthreads();
-    const int half = mm / 2;
+    const int half = mm / 2;                 // <= 32: the rotations of a round fit one warp
+    __shared__ int act_idx[SHCI_MAX_SUB / 2];
+    __shared__ int act_pos[SHCI_MAX_SUB / 2];
+    __shared__ int n_act[2];
     for (int sweep = 0; sweep < 30; sweep++) {
         int swept = 0;
         for (int round = 0; round < mm - 1; round++) {
-            // the round's mm/2 disjoint pairs; an inactive pair gets the identity
-            int active = 0;
-            if (tid < half) {
-                int x = tid, y = mm - 1 - tid;
-                int p = x == 0 ? 0 : ((x - 1 + round) % (mm - 1)) + 1;
-                int q = y == 0 ? 0 : ((y - 1 + round) % (mm - 1)) + 1;
-                if (p > q) { int t = p; p = q; q = t; }
-                const double apq = A[p][q];
-                double c = 1.0, s = 0.0;
-                if (fabs(apq) > 1e-14 * (fabs(A[p][p]) + fabs(A[q][q])) + 1e-300) {
-                    active = 1;
-                    const double diff = A[q][q] - A[p][p];
-                    const float tauf = (float)diff / (2.0f * (float)apq);
-                    if (fabs(apq) > 1e-30 && isfinite(tauf)) {
-                        // rotation angle in FP32 (the FP64 divide and square root are
-                        // long dependent chains on this part), then (c, s) renormalised
-                        // in FP64 so that c^2 + s^2 = 1 to FP64 precision: the rotation
-                        // stays exactly orthogonal and zeroes a_pq to ~1e-7 relative,
-                        // which the next sweep finishes
-                        const float tf = copysignf(1.0f, tauf) / (fabsf(tauf) + sqrtf(1.0f + tauf * tauf));
-                        const float cf = rsqrtf(1.0f + tf * tf);
-                        c = (double)cf;
-                        s = (double)(tf * cf);
-                        double f = 1.5 - 0.5 * (c * c + s * s);
-                        c *= f;
-                        s *= f;
-                        f = 1.5 - 0.5 * (c * c + s * s);
-                        c *= f;
-                        s *= f;
-                    } else {
-                        const double tau = diff / (2.0 * apq);
-                        const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-                        c = 1.0 / sqrt(1.0 + t * t);
-                        s = t * c;
+            // warp 0: the round's mm/2 disjoint pairs, their rotations and the list of
+            // active ones (an inactive pair is the identity)
+            if (tid < 32) {
+                int active = 0;
+                if (tid < half) {
+                    int x = tid, y = mm - 1 - tid;
+                    int p = x == 0 ? 0 : ((x - 1 + round) % (mm - 1)) + 1;
+                    int q = y == 0 ? 0 : ((y - 1 + round) % (mm - 1)) + 1;
+                    if (p > q) { int t = p; p = q; q = t; }
+                    const double apq = A[p][q];
+                    double c = 1.0, s = 0.0;
+                    if (fabs(apq) > 1e-14 * (fabs(A[p][p]) + fabs(A[q][q])) + 1e-300) {
+                        active = 1;
+                        const double diff = A[q][q] - A[p][p];
+                        const float tauf = (float)diff / (2.0f * (float)apq);
+                        if (fabs(apq) > 1e-30 && isfinite(tauf)) {
+                            // rotation angle in FP32 (an FP64 divide or square root is a long
+                            // chain of FP64 instructions, and one SM issues few of those),
+                            // then (c, s) renormalised in FP64 so that c^2 + s^2 = 1 to FP64
+                            // precision: the rotation stays exactly orthogonal and zeroes
+                            // a_pq to ~1e-7 relative, which the next sweep finishes
+                            const float tf = copysignf(1.0f, tauf) / (fabsf(tauf) + sqrtf(1.0f + tauf * tauf));
+                            const float cf = rsqrtf(1.0f + tf * tf);
+                            c = (double)cf;
+                            s = (double)(tf * cf);
+                            double f = 1.5 - 0.5 * (c * c + s * s);
+                            c *= f;
+                            s *= f;
+                            f = 1.5 - 0.5 * (c * c + s * s);
+                            c *= f;
+                            s *= f;
+                        } else {
+                            const double tau = diff / (2.0 * apq);
+                            const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+                            c = 1.0 / sqrt(1.0 + t * t);
+                            s = t * c;
+                        }
                     }
+                    cs[tid] = c;
+                    sn[tid] = s;
+                    pp[tid] = p;
+                    qq[tid] = q;
                 }
-                cs[tid] = c;
-                sn[tid] = s;
-                pp[tid] = p;
-                qq[tid] = q;
+                const unsigned mask = __ballot_sync(0xffffffffu, active);
+                const int pos = __popc(mask & ((1u << tid) - 1u));
+                if (active) act_idx[pos] = tid;
+                if (tid < half) act_pos[tid] = active ? pos : -1;
+                if (tid == 0) n_act[round & 1] = __popc(mask);
             }
-            if (!__syncthreads_or(active)) continue;     // uniform: every thread got the same answer
+            __syncthreads();
+            const int na = n_act[round & 1];       // double-buffered: warp 0 may run ahead
+            if (na == 0) continue;                 // uniform
             swept = 1;
-            // A <- J^T A J in one pass: the rotations are disjoint, so the 2 x 2 block
-            // of rows {p_t, q_t} and columns {p_u, q_u} depends only on itself and on
-            // rotations t and u
-            for (int e = tid; e < half * half; e += nt) {
-                const int t = e / half, u = e - t * half;
+            // A <- J^T A J in one pass over 2 x 2 blocks (rows of pair t, columns of
+            // pair u): a block depends only on itself and on rotations t and u.  Only
+            // blocks touched by an active rotation are computed, enumerated densely
+            // (active t, any u; the block of two active pairs once) so that the FP64
+            // work sits in as few warps as possible; the block u, t is written as
+            // the transpose, which keeps A exactly symmetric.
+            for (int e = tid; e < na * half; e += nt) {
+                const int x = e / half, u = e - x * half;
+                const int t = act_idx[x];
+                const int pu = act_pos[u];
+                if (pu >= 0 && pu < x) continue;
                 const int p = pp[t], q = qq[t], r = pp[u], v = qq[u];
                 const double ct = cs[t], st = sn[t], cu = cs[u], su = sn[u];
                 const double apr = A[p][r], apv = A[p][v], aqr = A[q][r], aqv = A[q][v];
                 const double bpr = ct * apr - st * aqr, bpv = ct * apv - st * aqv;   // rows
                 const double bqr = st * apr + ct * aqr, bqv = st * apv + ct * aqv;
-                A[p][r] = cu * bpr - su * bpv;                                      // columns
-                A[p][v] = su * bpr + cu * bpv;
-                A[q][r] = cu * bqr - su * bqv;
-                A[q][v] = su * bqr + cu * bqv;
+                const double npr = cu * bpr - su * bpv, npv = su * bpr + cu * bpv;  // columns
+                const double nqr = cu * bqr - su * bqv, nqv = su * bqr + cu * bqv;
+                if (t == u) {                      // r = p, v = q
+                    A[p][p] = npr;
+                    A[q][q] = nqv;
+                    A[p][q] = npv;
+                    A[q][p] = npv;
+                } else {
+                    A[p][r] = npr;
+                    A[p][v] = npv;
+                    A[q][r] = nqr;
+                    A[q][v] = nqv;
+                    A[r][p] = npr;
+                    A[v][p] = npv;
+                    A[r][q] = nqr;
+                    A[v][q] = nqv;
+                }
             }
-            // Q <- Q J
-            for (int e = tid; e < mm * half; e += nt) {
-                const int i = e / half, t = e - i * half;
+            // Q <- Q J over the active rotations
+            for (int e = tid; e < mm * na; e += nt) {
+                const int i = e / na, t = act_idx[e - i * na];
                 const int p = pp[t], q = qq[t];
                 const double c = cs[t], s = sn[t];
-                const double qp = Q[i][p], qv = Q[i][q];
-                Q[i][p] = c * qp - s * qv;
-                Q[i][q] = s * qp + c * qv;
+                const double qp = qget(i, p), qv = qget(i, q);
+                qset(i, p, c * qp - s * qv);
+                qset(i, q, s * qp + c * qv);
             }
             __syncthreads();
         }
@@ -193,11 +241,13 @@ __device__ __forceinline__ void jacobi_solve(const double *G, int ld, int m, int
         }
         if (rank < m) {
             eval[rank] = va;
-            for (int r = 0; r < m; r++) evec[rank * ld + r] = Q[r][a];
+            for (int r = 0; r < m; r++) evec[rank * ld + r] = qget(r, a);
         }
     }
 }
 
-constexpr size_t JACOBI_SMEM = sizeof(double) * (2 * SHCI_MAX_SUB * (SHCI_MAX_SUB + 1));
+constexpr size_t JACOBI_SMEM_A = sizeof(double) * SHCI_MAX_SUB * (SHCI_MAX_SUB + 1);
+constexpr size_t JACOBI_SMEM = 2 * JACOBI_SMEM_A;
+constexpr int JACOBI_Q_DOUBLES = SHCI_MAX_SUB * (SHCI_MAX_SUB + 1);
 
 }  // namespace shci
