@@ -190,9 +190,10 @@ int shci_energy_backward(shci_ctx *ctx, const double *c, double grad_out_scale, 
  * systems (up to 4 roots each; same stopping rule as shci_davidson) inside
  * one persistent cooperative kernel launch captured in a CUDA graph: each
  * phase of an iteration covers every active system, with grid-wide barriers
- * between phases.  The first call also runs the library's autotuner (rows
- * per stored-sigma work item, CTAs per SM) on a few iterations of the real
- * kernel.  Systems are limited to n_orb <= 64.  The batch keeps using the
+ * between phases.  The first call also runs the library's autotuner on a few
+ * iterations of the real kernel: rows per stored-sigma work item, the
+ * kernel variant (CTAs per SM and register budget) and the stored-row
+ * schedule (a warp per determinant, or 8 lanes per determinant).  Systems are limited to n_orb <= 64.  The batch keeps using the
  * creating context's stream; destroy the batch before the context. */
 typedef struct shci_batch shci_batch;
 
@@ -209,6 +210,7 @@ typedef struct {
     int n_sys, n_stored, n_on_the_fly;
     int64_t total_det, total_nnz_upper;
     int tuned_rows_per_item, tuned_ctas_per_sm;
+    int tuned_lanes_per_row;   /* stored sigma: 32 (a warp per determinant) or 8 */
     double tune_ms;            /* best time of the tuning trials (3 iterations) */
     double solve_ms;           /* last shci_batch_davidson, device time */
     int max_iters;             /* iterations of the slowest system */

@@ -70,6 +70,7 @@ class shci_batch_stats_t(ctypes.Structure):
         ("n_sys", ctypes.c_int), ("n_stored", ctypes.c_int), ("n_on_the_fly", ctypes.c_int),
         ("total_det", ctypes.c_int64), ("total_nnz_upper", ctypes.c_int64),
         ("tuned_rows_per_item", ctypes.c_int), ("tuned_ctas_per_sm", ctypes.c_int),
+        ("tuned_lanes_per_row", ctypes.c_int),
         ("tune_ms", ctypes.c_double), ("solve_ms", ctypes.c_double), ("max_iters", ctypes.c_int),
         ("graph", ctypes.c_int), ("grid_ctas", ctypes.c_int), ("phase_ms", ctypes.c_double * 16),
     ]

@@ -45,9 +45,8 @@ struct BSys {
     const int64_t *rowptr;
     const int32_t *col;
     const double *val, *diag;
-    EnumArgs ea;                           // on-the-fly enumeration (alpha items)
-    const int32_t *b_item_group, *b_item_first;
-    int64_t n_items_b;
+    EnumArgs ea, eb;                       // on-the-fly enumeration: alpha items, beta items
+                                           // (complete, read in place: no per-item copy)
     DevInts I;
     int64_t v_item_off, v_item_cnt;        // this system's vector items
     double *Vb[2], *AVb[2];                // current / rotation target (swapped by index)
@@ -89,6 +88,7 @@ struct BatchArgs {
     const int64_t *a2_local;
     int64_t n_a2;
     int srows;                             // rows per stored-sigma item
+    int lpr;                               // lanes per stored row: 32 or 8
     const int32_t *v_sys;                  // vector items
     const int64_t *v_start;
     int64_t n_v;
@@ -209,23 +209,31 @@ __device__ __forceinline__ double sum_items(const BatchArgs &B, const BSys &S, i
     return v;
 }
 
-// stored rows [r0, r0 + cnt): Y[i][q] = diag_i X[i][q] + sum_j H_ij X[j][q], q < nb
+// stored rows [r0, r0 + cnt): Y[i][q] = diag_i X[i][q] + sum_j H_ij X[j][q], q < nb.
+// LPR lanes per row: 32 is a warp per determinant; fewer lanes work on
+// 32 / LPR rows of a warp at once (short rows leave fewer lanes idle).
+template <int LPR>
 __device__ void sigma_rows(const BSys &S, int nb, int64_t r0, int cnt) {
+    constexpr int RPW = 32 / LPR;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int64_t i = r0 + warp; i < r0 + cnt && i < S.n; i += BT / 32) {
+    const int sub = lane / LPR, sl = lane % LPR;
+    const int64_t r1 = min(r0 + cnt, S.n);
+    for (int64_t i0 = r0 + (int64_t)warp * RPW; i0 < r1; i0 += (BT / 32) * RPW) {
+        const int64_t i = i0 + sub;
+        const bool ok = i < r1;
         double acc[BK] = {0.0, 0.0, 0.0, 0.0};
-        const int64_t beg = S.rowptr[i], end = S.rowptr[i + 1];
+        const int64_t beg = ok ? S.rowptr[i] : 0, end = ok ? S.rowptr[i + 1] : 0;
         // SR nonzeros per lane per step, all loads issued before the FMAs: the
         // persistent grid has few warps per SM, so each warp keeps several
         // gathers of X in flight
         constexpr int SR = 4;
-        for (int64_t p0 = beg + lane; p0 < end; p0 += 32 * SR) {
+        for (int64_t p0 = beg + sl; p0 < end; p0 += LPR * SR) {
             int32_t j[SR];
             double v[SR];
             double2 x01[SR], x23[SR];
 #pragma unroll
             for (int u = 0; u < SR; u++) {
-                const int64_t p = p0 + 32 * u;
+                const int64_t p = p0 + LPR * u;
                 j[u] = p < end ? __ldg(&S.col[p]) : -1;
                 v[u] = p < end ? __ldg(&S.val[p]) : 0.0;
             }
@@ -247,18 +255,32 @@ __device__ void sigma_rows(const BSys &S, int nb, int64_t r0, int cnt) {
                 }
             }
         }
+        // reduce over the row's LPR lanes (the whole warp takes part)
 #pragma unroll
         for (int q = 0; q < BK; q++) {
 #pragma unroll
-            for (int o = 16; o >= 1; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+            for (int o = LPR / 2; o >= 1; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
         }
-        if (lane == 0) {
+        if (ok && sl == 0) {
             const double d = S.diag[i];
 #pragma unroll
             for (int q = 0; q < BK; q++)
                 if (q < nb) S.Y[i * BK + q] = fma(d, __ldcg(&S.X[i * BK + q]), acc[q]);
         }
     }
+}
+
+// The enumeration items of the sigma phases, kept out of line: they are the
+// hot code of an on-the-fly system, and as separate functions they get their
+// registers allocated apart from the rest of the persistent kernel.
+__device__ __noinline__ void batch_alpha_item(const BSys &S, int64_t local, EnumSmem<1> &es, int nb) {
+    unsigned long long cand = 0;
+    enum_alpha_item<1, ENUM_SIGMA, BK>(S.ea, S.I, local, es.T, es.Q[threadIdx.x >> 5], cand, nb);
+}
+
+__device__ __noinline__ void batch_beta_item(const BSys &S, int64_t local, EnumSmem<1> &es, int nb) {
+    unsigned long long cand = 0;
+    enum_beta_item<1, ENUM_SIGMA, BK>(S.eb, S.I, local, es.T, es.Q[threadIdx.x >> 5], cand, nb);
 }
 
 // ---------------------------------------------------------------- the persistent kernel
@@ -341,16 +363,10 @@ __global__ void __launch_bounds__(BT, MINB) k_batch_davidson(BatchArgs B) {
             const int active = ldi(&B.st[s].active), nb = ldi(&B.st[s].nb);
             if (!active || nb == 0) continue;
             if (B.a1_kind[item] == 0) {
-                sigma_rows(S, nb, B.a1_local[item], B.srows);
+                if (B.lpr == 32) sigma_rows<32>(S, nb, B.a1_local[item], B.srows);
+                else sigma_rows<8>(S, nb, B.a1_local[item], B.srows);
             } else {
-                EnumArgs A = S.ea;
-                A.x = S.X;
-                A.y = S.Y;
-                A.diag = S.diag;
-                A.accumulate = 0;
-                A.k_active = nb;
-                unsigned long long cand = 0;
-                enum_alpha_item<1, ENUM_SIGMA, BK>(A, S.I, B.a1_local[item], es.T, es.Q[tid >> 5], cand);
+                batch_alpha_item(S, B.a1_local[item], es, nb);
             }
         }
         if (!grid_sync(B.bar, 1)) return;
@@ -362,17 +378,7 @@ __global__ void __launch_bounds__(BT, MINB) k_batch_davidson(BatchArgs B) {
             const BSys &S = B.sys[s];
             const int active = ldi(&B.st[s].active), nb = ldi(&B.st[s].nb);
             if (!active || nb == 0) continue;
-            EnumArgs A = S.ea;
-            A.item_group = S.b_item_group;
-            A.item_first = S.b_item_first;
-            A.n_items = S.n_items_b;
-            A.x = S.X;
-            A.y = S.Y;
-            A.diag = S.diag;
-            A.accumulate = 1;
-            A.k_active = nb;
-            unsigned long long cand = 0;
-            enum_beta_item<1, ENUM_SIGMA, BK>(A, S.I, B.a2_local[item], es.T, es.Q[tid >> 5], cand);
+            batch_beta_item(S, B.a2_local[item], es, nb);
         }
         if (!grid_sync(B.bar, 2)) return;
 
@@ -407,7 +413,7 @@ __global__ void __launch_bounds__(BT, MINB) k_batch_davidson(BatchArgs B) {
                 const int a = e / nb, q = e % nb;
                 const double v = sum_items(B, S, a * BK + q);
                 S.G[a * S.m_max + m + q] = v;
-                S.G[(m + q) * S.m_max + a] = v;
+                if (a < m) S.G[(m + q) * S.m_max + a] = v;   // the new corner: one writer per entry
             }
             __syncthreads();
             jacobi_solve<false>(S.G, S.m_max, mt, st.m_eig, S.eval, S.evec, sh, S.jq);
@@ -815,7 +821,7 @@ struct shci_batch {
     DevBuf<int64_t> a1_local, a2_local, v_start;
     DevBuf<double> partial;
     int64_t n_a1 = 0, n_a2 = 0, n_v = 0;
-    int srows = 256, blocks_per_sm = 3, grid = 0;
+    int srows = 256, blocks_per_sm = 3, lpr = 32, grid = 0;
     bool tuned = false;
     cudaGraphExec_t gexec = nullptr;
     int graph_max_iter = -1;
@@ -859,6 +865,7 @@ void launch_batch(shci_batch *b, int max_iter, bool capture_ok) {
     A.a2_local = b->a2_local.p;
     A.n_a2 = b->n_a2;
     A.srows = b->srows;
+    A.lpr = b->lpr;
     A.v_sys = b->v_sys.p;
     A.v_start = b->v_start.p;
     A.n_v = b->n_v;
@@ -999,6 +1006,12 @@ void prepare_davidson(shci_batch *b, int k, double tol) {
             S.T2 = b->alloc((size_t)BK * n);
             S.X = b->alloc((size_t)BK * n);
             S.Y = b->alloc((size_t)BK * n);
+            for (EnumArgs *e : {&S.ea, &S.eb}) {
+                e->x = S.X;
+                e->y = S.Y;
+                e->diag = S.diag;
+                e->k_active = 0;
+            }
             S.G = b->alloc((size_t)S.m_max * S.m_max);
             S.evec = b->alloc((size_t)S.m_max * S.m_max);
             S.erot = b->alloc((size_t)S.m_max * S.m_max);
@@ -1059,12 +1072,22 @@ void autotune(shci_batch *b) {
     const int rows_best = best_rows;
     for (int p = shci::BATCH_MINB_LO; p <= shci::BATCH_MINB_HI; p++)
         if (p != 3) trial(rows_best, p);
+    // lanes per stored row: a warp per determinant, or 8 lanes (4 rows per warp)
+    int best_lpr = 32;
+    if (b->stats.n_stored > 0) {
+        const double before = best;
+        b->lpr = 8;
+        trial(best_rows, best_bps);
+        if (best < before) best_lpr = 8;
+    }
+    b->lpr = best_lpr;
     b->srows = best_rows;
     b->blocks_per_sm = best_bps;
     build_worklists(b);
     set_grid(b);
     b->stats.tuned_rows_per_item = best_rows;
     b->stats.tuned_ctas_per_sm = best_bps;
+    b->stats.tuned_lanes_per_row = best_lpr;
     b->stats.tune_ms = best;
     b->tuned = true;
     if (b->gexec) {
@@ -1123,9 +1146,12 @@ int shci_batch_create(shci_ctx *ctx, int n_sys, const shci_system_desc *systems,
             S.ea.item_group = c->item_a_group.p;
             S.ea.item_first = c->item_a_first.p;
             S.ea.n_items = c->n_items_a;
-            S.b_item_group = c->item_b_group.p;
-            S.b_item_first = c->item_b_first.p;
-            S.n_items_b = c->n_items_b;
+            S.ea.accumulate = 0;
+            S.eb = shci::enum_args(c);
+            S.eb.item_group = c->item_b_group.p;
+            S.eb.item_first = c->item_b_first.p;
+            S.eb.n_items = c->n_items_b;
+            S.eb.accumulate = 1;
             S.I = shci::dev_ints(c);
             b->h_sys.push_back(S);
         }

@@ -137,8 +137,12 @@ __global__ void __launch_bounds__(DV_THREADS) k_gram_f(const double *__restrict_
             const int a = a0 + e / NB, b = e % NB;
             o.R[a * NB + b] = v;
             if (o.mode == EP_STORE) {
-                o.dst[(o.a0 + a) * o.ld + o.b0 + b] = v;
-                if (o.sym) o.dst[(o.b0 + b) * o.ld + o.a0 + a] = v;
+                const int r = o.a0 + a, c = o.b0 + b;
+                o.dst[r * o.ld + c] = v;
+                // the mirror, unless it is a product of its own (then both orders
+                // are kept as computed: one writer per entry, deterministic)
+                const bool own = c >= o.a0 && c < o.a0 + na && r >= o.b0 && r < o.b0 + NB;
+                if (o.sym && !own) o.dst[c * o.ld + r] = v;
             }
         }
     }

@@ -252,6 +252,7 @@ struct RowAcc {
     int64_t pos = 0;
     int qn = 0;
     int64_t i = 0;          // the row's determinant (gradient mode)
+    int ka = K;             // vectors in use (sigma mode)
     double ci = 0.0;        // its coefficient (gradient mode)
     double acc[K > 0 ? K : 1];
 };
@@ -292,7 +293,7 @@ __device__ __forceinline__ void flush(RowAcc<MODE, K> &R, const EnumArgs &A, con
                 R.acc[0] = fma(v, c2.x, R.acc[0]);
                 R.acc[K - 1] = fma(v, c2.y, R.acc[K - 1]);
             } else {
-                const int ka = A.k_active ? A.k_active : K;
+                const int ka = R.ka;
 #pragma unroll
                 for (int q = 0; q < K; q++)
                     if (q < ka) R.acc[q] = fma(v, __ldcg(&A.x[(int64_t)j * K + q]), R.acc[q]);
@@ -382,14 +383,18 @@ __device__ __forceinline__ void row_end(RowAcc<MODE, K> &R, const EnumArgs &A, c
         __syncwarp();
     }
     if (MODE == ENUM_SIGMA) {
+        // only the R.ka vectors in use (warp-uniform); the others' outputs are not read
 #pragma unroll
         for (int q = 0; q < K; q++) {
+            if (q < R.ka) {
 #pragma unroll
-            for (int o = 16; o >= 1; o >>= 1) R.acc[q] += __shfl_xor_sync(0xffffffffu, R.acc[q], o);
+                for (int o = 16; o >= 1; o >>= 1) R.acc[q] += __shfl_xor_sync(0xffffffffu, R.acc[q], o);
+            }
         }
         if (valid && lane == 0) {
 #pragma unroll
             for (int q = 0; q < K; q++) {
+                if (q >= R.ka) continue;
                 const int64_t xi = i * K + q;
                 if (A.accumulate) A.y[xi] = __ldcg(&A.y[xi]) + R.acc[q];
                 else A.y[xi] = fma(A.diag[i], __ldcg(&A.x[xi]), R.acc[q]);
@@ -408,7 +413,7 @@ __device__ __forceinline__ void row_end(RowAcc<MODE, K> &R, const EnumArgs &A, c
 // up to ENUM_NW rows of one alpha group, one per warp; called by the whole CTA.
 template <int W, int MODE, int K>
 __device__ __forceinline__ void enum_alpha_item(const EnumArgs &A, const DevInts &I, int64_t item, Tile<W> &T,
-                                                WarpQueue<W> &Q, unsigned long long &cand_local) {
+                                                WarpQueue<W> &Q, unsigned long long &cand_local, int k_active = 0) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr bool NEED_DET = MODE != ENUM_COUNT;
     const int a = A.item_group[item];
@@ -420,6 +425,7 @@ __device__ __forceinline__ void enum_alpha_item(const EnumArgs &A, const DevInts
     const Str<W> Bi = valid ? load_str<W>(A.ga_str, g_beg + r) : Str<W>{};
     RowAcc<MODE, K> R;
     row_begin(R, A, i, valid);
+    R.ka = k_active ? k_active : (A.k_active ? A.k_active : K);
     // same-spin beta: candidates with the same alpha string
     for (int64_t t0 = 0; t0 < g_len; t0 += ENUM_TILE) {
         const int cnt = (int)min((int64_t)ENUM_TILE, g_len - t0);
@@ -543,7 +549,7 @@ __device__ __forceinline__ void enum_alpha_item(const EnumArgs &A, const DevInts
 // the same beta string).  One work item, called by the whole CTA.
 template <int W, int MODE, int K>
 __device__ __forceinline__ void enum_beta_item(const EnumArgs &A, const DevInts &I, int64_t item, Tile<W> &T,
-                                               WarpQueue<W> &Q, unsigned long long &cand_local) {
+                                               WarpQueue<W> &Q, unsigned long long &cand_local, int k_active = 0) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr bool NEED_DET = MODE != ENUM_COUNT;
     const int b = A.item_group[item];
@@ -555,6 +561,7 @@ __device__ __forceinline__ void enum_beta_item(const EnumArgs &A, const DevInts 
     const Str<W> Ai = valid ? load_str<W>(A.gb_str, g_beg + r) : Str<W>{};
     RowAcc<MODE, K> R;
     row_begin(R, A, i, valid);
+    R.ka = k_active ? k_active : (A.k_active ? A.k_active : K);
     for (int64_t t0 = 0; t0 < g_len; t0 += ENUM_TILE) {
         const int cnt = (int)min((int64_t)ENUM_TILE, g_len - t0);
         stage<W, NEED_DET>(T, A.gb_str, A.gb_det, g_beg + t0, cnt);

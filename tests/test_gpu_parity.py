@@ -4,6 +4,8 @@ Bars: connected pair sets bit-exact; H_ij (signed, same convention) and H_ii
 within 1e-12 Ha; sigma within 1e-12 of the row scale sum_j |H_ij c_j|;
 eigenvalues within 1e-9 Ha.
 """
+import time
+
 import numpy as np
 import pytest
 import torch
@@ -159,6 +161,16 @@ def test_selected_space_two_roots(P, oracle_mod):
     assert np.all(np.diff(ts) >= 0.0) and ts[0] >= 0.0
     assert np.all(rn[-1] < 0.1 * np.sqrt(1e-10))
     assert np.all(np.diff(th[:, 0]) <= 1e-10)        # Ritz values never rise (thick restart keeps them)
+    # the part timer: every part accounted, summing to about the call's device time
+    P.shci_set_timing(B.ctx.handle, False, davidson_phases=True)
+    t0 = time.perf_counter()
+    e3, _, _ = B.davidson(2, tol=1e-10)
+    wall_ms = (time.perf_counter() - t0) * 1e3
+    parts = B.stats()["davidson_phase_ms"]
+    np.testing.assert_array_equal(e3, e)
+    assert all(x >= 0.0 for x in parts) and parts[1] > 0.0 and parts[5] > 0.0
+    assert 0.3 * wall_ms < sum(parts) <= wall_ms * 1.05 + 1.0
+    P.shci_set_timing(B.ctx.handle, False)
     # restarting from the converged vectors converges at once to the same roots
     e2, _, it2 = B.davidson(2, tol=1e-10, guess=vecs)
     np.testing.assert_allclose(e2, e_ref, atol=E_TOL, rtol=0)
