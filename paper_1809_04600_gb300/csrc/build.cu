@@ -398,31 +398,13 @@ __global__ void k_occ_prefix(const unsigned long long *__restrict__ occ, int64_t
     }
 }
 
-// estimates of the opposite-spin work: scanning whole alpha groups (per unique
-// alpha string: |G(a)| * sum_{k in singles(a)} |G(k)|) vs looking up every
-// (alpha single, beta single) pair (per determinant: |singles(a)| |singles(b)|)
-__global__ void k_opp_costs(const int64_t *__restrict__ ga_off, const int64_t *__restrict__ as_off,
-                            const int32_t *__restrict__ as_idx, int64_t Ua, const int32_t *__restrict__ ia,
-                            const int32_t *__restrict__ ib, const int64_t *__restrict__ bs_off, int64_t n,
-                            unsigned long long *__restrict__ cost) {
-    unsigned long long scan = 0, look = 0;
-    for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < Ua; a += (int64_t)gridDim.x * blockDim.x) {
-        unsigned long long s = 0;
-        for (int64_t t = as_off[a]; t < as_off[a + 1]; t++) {
-            const int k = as_idx[t];
-            s += ga_off[k + 1] - ga_off[k];
-        }
-        scan += s * (unsigned long long)(ga_off[a + 1] - ga_off[a]);
-    }
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        look += (unsigned long long)(as_off[ia[i] + 1] - as_off[ia[i]]) * (bs_off[ib[i] + 1] - bs_off[ib[i]]);
-    atomicAdd(&cost[0], scan);
-    atomicAdd(&cost[1], look);
-}
 
-// Beta-single lists and the occupancy bitmap, then the choice between
-// scanning and lookups for the opposite-spin doubles (SHCI_OPP_SPIN=scan,
-// lookup or auto overrides the estimate).
+// Beta-single lists and the occupancy bitmap for the opposite-spin doubles.
+// SHCI_OPP_SPIN=scan: no bitmap, every alpha single's group is scanned;
+// lookup: every (alpha single, beta single) pair is looked up; auto (default):
+// the enumeration chooses per alpha single (scan the group when it is short
+// compared with the CTA's beta-single lists, SHCI_OPP_FACTOR times at most).
+// The bitmap is skipped when it would take more than 4 GB.
 template <int W>
 static void opposite_spin_setup(shci_ctx *c) {
     cudaStream_t st = c->st;
@@ -432,6 +414,7 @@ static void opposite_spin_setup(shci_ctx *c) {
     const char *env = getenv("SHCI_OPP_SPIN");
     std::string pref = env ? env : "auto";
     c->opp_lookup = false;
+    c->opp_hybrid = false;
     if (pref == "scan" || bytes > 4.0e9) {
         c->occ.reset();
         c->occ_pref.reset();
@@ -442,21 +425,15 @@ static void opposite_spin_setup(shci_ctx *c) {
     CUDA_TRY(cudaMemsetAsync(c->occ.p, 0, sizeof(unsigned long long) * c->Ua * c->occ_words, st));
     k_occ_set<<<grid_for(c->n_det), 256, 0, st>>>(c->ia.p, c->ib.p, c->n_det, c->occ_words, c->occ.p);
     k_occ_prefix<<<grid_for(c->Ua), 256, 0, st>>>(c->occ.p, c->Ua, c->occ_words, c->occ_pref.p);
-    DevBuf<unsigned long long> cost;
-    cost.alloc(2);
-    CUDA_TRY(cudaMemsetAsync(cost.p, 0, 2 * sizeof(unsigned long long), st));
-    k_opp_costs<<<grid_for(std::max(c->Ua, c->n_det)), 256, 0, st>>>(c->ga_off.p, c->as_off.p, c->as_idx.p, c->Ua,
-                                                                      c->ia.p, c->ib.p, c->bs_off.p, c->n_det,
-                                                                      cost.p);
     KERNEL_CHECK();
-    LAUNCHED(3);
-    unsigned long long h[2];
-    CUDA_TRY(cudaMemcpyAsync(h, cost.p, sizeof(h), cudaMemcpyDeviceToHost, st));
-    CUDA_TRY(cudaStreamSynchronize(st));
-    c->opp_scan_cost = (int64_t)h[0];
-    c->opp_lookup_cost = (int64_t)h[1];
-    // a lookup is a few dependent L2 loads; a scanned candidate is one shared-memory load
-    c->opp_lookup = pref == "lookup" || (pref == "auto" && 4.0 * (double)h[1] < (double)h[0]);
+    LAUNCHED(2);
+    c->opp_lookup = true;
+    c->opp_hybrid = pref != "lookup";
+    // the crossover of the per-alpha-single choice (SHCI_OPP_FACTOR overrides):
+    // 0.5 measured fastest on GB300 among 0.5-4 (24- and 76-orbital shapes)
+    const char *fenv = getenv("SHCI_OPP_FACTOR");
+    c->opp_factor = fenv ? (float)atof(fenv) : 0.5f;
+    if (!(c->opp_factor >= 0.0f)) c->opp_factor = 0.5f;
 }
 
 template <int W>

@@ -53,8 +53,9 @@ struct shci_ctx {
     DevBuf<unsigned long long> occ;
     DevBuf<int32_t> occ_pref;
     int64_t occ_words = 0, n_beta_singles = 0;
-    bool opp_lookup = false;
-    int64_t opp_scan_cost = 0, opp_lookup_cost = 0;
+    bool opp_lookup = false;               // the occupancy bitmap is built
+    bool opp_hybrid = false;               // scan or look up per alpha single
+    float opp_factor = 0.5f;               // scan a group of up to this many x the beta singles
     // enumeration work items: chunks of rows of one alpha (beta) group
     DevBuf<int32_t> item_a_group, item_a_first, item_b_group, item_b_first;
     int64_t n_items_a = 0, n_items_b = 0;

@@ -20,6 +20,8 @@ inline EnumArgs enum_args(const shci_ctx *c) {
     A.as_idx = c->as_idx.p;
     A.work_counter = c->counter.p + 1;
     A.opp_lookup = c->opp_lookup ? 1 : 0;
+    A.opp_hybrid = c->opp_hybrid ? 1 : 0;
+    A.opp_factor = c->opp_factor;
     A.ib = c->ib.p;
     A.bs_off = c->bs_off.p;
     A.bs_idx = c->bs_idx.p;

@@ -39,8 +39,13 @@ struct EnumArgs {
     const uint64_t *ga_str, *gb_str;        // member's other string
     const int64_t *as_off;                  // alpha singles
     const int32_t *as_idx;
-    // opposite-spin lookups (used when opp_lookup != 0)
+    // opposite-spin lookups (used when opp_lookup != 0); with opp_hybrid the
+    // choice is made per alpha single k: scan group k when it has at most
+    // opp_factor times as many members as the CTA's rows have beta singles,
+    // else look up
     int opp_lookup;
+    int opp_hybrid;
+    float opp_factor;
     const int32_t *ib;                      // beta string index of each determinant
     const int64_t *bs_off;                  // beta singles
     const int32_t *bs_idx;
@@ -447,71 +452,31 @@ __device__ __forceinline__ void enum_alpha_item(const EnumArgs &A, const DevInts
         }
         __syncthreads();
     }
-    // opposite-spin doubles: candidates in the groups of the alpha singles of a
+    // opposite-spin doubles: candidates in the groups of the alpha singles of a,
+    // found by scanning each group k (tiles shared by the CTA's warps) or by
+    // looking up every (alpha single k of a, beta single kb of the row's beta
+    // string) in the occupancy bitmap; a hit's rank within row k is its member
+    // offset in alpha group k (members sorted by beta index)
     const int64_t s_beg = A.as_off[a], s_end = A.as_off[a + 1];
+    int sb_len = 0;
+    int64_t sb_beg = 0;
+    __shared__ int sb_max_sh;
+    int sb_max = 0;
     if (A.opp_lookup) {
-        // look up every (alpha single k of a, beta single kb of the row's beta
-        // string) in the occupancy bitmap; a hit's rank within row k is its
-        // member offset in alpha group k (members sorted by beta index).  The
-        // warps of the CTA work independently here.
         if (valid) {
             const int b = A.ib[i];
-            const int64_t sb_beg = A.bs_off[b];
-            const int sb_len = (int)(A.bs_off[b + 1] - sb_beg);
-            for (int64_t s = s_beg; s < s_end; s++) {
-                const int k = A.as_idx[s];
-                int ctx = 1;
-                if (MODE != ENUM_COUNT) {
-                    int pq_a, neg_a;
-                    move_info<W>(Ai, load_str<W>(A.astr, k), pq_a, neg_a);
-                    ctx = (pq_a << 2) | ((neg_a & 1) << 1) | 1;
-                }
-                const unsigned long long *row = A.occ + (int64_t)k * A.occ_words;
-                const int64_t k_off = A.ga_off[k];
-                cand_local += lane == 0 ? sb_len : 0;
-                // LU lookups per lane per step, each stage's loads issued together
-                // (independent L2 gathers in flight instead of one dependent chain)
-                constexpr int LU = W == 1 ? 4 : 2;
-                for (int y0 = 0; y0 < sb_len; y0 += 32 * LU) {
-                    int kb[LU];
-                    unsigned long long word[LU];
-                    bool match[LU];
-                    int32_t j[LU];
-                    Str<W> Bj[LU];
-#pragma unroll
-                    for (int u = 0; u < LU; u++) {
-                        const int y = y0 + 32 * u + lane;
-                        kb[u] = y < sb_len ? __ldg(&A.bs_idx[sb_beg + y]) : -1;
-                    }
-#pragma unroll
-                    for (int u = 0; u < LU; u++) word[u] = kb[u] >= 0 ? __ldg(&row[kb[u] >> 6]) : 0ull;
-#pragma unroll
-                    for (int u = 0; u < LU; u++) {
-                        match[u] = kb[u] >= 0 && ((word[u] >> (kb[u] & 63)) & 1ull);
-                        j[u] = 0;
-                        Bj[u] = Str<W>{};
-                    }
-                    if (NEED_DET) {
-                        int64_t m[LU];
-#pragma unroll
-                        for (int u = 0; u < LU; u++)
-                            m[u] = match[u] ? __ldg(&A.occ_pref[(int64_t)k * A.occ_words + (kb[u] >> 6)]) : 0;
-#pragma unroll
-                        for (int u = 0; u < LU; u++) {
-                            if (match[u]) {
-                                m[u] += k_off + __popcll(word[u] & ((1ull << (kb[u] & 63)) - 1ull));
-                                j[u] = __ldg(&A.ga_det[m[u]]);
-                                Bj[u] = load_str<W>(A.ga_str, m[u]);
-                            }
-                        }
-                    }
-#pragma unroll
-                    for (int u = 0; u < LU; u++) emit<W, MODE, K>(R, A, I, Q, Bi, Ai, match[u], j[u], Bj[u], ctx);
-                }
-            }
+            sb_beg = A.bs_off[b];
+            sb_len = (int)(A.bs_off[b + 1] - sb_beg);
         }
-        row_end<W, MODE, K>(R, A, I, Q, Bi, Ai, i, valid);
-        return;
+        if (A.opp_hybrid) {
+            // the CTA's longest beta-single list: the cost of a lookup pass for its slowest warp
+            if (threadIdx.x == 0) sb_max_sh = 0;
+            __syncthreads();
+            if (lane == 0) atomicMax(&sb_max_sh, sb_len);
+            __syncthreads();
+            sb_max = sb_max_sh;
+            __syncthreads();
+        }
     }
     for (int64_t s = s_beg; s < s_end; s++) {
         const int k = A.as_idx[s];
@@ -521,6 +486,52 @@ __device__ __forceinline__ void enum_alpha_item(const EnumArgs &A, const DevInts
             int pq_a, neg_a;
             move_info<W>(Ai, load_str<W>(A.astr, k), pq_a, neg_a);
             ctx = (pq_a << 2) | ((neg_a & 1) << 1) | 1;
+        }
+        const bool lookup = A.opp_lookup && (!A.opp_hybrid || (float)k_len > A.opp_factor * (float)sb_max);
+        if (lookup) {
+            if (!valid) continue;
+            const unsigned long long *row = A.occ + (int64_t)k * A.occ_words;
+            cand_local += lane == 0 ? sb_len : 0;
+            // LU lookups per lane per step, each stage's loads issued together
+            // (independent L2 gathers in flight instead of one dependent chain)
+            constexpr int LU = W == 1 ? 4 : 2;
+            for (int y0 = 0; y0 < sb_len; y0 += 32 * LU) {
+                int kb[LU];
+                unsigned long long word[LU];
+                bool match[LU];
+                int32_t j[LU];
+                Str<W> Bj[LU];
+#pragma unroll
+                for (int u = 0; u < LU; u++) {
+                    const int y = y0 + 32 * u + lane;
+                    kb[u] = y < sb_len ? __ldg(&A.bs_idx[sb_beg + y]) : -1;
+                }
+#pragma unroll
+                for (int u = 0; u < LU; u++) word[u] = kb[u] >= 0 ? __ldg(&row[kb[u] >> 6]) : 0ull;
+#pragma unroll
+                for (int u = 0; u < LU; u++) {
+                    match[u] = kb[u] >= 0 && ((word[u] >> (kb[u] & 63)) & 1ull);
+                    j[u] = 0;
+                    Bj[u] = Str<W>{};
+                }
+                if (NEED_DET) {
+                    int64_t m[LU];
+#pragma unroll
+                    for (int u = 0; u < LU; u++)
+                        m[u] = match[u] ? __ldg(&A.occ_pref[(int64_t)k * A.occ_words + (kb[u] >> 6)]) : 0;
+#pragma unroll
+                    for (int u = 0; u < LU; u++) {
+                        if (match[u]) {
+                            m[u] += k_beg + __popcll(word[u] & ((1ull << (kb[u] & 63)) - 1ull));
+                            j[u] = __ldg(&A.ga_det[m[u]]);
+                            Bj[u] = load_str<W>(A.ga_str, m[u]);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < LU; u++) emit<W, MODE, K>(R, A, I, Q, Bi, Ai, match[u], j[u], Bj[u], ctx);
+            }
+            continue;
         }
         for (int64_t t0 = 0; t0 < k_len; t0 += ENUM_TILE) {
             const int cnt = (int)min((int64_t)ENUM_TILE, k_len - t0);

@@ -123,13 +123,13 @@ def test_on_the_fly_sigma_and_energy(P, oracle_mod, name, n_det):
     B.close()
 
 
-@pytest.mark.parametrize("opp", ["scan", "lookup"])
+@pytest.mark.parametrize("opp", ["scan", "lookup", "auto"])
 @pytest.mark.parametrize("name,n_det", [("sel_24o_6a6b_1m", 20000), ("sel_76o_14a14b_50m", 3001),
                                         ("fci_10o_4a4b", None)])
 def test_opposite_spin_strategies(P, oracle_mod, monkeypatch, opp, name, n_det):
-    """Both opposite-spin strategies (scanning alpha groups; looking up
-    (alpha single, beta single) pairs in the occupancy bitmap) give the same
-    pairs, values and on-the-fly sigma."""
+    """Every opposite-spin strategy (scanning alpha groups; looking up
+    (alpha single, beta single) pairs in the occupancy bitmap; choosing per
+    alpha single) gives the same pairs, values and on-the-fly sigma."""
     monkeypatch.setenv("SHCI_OPP_SPIN", opp)
     cfg, h, eri, ec, dets = G.system(name, n_det)
     O = oracle_mod.System(h, eri, ec)
