@@ -56,6 +56,20 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
+def replica_totals(dist, seconds, units, device="cpu"):
+    """Whole-job figures of N independent replicas: the slowest rank's time and
+    the units all ranks processed (value = units / time).  ``dist`` is
+    torch.distributed (any backend) or None for one process."""
+    if dist is None:
+        return float(seconds), float(units)
+    import torch
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(u)
+    return float(t.item()), float(u.item())
+
+
 def kernel_source_digest(path):
     import hashlib
     return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
@@ -215,14 +229,7 @@ def run_ours(args):
     vec_mults = st["sigma_vectors"]             # vectors multiplied in the timed region
     sigma_ms = st["sigma_ms_total"]
     units = float(nnz_full) * vec_mults         # full-matrix nonzeros processed
-    if dist:
-        import torch.distributed as dist_
-        t = torch.tensor([ms], device="cuda")
-        dist_.all_reduce(t, op=dist_.ReduceOp.MAX)
-        ms = float(t.item())
-        u = torch.tensor([units], device="cuda", dtype=torch.float64)
-        dist_.all_reduce(u)
-        units = float(u.item())
+    ms, units = replica_totals(dist, ms, units, device="cuda")
     value = units / (ms / 1e3)
 
     # roofline of the dominant kernel (stored sigma): one FP64 FMA per stored
@@ -240,6 +247,10 @@ def run_ours(args):
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(P, H, cfg, h, eri, ec, dets, nnz_full, args)
+        # whole job: units of all replicas over the slowest replica's time
+        t_e2e, u_e2e = replica_totals(dist, e2e["s_per_step"], e2e["value"] * e2e["s_per_step"], device="cuda")
+        e2e["value"] = u_e2e / t_e2e
+        e2e["s_per_step"] = t_e2e
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
