@@ -994,7 +994,10 @@ void prepare_davidson(shci_batch *b, int k, double tol) {
             const int64_t n = c->n_det;
             if (k > n) throw ShciError{SHCI_ERR_INVALID, "k_roots exceeds the size of a system"};
             S.k = k;
-            S.m_max = (int)std::min<int64_t>(std::min(SHCI_MAX_SUB, 16 + 16 * k), n);
+            // the subspace rule of shci_davidson: 16 + 8k vectors with a stored H,
+            // 16 + 16k on the fly (at most 64)
+            const int per_root = c->mode == SHCI_ON_THE_FLY ? 16 : 8;
+            S.m_max = (int)std::min<int64_t>(std::min(SHCI_MAX_SUB, 16 + per_root * k), n);
             if (S.m_max < k) S.m_max = k;
             S.keep = std::max(k, std::min(S.m_max - k, std::max(2 * k, S.m_max / 3)));
             if (S.keep > 24) throw ShciError{SHCI_ERR_INVALID, "restart block exceeds the batch scratch"};

@@ -667,7 +667,11 @@ int davidson(shci_ctx *c, int k, double tol, int max_iter, const double *guess, 
     d.n = c->n_det;
     d.k = k;
     d.st = c->st;
-    d.m_max = (int)std::min<int64_t>(std::min(SHCI_MAX_SUB, 16 + 16 * k), c->n_det);
+    // subspace: larger when a product is expensive (on the fly), where fewer
+    // iterations pay; smaller with a stored H, where the per-iteration vector
+    // work and the eigensolver (both growing with the subspace) are a larger share
+    const int per_root = c->mode == SHCI_ON_THE_FLY ? 16 : 8;
+    d.m_max = (int)std::min<int64_t>(std::min(SHCI_MAX_SUB, 16 + per_root * k), c->n_det);
     if (d.m_max < k) d.m_max = k;
     d.keep = std::max(k, std::min(d.m_max - k, std::max(2 * k, d.m_max / 3)));
     d.vec_blocks = std::max(1, std::min<int>((int)ceil_div(d.n, DV_THREADS), c->n_sm * 8));
