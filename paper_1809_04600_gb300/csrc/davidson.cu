@@ -267,12 +267,11 @@ __global__ void __launch_bounds__(DV_THREADS) k_combine(const double *__restrict
     }
 }
 
-// out[l'] = sum_j M[j * KB + l'] T[j] for l' < KB; slots l' >= *count are
-// zero-filled when zero_fill, otherwise left untouched
+// out[l'] = sum_j M[j * KB + l'] T[j] for l' < *count (the accepted vectors)
 template <int KB>
 __global__ void __launch_bounds__(DV_THREADS) k_apply_coef(const double *__restrict__ T,
                                                           const double *__restrict__ M,
-                                                          const int *__restrict__ count, int zero_fill, int64_t n,
+                                                          const int *__restrict__ count, int64_t n,
                                                           double *__restrict__ out) {
     __shared__ double ms[KB * KB];
     for (int e = threadIdx.x; e < KB * KB; e += blockDim.x) ms[e] = M[e];
@@ -289,8 +288,6 @@ __global__ void __launch_bounds__(DV_THREADS) k_apply_coef(const double *__restr
 #pragma unroll
                 for (int j = 0; j < KB; j++) s = fma(ms[j * KB + l], t[j], s);
                 out[l * n + i] = s;
-            } else if (zero_fill) {
-                out[l * n + i] = 0.0;
             }
         }
     }
@@ -562,8 +559,8 @@ struct Dav {
         g_kernel_launches += 1;
     }
 
-    void apply_coef(const double *T, int kb, double *out, bool zero_fill) {
-#define F(KB) k_apply_coef<KB><<<vec_blocks, DV_THREADS, 0, st>>>(T, M, d_count, zero_fill ? 1 : 0, n, out)
+    void apply_coef(const double *T, int kb, double *out) {
+#define F(KB) k_apply_coef<KB><<<vec_blocks, DV_THREADS, 0, st>>>(T, M, d_count, n, out)
         DISPATCH_K(kb, F)
 #undef F
         KERNEL_CHECK();
@@ -598,7 +595,7 @@ struct Dav {
         q.M = M;
         q.count = d_count;
         gram_dispatch(kb, nullptr, 0, T, kb, T, q, nullptr);
-        apply_coef(T, kb, Vr(m), false);
+        apply_coef(T, kb, Vr(m));
         int added = 0;
         CUDA_TRY(cudaMemcpyAsync(&added, d_count, sizeof(int), cudaMemcpyDeviceToHost, st));
         CUDA_TRY(cudaStreamSynchronize(st));
