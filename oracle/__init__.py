@@ -91,6 +91,10 @@ def _load():
         lib.oracle_rdm2.restype = ctypes.c_int
         lib.oracle_rdm2.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int64, _u64p, _f64p,
                                     ctypes.c_int64, _i32p, _f64p]
+        lib.oracle_select.restype = ctypes.c_int64
+        lib.oracle_select.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, _f64p, _f64p,
+                                      ctypes.c_int64, _u64p, ctypes.c_int, _f64p, ctypes.c_double,
+                                      ctypes.c_int64, _u64p]
         lib.oracle_num_threads.restype = ctypes.c_int
         lib.oracle_num_threads.argtypes = []
         _lib = lib
@@ -163,6 +167,28 @@ class System:
                                dets.shape[0], _p(dets, _u64p), int(i), cap, _p(cols, _i64p), _p(vals, _f64p))
             if m <= cap:
                 return cols[:m].copy(), vals[:m].copy()
+            cap = int(m)
+
+    # ---------------------------------------------------------- selection
+    def select(self, dets, c, eps1) -> np.ndarray:
+        """Determinants outside V selected by the criterion of Sec. II (Eq. 2):
+        some D_i in V has |H_ai| * max_l |c_l[i]| >= eps1.  Brute force over
+        every single and double excitation; rows sorted ascending with the
+        last stored word most significant, no repeats."""
+        dets = _u64(dets)
+        c = _f64(np.atleast_2d(c))
+        W = n_words(dets)
+        lib = _load()
+        cap = 1 << 16
+        while True:
+            out = np.empty((cap, 2 * W), np.uint64)
+            m = lib.oracle_select(self.n, W, self.e_core, _p(self.h, _f64p), _p(self.eri, _f64p),
+                                  dets.shape[0], _p(dets, _u64p), c.shape[0], _p(c, _f64p), float(eps1),
+                                  cap, _p(out, _u64p))
+            if m < 0:
+                raise RuntimeError("oracle_select failed (%d)" % m)
+            if m <= cap:
+                return out[:m].copy()
             cap = int(m)
 
     # ---------------------------------------------------------- sigma

@@ -552,3 +552,93 @@ int oracle_num_threads(void)
     return 1;
 #endif
 }
+
+/* ------------------------------------------------------------ heat-bath selection */
+
+/* ascending order of a determinant read as one 128W-bit integer whose most
+ * significant word is the last stored word (beta word W-1) */
+static int g_sel_words = 2;
+static int cmp_det_desc_words(const void *a, const void *b)
+{
+    const uint64_t *x = (const uint64_t *)a, *y = (const uint64_t *)b;
+    for (int w = g_sel_words - 1; w >= 0; w--) {
+        if (x[w] != y[w]) return x[w] < y[w] ? -1 : 1;
+    }
+    return 0;
+}
+
+/*
+ * The selection criterion of Sec. II (Eq. 2): a determinant D_a outside V is
+ * selected when some D_i in V has |H_ai c_i| >= eps1, c_i taken as the largest
+ * |coefficient| of D_i over the k given vectors c[k][n_det].  Brute force:
+ * every single and double excitation of every D_i is generated, its H_ai
+ * evaluated exactly (Slater-Condon, operator form) and the product compared in
+ * FP64 as |H_ai| * |c_i| >= eps1.  The selected determinants are written to
+ * out (cap rows of 2W words) sorted ascending (last stored word most
+ * significant) without repeats; returns their number (which may exceed cap:
+ * only cap rows are written), -1 on OOM, -2 on duplicate determinants in V.
+ */
+int64_t oracle_select(int n, int W, double e_core, const double *h, const double *eri, int64_t n_det,
+                      const uint64_t *dets, int k, const double *c, double eps1, int64_t cap, uint64_t *out)
+{
+    oints I = {n, W, e_core, h, eri};
+    dtable t;
+    int rc = dtable_init(&t, n_det, W, dets);
+    if (rc) { free(t.slot); return rc; }
+    const int W2 = 2 * W, nso = 2 * n;
+    int64_t m = 0, mcap = 1024;
+    uint64_t *buf = (uint64_t *)malloc(sizeof(uint64_t) * W2 * mcap);
+    if (!buf) { free(t.slot); return -1; }
+    uint64_t x[8];
+    for (int64_t i = 0; i < n_det; i++) {
+        const uint64_t *d = dets + i * W2;
+        double ci = 0.0;
+        for (int l = 0; l < k; l++) ci = fmax(ci, fabs(c[(int64_t)l * n_det + i]));
+        if (ci == 0.0) continue;
+        for (int q = 0; q < nso; q++) {
+            if (!occ(&I, d, q)) continue;
+            for (int pass = 0; pass < 2; pass++) {
+                /* pass 0: singles q -> p; pass 1: doubles {q, s} -> {p, r} */
+                for (int s = (pass ? q + 1 : nso); s < (pass ? nso : nso + 1); s++) {
+                    if (pass && !occ(&I, d, s)) continue;
+                    for (int p = 0; p < nso; p++) {
+                        if (occ(&I, d, p)) continue;
+                        for (int r = (pass ? p + 1 : nso); r < (pass ? nso : nso + 1); r++) {
+                            if (pass && occ(&I, d, r)) continue;
+                            if (!pass && so_spin(&I, p) != so_spin(&I, q)) continue;
+                            if (pass && so_spin(&I, q) + so_spin(&I, s) != so_spin(&I, p) + so_spin(&I, r))
+                                continue;
+                            memcpy(x, d, 8 * W2);
+                            put(&I, x, q, 0);
+                            put(&I, x, p, 1);
+                            if (pass) { put(&I, x, s, 0); put(&I, x, r, 1); }
+                            if (dtable_find(&t, x) >= 0) continue;          /* already in V */
+                            double hv = matrix_element(&I, x, d);
+                            if (!(fabs(hv) * ci >= eps1)) continue;
+                            if (m == mcap) {
+                                mcap *= 2;
+                                uint64_t *nb = (uint64_t *)realloc(buf, sizeof(uint64_t) * W2 * mcap);
+                                if (!nb) { free(buf); free(t.slot); return -1; }
+                                buf = nb;
+                            }
+                            memcpy(buf + m * W2, x, 8 * W2);
+                            m++;
+                        }
+                    }
+                }
+            }
+        }
+    }
+    free(t.slot);
+    g_sel_words = W2;
+    qsort(buf, (size_t)m, sizeof(uint64_t) * W2, cmp_det_desc_words);
+    int64_t u = 0;
+    for (int64_t e = 0; e < m; e++) {
+        if (u > 0 && memcmp(buf + (u - 1) * W2, buf + e * W2, 8 * W2) == 0) continue;
+        if (u != e) memmove(buf + u * W2, buf + e * W2, 8 * W2);
+        u++;
+    }
+    for (int64_t e = 0; e < u && e < cap; e++) memcpy(out + e * W2, buf + e * W2, 8 * W2);
+    free(buf);
+    return u;
+}

@@ -311,3 +311,57 @@ def test_planted_mistake_is_caught(oracle_mod, tmp_path, name):
             got[i, j] = lib.oracle_hij(n, 1, 0.0, h.ctypes.data_as(f64p), eri.ctypes.data_as(f64p),
                                        di.ctypes.data_as(u64p), dj.ctypes.data_as(u64p))
     assert np.max(np.abs(got - ref)) > 1e-6, "planted mistake was not detected"
+
+
+# ---------------------------------------------------------------- heat-bath selection (Sec. II, Eq. 2)
+
+def _excitation_degree(a, b):
+    return int(sum(bin(int(x) ^ int(y)).count("1") for x, y in zip(a, b))) // 2
+
+
+def test_selection_from_one_determinant_reaches_every_connection(oracle_mod):
+    """From V = {HF} with a threshold below every matrix element, the selected
+    set is every determinant one or two excitations away: 804 for 10 orbitals
+    with 4a4b (24 + 24 singles, 90 + 90 same-spin and 576 opposite-spin
+    doubles), each at excitation degree 1 or 2 from HF."""
+    h, eri, ec = S.integrals(10, 20, 1000)
+    hf = S.fci_dets(10, 4, 4)[:1]
+    O = oracle_mod.System(h, eri, ec)
+    sel = O.select(hf, np.ones((1, 1)), 1e-14)
+    assert sel.shape[0] == 804
+    deg = [_excitation_degree(hf[0], d) for d in sel]
+    assert sorted(set(deg)) == [1, 2]
+    assert deg.count(1) == 48
+
+
+def test_selection_matches_dense_hamiltonian(oracle_mod):
+    """V a random subset of the full-CI space (8 orbitals, 3a2b): the selected
+    set equals {a outside V : max_i |H_ai| |c_i| >= eps1} read off the dense
+    full-CI matrix (whose entries the Jordan-Wigner pin checks), borderline
+    products aside; a larger eps1 selects a subset; V = full space selects
+    nothing."""
+    n, na, nb = 8, 3, 2
+    h, eri, ec = S.integrals(n, 10, 4242)
+    fci = S.fci_dets(n, na, nb)
+    O = oracle_mod.System(h, eri, ec)
+    H = O.dense_h(fci)
+    rng = np.random.default_rng(3)
+    vidx = np.sort(rng.choice(fci.shape[0], 25, replace=False))
+    c = rng.standard_normal((2, vidx.size))
+    cmax = np.max(np.abs(c), axis=0)
+    prod = np.abs(H[:, vidx]) * cmax[None, :]
+    prod[vidx, :] = 0.0                              # determinants already in V are never selected
+    best = prod.max(axis=1)
+    key = lambda d: tuple(int(x) for x in d[::-1])   # last stored word most significant
+    prev = None
+    for eps1 in (1e-1, 1e-2, 1e-3):
+        sel = O.select(fci[vidx], c, eps1)
+        got = {key(d) for d in sel}
+        want = {key(fci[a]) for a in np.nonzero(best >= eps1)[0]}
+        border = {key(fci[a]) for a in np.nonzero(np.abs(best - eps1) <= 1e-12 * eps1)[0]}
+        assert got - border == want - border
+        assert [key(d) for d in sel] == sorted(got)  # ascending, no repeats
+        if prev is not None:
+            assert prev <= got                       # smaller eps1: superset
+        prev = got
+    assert O.select(fci, np.ones((1, fci.shape[0])), 1e-6).shape[0] == 0
