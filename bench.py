@@ -574,6 +574,55 @@ def run_adjoint(args):
     ctx.close()
 
 
+def run_select(args):
+    """Heat-bath selection (Sec. II, Eq. 2) from the bench's 1e6-determinant
+    space with its converged 2-root coefficients: GPU time per selection, the
+    candidates and new determinants, and the oracle's brute force on a sample
+    of determinants of V on the host cores."""
+    torch, P = _gpu_setup()
+    import oracle as O
+    cfg = S.config(args.config)
+    h, eri, ec, dets = S.make_system(cfg)
+    ctx = P.Context(0, torch.cuda.current_stream())
+    H = ctx.handle
+    P.shci_load_integrals(H, cfg.n_orb, ec, _dev(torch, h), _dev(torch, eri))
+    P.shci_build_connectivity(H, cfg.n_alpha, cfg.n_beta, _dev(torch, dets), P.SHCI_STORED)
+    vecs = torch.empty((cfg.roots, dets.shape[0]), dtype=torch.float64, device="cuda")
+    P.shci_davidson(H, cfg.roots, TOL, MAX_ITER, vecs=vecs)
+    lines = []
+    for eps1 in (args.eps1 or [1e-4, 3e-5]):
+        t = time.perf_counter()
+        new = P.shci_select(H, vecs, eps1)
+        torch.cuda.synchronize()
+        first = time.perf_counter() - t
+        cap = int(new.shape[0])                 # one call per selection from here on
+        times = []
+        for _ in range(max(1, args.steps)):
+            t = time.perf_counter()
+            new = P.shci_select(H, vecs, eps1, cap=cap)
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t)
+        st = P.shci_get_stats(H)
+        # the oracle on a sample of V (same coefficients), timed on the host cores
+        rng = np.random.default_rng(0)
+        samp = np.sort(rng.choice(dets.shape[0], args.select_sample, replace=False))
+        c_h = vecs.cpu().numpy()
+        osys = O.System(h, eri, ec)
+        t = time.perf_counter()
+        osys.select(dets[samp], c_h[:, samp], eps1)
+        t_or = time.perf_counter() - t
+        lines.append({"eps1": eps1, "n_det": int(dets.shape[0]), "new_dets": int(new.shape[0]),
+                      "candidates": st["select_candidates"], "first_call_s": first,
+                      "select_s": float(np.median(times)), "select_device_ms": st["select_ms"],
+                      "dets_screened_per_s": dets.shape[0] / float(np.median(times)),
+                      "oracle": {"sample_dets": int(samp.size), "seconds": t_or,
+                                 "dets_screened_per_s": samp.size / t_or, "cores": 1,
+                                 "kind": "brute force over every single and double excitation"}})
+    print(json.dumps({"workload": workload_desc(cfg) + ", heat-bath selection with the converged 2-root "
+                                                       "coefficients", "lines": lines}))
+    ctx.close()
+
+
 BATCH_PHASES = ("start", "sigma_stored_and_alpha_items", "sigma_beta_items", "gram_columns", "eigensolver",
                 "ritz_residuals", "convergence_restart", "basis_rotation", "second_pass_coef", "second_projection",
                 "cholqr1_coef", "cholqr_apply", "cholqr2_coef", "next_block", "bookkeeping")
@@ -661,12 +710,15 @@ def main():
                     help="profiling only: a smaller space of the same shape (not a bench line)")
     ap.add_argument("--sigma-only", type=int, default=0,
                     help="profiling only: build once, then launch the sigma kernel this many times")
-    ap.add_argument("--workload", default="main", choices=["main", "fci", "large", "adjoint", "batch"],
+    ap.add_argument("--workload", default="main", choices=["main", "fci", "large", "adjoint", "batch", "select"],
                     help="main: the bench line; others print the measurement line of another workload")
     ap.add_argument("--batch-budget-gb", type=float, default=180.0)
+    ap.add_argument("--eps1", type=float, action="append", help="selection thresholds (select workload)")
+    ap.add_argument("--select-sample", type=int, default=200, help="determinants of V the oracle screens")
     args = ap.parse_args()
     if args.workload != "main":
-        {"fci": run_fci, "large": run_large, "adjoint": run_adjoint, "batch": run_batch}[args.workload](args)
+        {"fci": run_fci, "large": run_large, "adjoint": run_adjoint, "batch": run_batch,
+         "select": run_select}[args.workload](args)
     elif args.sigma_only:
         run_sigma_only(args)
     elif args.impl == "reference":

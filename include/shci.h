@@ -164,6 +164,23 @@ int shci_davidson(shci_ctx *ctx, int k_roots, double tol, int max_iter, const do
  * cap < 0 or n_out is NULL. */
 int shci_davidson_history(shci_ctx *ctx, int cap, double *theta, double *rnorm, double *t_s, int *n_out);
 
+/* Heat-bath selection (Sec. II, Eq. 2): the determinants D_a outside V for
+ * which some D_i in V has |H_ai| * |c_i| >= eps1, |c_i| being the largest
+ * |coefficient| of D_i over the k_roots vectors c[k_roots][n_det] (mem_space).
+ * Double excitations come from per-orbital-pair lists of |H| sorted in
+ * decreasing order (built on the first call after shci_load_integrals), each
+ * walked until its elements fall below eps1 / |c_i|; single excitations are
+ * evaluated exactly.  The comparison is |H_ai| * |c_i| >= eps1 in FP64.
+ * new_dets (mem_space) receives min(cap, count) rows of 2W words in the
+ * layout of shci_build_connectivity, ascending as 128W-bit integers whose
+ * most significant word is the last (beta word W-1), without repeats; *n_new
+ * (host) = count.  cap = 0 with new_dets = NULL queries the count.  Needs a
+ * completed shci_build_connectivity (either mode), k_roots in [1, 8], eps1
+ * positive and finite, n_orb <= 128; at most 2^32 - 1 candidates before
+ * removing repeats (SHCI_ERR_INVALID otherwise: raise eps1). */
+int shci_select(shci_ctx *ctx, int k_roots, const double *c, double eps1, int64_t cap, uint64_t *new_dets,
+                int64_t *n_new, int mem_space);
+
 /* Adjoint of a variational eigenvalue (no counterpart in the paper, which
  * has no derivatives): for a normalised real eigenvector c of H on V,
  * E = c^T H c and, by Hellmann-Feynman, dE/dX = c^T (dH/dX) c.  Writes
@@ -257,6 +274,8 @@ typedef struct {
      * residuals (with the read of the Ritz values), 3 restarts,
      * 4 orthonormalisation, 5 sigma (with layout changes), 6 new Gram columns */
     double davidson_phase_ms[8];
+    double select_ms;           /* last shci_select, device time (lists included when built) */
+    int64_t select_candidates;  /* last shci_select: candidates before removing repeats and V */
 } shci_stats_t;
 
 /* Fill *out.  Kernel times are recorded only while timing is enabled. */

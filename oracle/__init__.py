@@ -94,7 +94,7 @@ def _load():
         lib.oracle_select.restype = ctypes.c_int64
         lib.oracle_select.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, _f64p, _f64p,
                                       ctypes.c_int64, _u64p, ctypes.c_int, _f64p, ctypes.c_double,
-                                      ctypes.c_int64, _u64p]
+                                      ctypes.c_int64, _u64p, _f64p]
         lib.oracle_num_threads.restype = ctypes.c_int
         lib.oracle_num_threads.argtypes = []
         _lib = lib
@@ -170,11 +170,12 @@ class System:
             cap = int(m)
 
     # ---------------------------------------------------------- selection
-    def select(self, dets, c, eps1) -> np.ndarray:
+    def select(self, dets, c, eps1, with_best=False):
         """Determinants outside V selected by the criterion of Sec. II (Eq. 2):
         some D_i in V has |H_ai| * max_l |c_l[i]| >= eps1.  Brute force over
         every single and double excitation; rows sorted ascending with the
-        last stored word most significant, no repeats."""
+        last stored word most significant, no repeats.  with_best: also the
+        largest product of each over V."""
         dets = _u64(dets)
         c = _f64(np.atleast_2d(c))
         W = n_words(dets)
@@ -182,13 +183,14 @@ class System:
         cap = 1 << 16
         while True:
             out = np.empty((cap, 2 * W), np.uint64)
+            best = np.empty(cap)
             m = lib.oracle_select(self.n, W, self.e_core, _p(self.h, _f64p), _p(self.eri, _f64p),
                                   dets.shape[0], _p(dets, _u64p), c.shape[0], _p(c, _f64p), float(eps1),
-                                  cap, _p(out, _u64p))
+                                  cap, _p(out, _u64p), _p(best, _f64p))
             if m < 0:
                 raise RuntimeError("oracle_select failed (%d)" % m)
             if m <= cap:
-                return out[:m].copy()
+                return (out[:m].copy(), best[:m].copy()) if with_best else out[:m].copy()
             cap = int(m)
 
     # ---------------------------------------------------------- sigma

@@ -555,7 +555,8 @@ int oracle_num_threads(void)
 
 /* ------------------------------------------------------------ heat-bath selection */
 
-/* ascending order of a determinant read as one 128W-bit integer whose most
+/* records of 2W determinant words followed by the bits of the best product;
+ * ascending order of the words read as one 128W-bit integer whose most
  * significant word is the last stored word (beta word W-1) */
 static int g_sel_words = 2;
 static int cmp_det_desc_words(const void *a, const void *b)
@@ -575,19 +576,21 @@ static int cmp_det_desc_words(const void *a, const void *b)
  * evaluated exactly (Slater-Condon, operator form) and the product compared in
  * FP64 as |H_ai| * |c_i| >= eps1.  The selected determinants are written to
  * out (cap rows of 2W words) sorted ascending (last stored word most
- * significant) without repeats; returns their number (which may exceed cap:
- * only cap rows are written), -1 on OOM, -2 on duplicate determinants in V.
+ * significant) without repeats, and, when best is not NULL, the largest
+ * product |H_ai| |c_i| over V of each; returns their number (which may exceed
+ * cap: only cap rows are written), -1 on OOM, -2 on duplicate determinants.
  */
 int64_t oracle_select(int n, int W, double e_core, const double *h, const double *eri, int64_t n_det,
-                      const uint64_t *dets, int k, const double *c, double eps1, int64_t cap, uint64_t *out)
+                      const uint64_t *dets, int k, const double *c, double eps1, int64_t cap, uint64_t *out,
+                      double *best)
 {
     oints I = {n, W, e_core, h, eri};
     dtable t;
     int rc = dtable_init(&t, n_det, W, dets);
     if (rc) { free(t.slot); return rc; }
-    const int W2 = 2 * W, nso = 2 * n;
+    const int W2 = 2 * W, nso = 2 * n, R = 2 * W + 1;
     int64_t m = 0, mcap = 1024;
-    uint64_t *buf = (uint64_t *)malloc(sizeof(uint64_t) * W2 * mcap);
+    uint64_t *buf = (uint64_t *)malloc(sizeof(uint64_t) * R * mcap);
     if (!buf) { free(t.slot); return -1; }
     uint64_t x[8];
     for (int64_t i = 0; i < n_det; i++) {
@@ -613,15 +616,16 @@ int64_t oracle_select(int n, int W, double e_core, const double *h, const double
                             put(&I, x, p, 1);
                             if (pass) { put(&I, x, s, 0); put(&I, x, r, 1); }
                             if (dtable_find(&t, x) >= 0) continue;          /* already in V */
-                            double hv = matrix_element(&I, x, d);
-                            if (!(fabs(hv) * ci >= eps1)) continue;
+                            const double prod = fabs(matrix_element(&I, x, d)) * ci;
+                            if (!(prod >= eps1)) continue;
                             if (m == mcap) {
                                 mcap *= 2;
-                                uint64_t *nb = (uint64_t *)realloc(buf, sizeof(uint64_t) * W2 * mcap);
+                                uint64_t *nb = (uint64_t *)realloc(buf, sizeof(uint64_t) * R * mcap);
                                 if (!nb) { free(buf); free(t.slot); return -1; }
                                 buf = nb;
                             }
-                            memcpy(buf + m * W2, x, 8 * W2);
+                            memcpy(buf + m * R, x, 8 * W2);
+                            memcpy(buf + m * R + W2, &prod, 8);
                             m++;
                         }
                     }
@@ -631,14 +635,23 @@ int64_t oracle_select(int n, int W, double e_core, const double *h, const double
     }
     free(t.slot);
     g_sel_words = W2;
-    qsort(buf, (size_t)m, sizeof(uint64_t) * W2, cmp_det_desc_words);
+    qsort(buf, (size_t)m, sizeof(uint64_t) * R, cmp_det_desc_words);
     int64_t u = 0;
     for (int64_t e = 0; e < m; e++) {
-        if (u > 0 && memcmp(buf + (u - 1) * W2, buf + e * W2, 8 * W2) == 0) continue;
-        if (u != e) memmove(buf + u * W2, buf + e * W2, 8 * W2);
+        if (u > 0 && memcmp(buf + (u - 1) * R, buf + e * R, 8 * W2) == 0) {
+            double a, b;
+            memcpy(&a, buf + (u - 1) * R + W2, 8);
+            memcpy(&b, buf + e * R + W2, 8);
+            if (b > a) memcpy(buf + (u - 1) * R + W2, &b, 8);
+            continue;
+        }
+        if (u != e) memmove(buf + u * R, buf + e * R, 8 * R);
         u++;
     }
-    for (int64_t e = 0; e < u && e < cap; e++) memcpy(out + e * W2, buf + e * W2, 8 * W2);
+    for (int64_t e = 0; e < u && e < cap; e++) {
+        memcpy(out + e * W2, buf + e * R, 8 * W2);
+        if (best) memcpy(best + e, buf + e * R + W2, 8);
+    }
     free(buf);
     return u;
 }

@@ -37,7 +37,7 @@ EXPORTED = [
     "shci_create", "shci_destroy", "shci_last_error", "shci_load_integrals", "shci_build_connectivity",
     "shci_get_diag", "shci_get_pairs", "shci_get_row", "shci_sigma", "shci_sigma_noalloc", "shci_energy_backward",
     "shci_batch_create", "shci_batch_davidson", "shci_batch_get_stats", "shci_batch_destroy", "shci_davidson",
-    "shci_davidson_history", "shci_get_stats", "shci_set_timing",
+    "shci_davidson_history", "shci_select", "shci_get_stats", "shci_set_timing",
 ]
 
 
@@ -54,6 +54,7 @@ class shci_stats_t(ctypes.Structure):
         ("build_ms", ctypes.c_double), ("sigma_ms_total", ctypes.c_double), ("sigma_launches", ctypes.c_int64),
         ("sigma_vectors", ctypes.c_int64), ("kernel_launches", ctypes.c_int64), ("davidson_iters", ctypes.c_int),
         ("mode", ctypes.c_int), ("n_words", ctypes.c_int), ("davidson_phase_ms", ctypes.c_double * 8),
+        ("select_ms", ctypes.c_double), ("select_candidates", ctypes.c_int64),
     ]
 
 
@@ -106,6 +107,7 @@ def load_library(path: str = LIB_PATH):
         "shci_batch_destroy": (None, [vp]),
         "shci_davidson": (i32, [vp, i32, f64, i32, vp, vp, vp, i32, ctypes.POINTER(i32)]),
         "shci_davidson_history": (i32, [vp, i32, vp, vp, vp, ctypes.POINTER(i32)]),
+        "shci_select": (i32, [vp, i32, vp, f64, i64, vp, ctypes.POINTER(i64), i32]),
         "shci_get_stats": (i32, [vp, ctypes.POINTER(shci_stats_t)]),
         "shci_set_timing": (i32, [vp, i32]),
     }
@@ -266,6 +268,30 @@ def shci_davidson_history(ctx, k_roots):
     _check(ctx, lib.shci_davidson_history(ctx, n.value, th.ctypes.data, rn.ctypes.data, ts.ctypes.data,
                                           ctypes.byref(n)))
     return th, rn, ts
+
+
+def shci_select(ctx, c, eps1, cap=None):
+    """Heat-bath selection: the new determinants [count, 2W] (uint64 numpy for a
+    host c, int64 torch tensor on c's device for a device c), ascending, no
+    repeats.  c: [k, n_det] (or [n_det]) coefficients of V."""
+    lib = load_library()
+    pc, mc, kc = _ptr(c, np.float64)
+    k = 1 if len(c.shape) == 1 else int(c.shape[0])
+    n_det = int(c.shape[-1])
+    W = shci_get_stats(ctx)["n_words"]
+    cap = max(1024, 2 * n_det) if cap is None else int(cap)
+    n = ctypes.c_int64(0)
+    while True:
+        if mc == SHCI_MEM_DEVICE:
+            import torch
+            out = torch.empty((max(cap, 1), 2 * W), dtype=torch.int64, device=c.device)
+        else:
+            out = np.empty((max(cap, 1), 2 * W), np.uint64)
+        po, mo, ko = _ptr(out, np.uint64)
+        _check(ctx, lib.shci_select(ctx, k, pc, float(eps1), cap, po, ctypes.byref(n), mc))
+        if n.value <= cap:
+            return out[:n.value]
+        cap = int(n.value)
 
 
 def shci_energy_backward(ctx, c, grad_out_scale, dE_dh, dE_deri_packed):

@@ -215,6 +215,14 @@ int shci_davidson_history(shci_ctx *c, int cap, double *theta, double *rnorm, do
     });
 }
 
+int shci_select(shci_ctx *c, int k, const double *coef, double eps1, int64_t cap, uint64_t *out, int64_t *n_out,
+                int mem) {
+    return guarded(c, [&] {
+        shci::select_dets(c, k, coef, eps1, cap, out, n_out, mem);
+        return SHCI_OK;
+    });
+}
+
 int shci_get_stats(shci_ctx *c, shci_stats_t *out) {
     return guarded(c, [&] {
         if (!out) throw ShciError{SHCI_ERR_INVALID, "null pointer"};

@@ -74,6 +74,7 @@ void load_integrals(shci_ctx *c, int n_orb, double e_core, const double *h, cons
     c->n_orb = n_orb;
     c->e_core = e_core;
     c->have_ints = true;
+    c->hb_valid = false;
 }
 
 DevInts dev_ints(const shci_ctx *c) {

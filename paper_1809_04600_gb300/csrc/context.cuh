@@ -19,6 +19,17 @@ struct DavidsonWork {
     double *h_status = nullptr;  // pinned host mirror of the status block
 };
 
+// Double excitations from one orbital pair, sorted by decreasing |H| (CSR
+// over the pair slot p * n + q): target pair (r | s << 16), |H|, and |H|
+// rounded toward zero to FP32 (the sort key).
+struct HBList {
+    DevBuf<int64_t> off;
+    DevBuf<uint32_t> rs;
+    DevBuf<double> val;
+    DevBuf<float> kf;
+    int64_t entries = 0;
+};
+
 struct shci_ctx {
     int device = 0;
     cudaStream_t st = nullptr;
@@ -31,6 +42,9 @@ struct shci_ctx {
     int n_orb = 0;
     double e_core = 0.0;
     DevBuf<double> h, eri, jk1, j1, jdiag, kdiag;
+    // heat-bath lists for the selection (built on first use per set of integrals)
+    bool hb_valid = false;
+    HBList hb_same, hb_opp;
 
     // variational space and helper lists (Table I)
     bool built = false;
@@ -103,6 +117,10 @@ void export_pairs(shci_ctx *c, int64_t cap, int64_t *i_out, int64_t *j_out, doub
 // sigma.cu: y = H x for k vectors; `inter` selects the interleaved [n][k]
 // layout (otherwise vector-major [k][n]).
 void sigma(shci_ctx *c, int k, const double *x, double *y, bool inter);
+
+// select.cu: heat-bath selection of new determinants (Sec. II)
+void select_dets(shci_ctx *c, int k, const double *coef, double eps1, int64_t cap, uint64_t *out, int64_t *n_out,
+                 int mem);
 
 // davidson.cu
 int davidson(shci_ctx *c, int k, double tol, int max_iter, const double *guess, double *energies,

@@ -1,0 +1,458 @@
+// Heat-bath selection of new determinants (Sec. II, Eq. 2): D_a outside V is
+// selected when some D_i in V has |H_ai c_i| >= eps1.
+//
+// Double excitations are found the way the paper describes: for every pair
+// of occupied orbitals, the magnitudes of the matrix elements of all double
+// excitations from that pair depend only on the four orbitals, so they are
+// computed once per set of integrals and stored sorted in decreasing order;
+// a determinant walks the list of each of its occupied pairs and stops at
+// the first element below eps1 / |c_i|.  Single excitations depend on the
+// whole determinant and are evaluated exactly (Slater-Condon) for every
+// occupied -> virtual move.  Candidates are written per determinant (count
+// pass, scan, fill pass), sorted as multi-word integers, made unique and
+// removed when already in V.
+#include <algorithm>
+#include <cfloat>
+#include <cmath>
+
+#include "context.cuh"
+#include "enumerate.cuh"
+
+namespace shci {
+
+constexpr int SEL_THREADS = 256;
+
+// ---------------------------------------------------------------- sorted double-excitation lists
+
+// Tuple t = ((p n + q) n + r) n + s.  List 0 (same spin): p < q, r < s,
+// {r, s} disjoint from {p, q}, magnitude |(pr|qs) - (ps|qr)|.  List 1
+// (opposite spin, p and r alpha, q and s beta): r != p, s != q, magnitude
+// |(pr|qs)|.  Entries with magnitude 0 never meet eps1 > 0 and are dropped.
+__device__ __forceinline__ bool hb_entry(const DevInts &I, int same, int64_t t, int &slot, int &r, int &s,
+                                         double &v) {
+    const int n = I.n;
+    s = (int)(t % n);
+    r = (int)((t / n) % n);
+    const int q = (int)((t / ((int64_t)n * n)) % n);
+    const int p = (int)(t / ((int64_t)n * n * n));
+    slot = p * n + q;
+    if (same) {
+        if (!(p < q && r < s) || r == p || r == q || s == p || s == q) return false;
+        v = fabs(eri_get(I, p, r, q, s) - eri_get(I, p, s, q, r));
+    } else {
+        if (r == p || s == q) return false;
+        v = fabs(eri_get(I, p, r, q, s));
+    }
+    return v > 0.0;
+}
+
+// key: slot in the high word, then the magnitude rounded toward zero to FP32
+// with its bits inverted (ascending keys = decreasing magnitude); excluded
+// tuples get the largest key and sort last
+__global__ void k_hb_gen(const DevInts I, int same, int64_t total, uint64_t *__restrict__ keys,
+                         uint32_t *__restrict__ vals, unsigned long long *__restrict__ cnt) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        int slot, r, s;
+        double v;
+        vals[t] = (uint32_t)t;
+        if (!hb_entry(I, same, t, slot, r, s, v)) {
+            keys[t] = ~0ull;
+            continue;
+        }
+        const uint32_t fb = __float_as_uint(__double2float_rz(v));
+        keys[t] = ((uint64_t)slot << 32) | (uint64_t)(~fb);
+        atomicAdd(&cnt[slot], 1ull);
+    }
+}
+
+__global__ void k_hb_final(const DevInts I, int same, int64_t n_valid, const uint32_t *__restrict__ vals,
+                           uint32_t *__restrict__ rs, double *__restrict__ val, float *__restrict__ kf) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n_valid;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int slot, r, s;
+        double v = 0.0;
+        hb_entry(I, same, (int64_t)vals[e], slot, r, s, v);
+        rs[e] = (uint32_t)r | ((uint32_t)s << 16);
+        val[e] = v;
+        kf[e] = __double2float_rz(v);
+    }
+}
+
+static void build_hb_list(shci_ctx *c, int same, HBList &L) {
+    cudaStream_t st = c->st;
+    const int n = c->n_orb;
+    const int64_t total = (int64_t)n * n * n * n;
+    const DevInts I = dev_ints(c);
+    DevBuf<uint64_t> keys;
+    DevBuf<uint32_t> vals;
+    DevBuf<unsigned long long> cnt;
+    keys.alloc((size_t)total);
+    vals.alloc((size_t)total);
+    cnt.alloc((size_t)n * n + 1);
+    CUDA_TRY(cudaMemsetAsync(cnt.p, 0, sizeof(unsigned long long) * (n * n + 1), st));
+    const int blocks = (int)std::min<int64_t>(ceil_div(total, SEL_THREADS), (int64_t)c->n_sm * 16);
+    k_hb_gen<<<blocks, SEL_THREADS, 0, st>>>(I, same, total, keys.p, vals.p, cnt.p);
+    KERNEL_CHECK();
+    g_kernel_launches += 1;
+    radix_sort<1>(keys.p, vals.p, total, c->sw, st);
+    L.off.alloc((size_t)n * n + 1);
+    DevBuf<int64_t> tmp;
+    tmp.alloc((size_t)scan_tmp_len(n * n + 1));
+    exclusive_scan<int64_t>(reinterpret_cast<const int64_t *>(cnt.p), L.off.p, (int64_t)n * n, tmp.p, st);
+    int64_t n_valid = 0;
+    CUDA_TRY(cudaMemcpyAsync(&n_valid, L.off.p + (int64_t)n * n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    L.rs.alloc((size_t)std::max<int64_t>(n_valid, 1));
+    L.val.alloc((size_t)std::max<int64_t>(n_valid, 1));
+    L.kf.alloc((size_t)std::max<int64_t>(n_valid, 1));
+    if (n_valid > 0) {
+        k_hb_final<<<(int)std::min<int64_t>(ceil_div(n_valid, SEL_THREADS), (int64_t)c->n_sm * 16), SEL_THREADS, 0,
+                     st>>>(I, same, n_valid, vals.p, L.rs.p, L.val.p, L.kf.p);
+        KERNEL_CHECK();
+        g_kernel_launches += 1;
+    }
+    L.entries = n_valid;
+    CUDA_TRY(cudaStreamSynchronize(st));
+}
+
+// ---------------------------------------------------------------- selection kernels
+
+struct SelArgs {
+    int64_t n_det;
+    const uint64_t *dets;                   // [n][2W]
+    int k;
+    const double *c;                        // [k][n]
+    double eps1;
+    int n, na, nb;
+    const int64_t *ss_off, *os_off;
+    const uint32_t *ss_rs, *os_rs;
+    const double *ss_v, *os_v;
+    const float *ss_kf, *os_kf;
+    unsigned long long *cnt;                // count pass: candidates per determinant
+    const int64_t *off;                     // fill pass: first slot of each determinant
+    uint64_t *out;                          // fill pass: [total][2W]
+};
+
+// orbital of the x-th (0-based) set bit of s
+template <int W>
+__device__ __forceinline__ int nth_set(const Str<W> &s, int x) {
+#pragma unroll
+    for (int k = 0; k < W; k++) {
+        const int c = __popcll(s.w[k]);
+        if (x < c) {
+            uint64_t m = s.w[k];
+            for (int j = 0; j < x; j++) m &= m - 1;
+            return 64 * k + __ffsll((long long)m) - 1;
+        }
+        x -= c;
+    }
+    return -1;
+}
+
+// orbital of the y-th (0-based) empty orbital below n
+template <int W>
+__device__ __forceinline__ int nth_unset(const Str<W> &s, int y, int n) {
+#pragma unroll
+    for (int k = 0; k < W; k++) {
+        const int lo = 64 * k;
+        if (lo >= n) break;
+        const int nb = min(64, n - lo);
+        const uint64_t mask = nb == 64 ? ~0ull : ((1ull << nb) - 1);
+        uint64_t m = ~s.w[k] & mask;
+        const int c = __popcll(m);
+        if (y < c) {
+            for (int j = 0; j < y; j++) m &= m - 1;
+            return lo + __ffsll((long long)m) - 1;
+        }
+        y -= c;
+    }
+    return -1;
+}
+
+template <int W>
+__device__ __forceinline__ bool has_bit(const Str<W> &s, int b) {
+    return (s.w[b >> 6] >> (b & 63)) & 1ull;
+}
+
+// Above this bound no later entry of a list can meet the threshold: a key is
+// the magnitude rounded toward zero to FP32, so the magnitude is below
+// key (1 + 2^-23) for normal keys and below FLT_MIN otherwise.
+__device__ __forceinline__ double key_bound(float kf) {
+    return kf < FLT_MIN ? (double)FLT_MIN : (double)kf * (1.0 + 0x1p-22);
+}
+
+template <int W, bool FILL>
+__device__ __forceinline__ void sel_emit(const SelArgs &S, unsigned long long &cnt, int64_t base, unsigned *cursor,
+                                         const Str<W> &a, const Str<W> &b) {
+    if (!FILL) {
+        cnt++;
+        return;
+    }
+    const int64_t pos = base + atomicAdd(cursor, 1u);
+    uint64_t *o = S.out + pos * 2 * W;
+#pragma unroll
+    for (int k = 0; k < W; k++) {
+        o[k] = a.w[k];
+        o[W + k] = b.w[k];
+    }
+}
+
+// walk one sorted list from slot; `spin` 0: both moves in a (same spin alpha),
+// 1: both in b (same spin beta), 2: p -> r in a and q -> s in b
+template <int W, bool FILL>
+__device__ __forceinline__ void sel_walk(const SelArgs &S, const int64_t *off, const uint32_t *rs, const double *val,
+                                         const float *kf, int slot, int p, int q, int spin, double cmax,
+                                         const Str<W> &A, const Str<W> &B, unsigned long long &cnt, int64_t base,
+                                         unsigned *cursor) {
+    const int64_t e0 = __ldg(&off[slot]), e1 = __ldg(&off[slot + 1]);
+    for (int64_t e = e0; e < e1; e++) {
+        if (key_bound(__ldg(&kf[e])) * cmax < S.eps1) break;
+        const uint32_t x = __ldg(&rs[e]);
+        const int r = (int)(x & 0xFFFFu), s = (int)(x >> 16);
+        Str<W> a = A, b = B;
+        if (spin == 0) {
+            if (has_bit(A, r) || has_bit(A, s)) continue;
+            flip_bit(a, p); flip_bit(a, q); flip_bit(a, r); flip_bit(a, s);
+        } else if (spin == 1) {
+            if (has_bit(B, r) || has_bit(B, s)) continue;
+            flip_bit(b, p); flip_bit(b, q); flip_bit(b, r); flip_bit(b, s);
+        } else {
+            if (has_bit(A, r) || has_bit(B, s)) continue;
+            flip_bit(a, p); flip_bit(a, r); flip_bit(b, q); flip_bit(b, s);
+        }
+        if (!(__ldg(&val[e]) * cmax >= S.eps1)) continue;
+        sel_emit<W, FILL>(S, cnt, base, cursor, a, b);
+    }
+}
+
+// One warp per determinant; the lanes share its units of work: every single
+// move (alpha then beta) and every occupied pair (alpha-alpha, beta-beta,
+// alpha-beta), whose sorted list the lane walks.
+template <int W, bool FILL>
+__global__ void __launch_bounds__(SEL_THREADS) k_select(SelArgs S, DevInts I) {
+    __shared__ unsigned cursor[SEL_THREADS / 32];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int n = S.n, na = S.na, nb = S.nb;
+    const int64_t u_sa = (int64_t)na * (n - na), u_sb = (int64_t)nb * (n - nb);
+    const int64_t u_paa = (int64_t)na * (na - 1) / 2, u_pbb = (int64_t)nb * (nb - 1) / 2, u_pab = (int64_t)na * nb;
+    const int64_t units = u_sa + u_sb + u_paa + u_pbb + u_pab;
+    const int64_t warps = (int64_t)gridDim.x * (SEL_THREADS / 32);
+    for (int64_t i = ((int64_t)blockIdx.x * SEL_THREADS + threadIdx.x) >> 5; i < S.n_det; i += warps) {
+        double cmax = 0.0;
+        for (int l = 0; l < S.k; l++) cmax = fmax(cmax, fabs(__ldg(&S.c[(int64_t)l * S.n_det + i])));
+        const Str<W> A = load_str<W>(S.dets, 2 * i), B = load_str<W>(S.dets, 2 * i + 1);
+        unsigned long long cnt = 0;
+        const int64_t base = FILL ? __ldg(&S.off[i]) : 0;
+        if (FILL && lane == 0) cursor[wib] = 0u;
+        __syncwarp();
+        if (cmax > 0.0) {
+            for (int64_t u = lane; u < units; u += 32) {
+                int64_t v = u;
+                if (v < u_sa + u_sb) {                               // single move p -> r
+                    const bool alpha = v < u_sa;
+                    if (!alpha) v -= u_sa;
+                    const int ne = alpha ? na : nb;
+                    const Str<W> &si = alpha ? A : B;
+                    const int p = nth_set(si, (int)(v / (n - ne)));
+                    const int r = nth_unset(si, (int)(v % (n - ne)), n);
+                    Str<W> sj = si;
+                    flip_bit(sj, p);
+                    flip_bit(sj, r);
+                    const double hv = single_exc<W>(I, si, sj, alpha ? B : A);
+                    if (!(fabs(hv) * cmax >= S.eps1)) continue;
+                    if (alpha) sel_emit<W, FILL>(S, cnt, base, &cursor[wib], sj, B);
+                    else sel_emit<W, FILL>(S, cnt, base, &cursor[wib], A, sj);
+                    continue;
+                }
+                v -= u_sa + u_sb;
+                if (v < u_paa + u_pbb) {                             // same-spin pair (p < q)
+                    const bool alpha = v < u_paa;
+                    if (!alpha) v -= u_paa;
+                    // pair rank v -> (x < y): y is the largest with y (y - 1) / 2 <= v
+                    int y = (int)((1.0 + sqrt(1.0 + 8.0 * (double)v)) * 0.5);
+                    while ((int64_t)y * (y - 1) / 2 > v) y--;
+                    while ((int64_t)(y + 1) * y / 2 <= v) y++;
+                    const int x = (int)(v - (int64_t)y * (y - 1) / 2);
+                    const Str<W> &si = alpha ? A : B;
+                    const int p = nth_set(si, x), q = nth_set(si, y);
+                    sel_walk<W, FILL>(S, S.ss_off, S.ss_rs, S.ss_v, S.ss_kf, p * n + q, p, q, alpha ? 0 : 1, cmax, A,
+                                      B, cnt, base, &cursor[wib]);
+                    continue;
+                }
+                v -= u_paa + u_pbb;                                  // opposite-spin pair
+                const int p = nth_set(A, (int)(v / nb)), q = nth_set(B, (int)(v % nb));
+                sel_walk<W, FILL>(S, S.os_off, S.os_rs, S.os_v, S.os_kf, p * n + q, p, q, 2, cmax, A, B, cnt, base,
+                                  &cursor[wib]);
+            }
+        }
+        if (!FILL) {
+#pragma unroll
+            for (int o = 16; o >= 1; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+            if (lane == 0) S.cnt[i] = cnt;
+        }
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------- unique, minus V
+
+// lexicographic comparison with the last word most significant
+template <int KW>
+__device__ __forceinline__ int cmp_words(const uint64_t *a, const uint64_t *b) {
+#pragma unroll
+    for (int w = KW - 1; w >= 0; w--)
+        if (a[w] != b[w]) return a[w] < b[w] ? -1 : 1;
+    return 0;
+}
+
+// flag[e] = candidate e is the first of its run and not in the sorted V
+template <int KW>
+__global__ void k_sel_mark(const uint64_t *__restrict__ cand, int64_t total, const uint64_t *__restrict__ vs,
+                           int64_t nv, int64_t *__restrict__ flag) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t *x = cand + e * KW;
+        int keep = e == 0 || cmp_words<KW>(cand + (e - 1) * KW, x) != 0;
+        if (keep) {
+            int64_t lo = 0, hi = nv;
+            while (lo < hi) {
+                const int64_t mid = (lo + hi) >> 1;
+                if (cmp_words<KW>(vs + mid * KW, x) < 0) lo = mid + 1;
+                else hi = mid;
+            }
+            if (lo < nv && cmp_words<KW>(vs + lo * KW, x) == 0) keep = 0;
+        }
+        flag[e] = keep;
+    }
+}
+
+template <int KW>
+__global__ void k_sel_compact(const uint64_t *__restrict__ cand, int64_t total, const int64_t *__restrict__ pos,
+                              uint64_t *__restrict__ out) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        if (pos[e + 1] == pos[e]) continue;
+#pragma unroll
+        for (int w = 0; w < KW; w++) out[pos[e] * KW + w] = cand[e * KW + w];
+    }
+}
+
+template <int W>
+static void select_w(shci_ctx *c, int k, const double *cd, double eps1, DevBuf<uint64_t> &result, int64_t &n_new) {
+    cudaStream_t st = c->st;
+    constexpr int KW = 2 * W;
+    const int64_t n = c->n_det;
+    SelArgs S{};
+    S.n_det = n;
+    S.dets = c->dets.p;
+    S.k = k;
+    S.c = cd;
+    S.eps1 = eps1;
+    S.n = c->n_orb;
+    S.na = c->n_alpha;
+    S.nb = c->n_beta;
+    S.ss_off = c->hb_same.off.p;
+    S.ss_rs = c->hb_same.rs.p;
+    S.ss_v = c->hb_same.val.p;
+    S.ss_kf = c->hb_same.kf.p;
+    S.os_off = c->hb_opp.off.p;
+    S.os_rs = c->hb_opp.rs.p;
+    S.os_v = c->hb_opp.val.p;
+    S.os_kf = c->hb_opp.kf.p;
+    const DevInts I = dev_ints(c);
+    const int blocks = c->n_sm * (2048 / SEL_THREADS);
+    DevBuf<unsigned long long> cnt;
+    cnt.alloc((size_t)n + 1);
+    S.cnt = cnt.p;
+    k_select<W, false><<<blocks, SEL_THREADS, 0, st>>>(S, I);
+    KERNEL_CHECK();
+    DevBuf<int64_t> off, tmp;
+    off.alloc((size_t)n + 1);
+    tmp.alloc((size_t)scan_tmp_len(n + 1));
+    exclusive_scan<int64_t>(reinterpret_cast<const int64_t *>(cnt.p), off.p, n, tmp.p, st);
+    int64_t total = 0;
+    CUDA_TRY(cudaMemcpyAsync(&total, off.p + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    c->stats.select_candidates = total;
+    n_new = 0;
+    g_kernel_launches += 1;
+    if (total == 0) return;
+    if (total > 0xFFFFFFFFll) throw ShciError{SHCI_ERR_INVALID, "too many candidates: raise eps1"};
+    DevBuf<uint64_t> cand;
+    cand.alloc((size_t)total * KW);
+    S.off = off.p;
+    S.out = cand.p;
+    k_select<W, true><<<blocks, SEL_THREADS, 0, st>>>(S, I);
+    KERNEL_CHECK();
+    g_kernel_launches += 1;
+    DevBuf<uint32_t> dummy;
+    dummy.alloc((size_t)std::max(total, n));
+    radix_sort<KW>(cand.p, dummy.p, total, c->sw, st);
+    // V sorted the same way
+    DevBuf<uint64_t> vs;
+    vs.alloc((size_t)n * KW);
+    CUDA_TRY(cudaMemcpyAsync(vs.p, c->dets.p, sizeof(uint64_t) * n * KW, cudaMemcpyDeviceToDevice, st));
+    radix_sort<KW>(vs.p, dummy.p, n, c->sw, st);
+    DevBuf<int64_t> flag, pos, tmp2;
+    flag.alloc((size_t)total + 1);
+    pos.alloc((size_t)total + 1);
+    tmp2.alloc((size_t)scan_tmp_len(total + 1));
+    const int gb = (int)std::min<int64_t>(ceil_div(total, SEL_THREADS), (int64_t)c->n_sm * 16);
+    k_sel_mark<KW><<<gb, SEL_THREADS, 0, st>>>(cand.p, total, vs.p, n, flag.p);
+    KERNEL_CHECK();
+    exclusive_scan<int64_t>(flag.p, pos.p, total, tmp2.p, st);
+    CUDA_TRY(cudaMemcpyAsync(&n_new, pos.p + total, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    result.alloc((size_t)std::max<int64_t>(n_new, 1) * KW);
+    k_sel_compact<KW><<<gb, SEL_THREADS, 0, st>>>(cand.p, total, pos.p, result.p);
+    KERNEL_CHECK();
+    g_kernel_launches += 2;
+    CUDA_TRY(cudaStreamSynchronize(st));
+}
+
+void select_dets(shci_ctx *c, int k, const double *coef, double eps1, int64_t cap, uint64_t *out, int64_t *n_out,
+                 int mem) {
+    if (!c->built) throw ShciError{SHCI_ERR_STATE, "build the connectivity before selecting"};
+    if (k < 1 || k > SHCI_MAX_K) throw ShciError{SHCI_ERR_INVALID, "k must be in [1, 8]"};
+    if (!(eps1 > 0.0) || !std::isfinite(eps1)) throw ShciError{SHCI_ERR_INVALID, "eps1 must be positive and finite"};
+    if (!coef || !n_out) throw ShciError{SHCI_ERR_INVALID, "null pointer"};
+    if (cap < 0) throw ShciError{SHCI_ERR_INVALID, "cap must be >= 0"};
+    if (mem != SHCI_MEM_HOST && mem != SHCI_MEM_DEVICE) throw ShciError{SHCI_ERR_INVALID, "unknown mem_space"};
+    if (c->n_orb > 128) throw ShciError{SHCI_ERR_INVALID, "selection supports up to 128 orbitals"};
+    cudaStream_t st = c->st;
+    cudaEvent_t e0, e1;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    CUDA_TRY(cudaEventRecord(e0, st));
+    if (!c->hb_valid) {
+        build_hb_list(c, 1, c->hb_same);
+        build_hb_list(c, 0, c->hb_opp);
+        c->hb_valid = true;
+    }
+    const double *cd = coef;
+    DevBuf<double> cbuf;
+    if (mem == SHCI_MEM_HOST) {
+        cbuf.alloc((size_t)k * c->n_det);
+        CUDA_TRY(cudaMemcpyAsync(cbuf.p, coef, sizeof(double) * k * c->n_det, cudaMemcpyHostToDevice, st));
+        cd = cbuf.p;
+    }
+    DevBuf<uint64_t> result;
+    int64_t n_new = 0;
+    if (c->W == 1) select_w<1>(c, k, cd, eps1, result, n_new);
+    else select_w<2>(c, k, cd, eps1, result, n_new);
+    *n_out = n_new;
+    const int KW = 2 * c->W;
+    if (n_new > 0 && cap > 0) {
+        if (!out) throw ShciError{SHCI_ERR_INVALID, "null output pointer"};
+        const int64_t m = std::min(cap, n_new);
+        CUDA_TRY(cudaMemcpyAsync(out, result.p, sizeof(uint64_t) * m * KW,
+                                 mem == SHCI_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
+    }
+    CUDA_TRY(cudaEventRecord(e1, st));
+    CUDA_TRY(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->stats.select_ms = ms;
+}
+
+}  // namespace shci

@@ -1,0 +1,104 @@
+"""Heat-bath selection (Sec. II, Eq. 2) on the GPU against the oracle's brute
+force: the selected sets are compared as sets of determinants, bit-exact.
+The GPU tests |H_ai| |c_i| >= eps1 in FP64 with matrix elements summed in
+another order than the oracle's, so products within 1e-9 of eps1 may fall
+either way: the GPU set at eps1 must contain the oracle set at
+eps1 (1 + 1e-9) and lie inside the oracle set at eps1 (1 - 1e-9)."""
+import numpy as np
+import pytest
+import torch
+
+import shci_synth as S
+from tests import gpu_common as G
+
+pytestmark = pytest.mark.gpu
+
+@pytest.fixture(scope="module")
+def P():
+    return G.lib()
+
+
+def _rows(a):
+    a = np.asarray(a)
+    if a.dtype != np.uint64:
+        a = a.view(np.uint64)
+    return {tuple(int(x) for x in d) for d in a}
+
+
+def _check(P, O, B, dets, c, eps1, device=True):
+    cc = G.dev(c) if device else np.ascontiguousarray(c)
+    got = P.shci_select(B.ctx.handle, cc, eps1)
+    got = got.cpu().numpy() if device else got
+    g = _rows(got)
+    assert len(g) == got.shape[0]                              # no repeats
+    keys = [tuple(int(x) for x in d[::-1]) for d in got.view(np.uint64)]
+    assert keys == sorted(keys)                                # ascending, last word most significant
+    ref, best = O.select(dets, c, eps1 * (1 - 1e-9), with_best=True)
+    hi = _rows(ref)
+    lo = _rows(ref[best >= eps1 * (1 + 1e-9)])
+    assert lo <= g <= hi
+    assert not (g & _rows(dets))                               # nothing already in V
+    st = P.shci_get_stats(B.ctx.handle)
+    assert st["select_candidates"] >= got.shape[0] and st["select_ms"] > 0.0
+    return g
+
+
+def test_from_one_determinant_every_connection(P, oracle_mod):
+    h, eri, ec = S.integrals(10, 20, 1000)
+    hf = S.fci_dets(10, 4, 4)[:1]
+    O = oracle_mod.System(h, eri, ec)
+    B = G.Built(P, h, eri, ec, hf, 4, 4)
+    g = _check(P, O, B, hf, np.ones((1, 1)), 1e-12)
+    assert len(g) == 804
+    B.close()
+
+
+@pytest.mark.parametrize("eps1", [3e-2, 3e-3, 3e-4])
+def test_full_ci_subset(P, oracle_mod, eps1):
+    cfg, h, eri, ec, dets = G.system("fci_10o_4a4b", None)
+    rng = np.random.default_rng(7)
+    v = dets[np.sort(rng.choice(dets.shape[0], 400, replace=False))]
+    c = rng.standard_normal((2, v.shape[0])) / np.sqrt(v.shape[0])
+    O = oracle_mod.System(h, eri, ec)
+    B = G.Built(P, h, eri, ec, v, 4, 4)
+    g = _check(P, O, B, v, c, eps1)
+    assert len(g) > 0
+    B.close()
+
+
+def test_selected_space_ground_state_coefficients(P, oracle_mod):
+    cfg, h, eri, ec, dets = G.system("sel_24o_6a6b_1m", 600)
+    O = oracle_mod.System(h, eri, ec)
+    B = G.Built(P, h, eri, ec, dets, 6, 6)
+    e, vecs, it = B.davidson(1, tol=1e-10)
+    for eps1 in (1e-3, 1e-4):
+        g = _check(P, O, B, dets, vecs, eps1)
+        assert len(g) > 0
+    # host coefficients give the same set
+    assert _check(P, O, B, dets, vecs, 1e-3, device=False) == _check(P, O, B, dets, vecs, 1e-3)
+    B.close()
+
+
+def test_two_word_strings(P, oracle_mod):
+    cfg, h, eri, ec, dets = G.system("sel_76o_14a14b_50m", 12)
+    rng = np.random.default_rng(5)
+    c = rng.standard_normal((1, dets.shape[0]))
+    O = oracle_mod.System(h, eri, ec)
+    B = G.Built(P, h, eri, ec, dets, 14, 14)
+    g = _check(P, O, B, dets, c, 2e-2)
+    assert len(g) > 0
+    B.close()
+
+
+def test_full_space_selects_nothing_and_bad_arguments(P, oracle_mod):
+    h, eri, ec = S.integrals(8, 10, 4242)
+    fci = S.fci_dets(8, 3, 2)
+    B = G.Built(P, h, eri, ec, fci, 3, 2)
+    c = G.dev(np.ones((1, fci.shape[0])))
+    assert P.shci_select(B.ctx.handle, c, 1e-8).shape[0] == 0
+    for bad in (0.0, -1.0, float("inf"), float("nan")):
+        with pytest.raises(P.ShciError):
+            P.shci_select(B.ctx.handle, c, bad)
+    with pytest.raises(P.ShciError):
+        P.shci_select(B.ctx.handle, G.dev(np.ones((9, fci.shape[0]))), 1e-3)   # k out of range
+    B.close()
