@@ -95,6 +95,9 @@ def _load():
         lib.oracle_select.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, _f64p, _f64p,
                                       ctypes.c_int64, _u64p, ctypes.c_int, _f64p, ctypes.c_double,
                                       ctypes.c_int64, _u64p, _f64p]
+        lib.oracle_pt2.restype = ctypes.c_int
+        lib.oracle_pt2.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, _f64p, _f64p, ctypes.c_int64,
+                                   _u64p, _f64p, ctypes.c_double, ctypes.c_double, _f64p, _i64p]
         lib.oracle_num_threads.restype = ctypes.c_int
         lib.oracle_num_threads.argtypes = []
         _lib = lib
@@ -192,6 +195,20 @@ class System:
             if m <= cap:
                 return (out[:m].copy(), best[:m].copy()) if with_best else out[:m].copy()
             cap = int(m)
+
+    def pt2(self, dets, c, e_var, eps2):
+        """(dE2, number of perturbative determinants): the screened second-order
+        Epstein-Nesbet energy of Sec. II.B (Eq. 7) by brute force."""
+        dets = _u64(dets)
+        c = _f64(np.ravel(c))
+        e2 = np.zeros(1)
+        npert = np.zeros(1, np.int64)
+        rc = _load().oracle_pt2(self.n, n_words(dets), self.e_core, _p(self.h, _f64p), _p(self.eri, _f64p),
+                                dets.shape[0], _p(dets, _u64p), _p(c, _f64p), float(e_var), float(eps2),
+                                _p(e2, _f64p), _p(npert, _i64p))
+        if rc != 0:
+            raise RuntimeError("oracle_pt2 failed (%d)" % rc)
+        return float(e2[0]), int(npert[0])
 
     # ---------------------------------------------------------- sigma
     def sigma_rows(self, dets, c, rows) -> np.ndarray:

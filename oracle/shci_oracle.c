@@ -655,3 +655,100 @@ int64_t oracle_select(int n, int W, double e_core, const double *h, const double
     free(buf);
     return u;
 }
+
+/* ------------------------------------------------------------ Epstein-Nesbet PT2 */
+
+/* records: 2W determinant words, the term H_ai c_i (bits), generation index */
+static int cmp_pt_records(const void *a, const void *b)
+{
+    const uint64_t *x = (const uint64_t *)a, *y = (const uint64_t *)b;
+    for (int w = g_sel_words - 1; w >= 0; w--) {
+        if (x[w] != y[w]) return x[w] < y[w] ? -1 : 1;
+    }
+    return (x[g_sel_words + 1] > y[g_sel_words + 1]) - (x[g_sel_words + 1] < y[g_sel_words + 1]);
+}
+
+/*
+ * The screened second-order Epstein-Nesbet energy of Sec. II.B (Eq. 7):
+ *   dE2 = sum_{a not in V} (sum_i^{(eps2)} H_ai c_i)^2 / (E_V - H_aa),
+ * where the inner sum keeps only the terms with |H_ai c_i| >= eps2 (FP64).
+ * Brute force: every single and double excitation a of every D_i, the term
+ * H_ai c_i by Slater-Condon (operator form), terms gathered per a (sorted by
+ * determinant, then by generation order), H_aa from the diagonal rule.
+ * *n_pert receives the number of determinants a with at least one term.
+ * Returns 0, -1 on OOM, -2 on duplicate determinants.
+ */
+int oracle_pt2(int n, int W, double e_core, const double *h, const double *eri, int64_t n_det,
+               const uint64_t *dets, const double *c, double e_var, double eps2, double *e2, int64_t *n_pert)
+{
+    oints I = {n, W, e_core, h, eri};
+    dtable t;
+    int rc = dtable_init(&t, n_det, W, dets);
+    if (rc) { free(t.slot); return rc; }
+    const int W2 = 2 * W, nso = 2 * n, R = 2 * W + 2;
+    int64_t m = 0, mcap = 1024;
+    uint64_t *buf = (uint64_t *)malloc(sizeof(uint64_t) * R * mcap);
+    if (!buf) { free(t.slot); return -1; }
+    uint64_t x[8];
+    for (int64_t i = 0; i < n_det; i++) {
+        const uint64_t *d = dets + i * W2;
+        if (c[i] == 0.0) continue;
+        for (int q = 0; q < nso; q++) {
+            if (!occ(&I, d, q)) continue;
+            for (int pass = 0; pass < 2; pass++) {
+                for (int s = (pass ? q + 1 : nso); s < (pass ? nso : nso + 1); s++) {
+                    if (pass && !occ(&I, d, s)) continue;
+                    for (int p = 0; p < nso; p++) {
+                        if (occ(&I, d, p)) continue;
+                        for (int r = (pass ? p + 1 : nso); r < (pass ? nso : nso + 1); r++) {
+                            if (pass && occ(&I, d, r)) continue;
+                            if (!pass && so_spin(&I, p) != so_spin(&I, q)) continue;
+                            if (pass && so_spin(&I, q) + so_spin(&I, s) != so_spin(&I, p) + so_spin(&I, r))
+                                continue;
+                            memcpy(x, d, 8 * W2);
+                            put(&I, x, q, 0);
+                            put(&I, x, p, 1);
+                            if (pass) { put(&I, x, s, 0); put(&I, x, r, 1); }
+                            if (dtable_find(&t, x) >= 0) continue;
+                            const double term = matrix_element(&I, x, d) * c[i];
+                            if (!(fabs(term) >= eps2)) continue;
+                            if (m == mcap) {
+                                mcap *= 2;
+                                uint64_t *nb = (uint64_t *)realloc(buf, sizeof(uint64_t) * R * mcap);
+                                if (!nb) { free(buf); free(t.slot); return -1; }
+                                buf = nb;
+                            }
+                            memcpy(buf + m * R, x, 8 * W2);
+                            memcpy(buf + m * R + W2, &term, 8);
+                            buf[m * R + W2 + 1] = (uint64_t)m;
+                            m++;
+                        }
+                    }
+                }
+            }
+        }
+    }
+    free(t.slot);
+    g_sel_words = W2;
+    qsort(buf, (size_t)m, sizeof(uint64_t) * R, cmp_pt_records);
+    double sum = 0.0;
+    int64_t runs = 0;
+    for (int64_t e = 0; e < m;) {
+        int64_t f = e;
+        double num = 0.0;
+        while (f < m && memcmp(buf + f * R, buf + e * R, 8 * W2) == 0) {
+            double v;
+            memcpy(&v, buf + f * R + W2, 8);
+            num += v;
+            f++;
+        }
+        const double haa = diag_element(&I, buf + e * R);
+        sum += num * num / (e_var - haa);
+        runs++;
+        e = f;
+    }
+    free(buf);
+    *e2 = sum;
+    *n_pert = runs;
+    return 0;
+}

@@ -365,3 +365,40 @@ def test_selection_matches_dense_hamiltonian(oracle_mod):
             assert prev <= got                       # smaller eps1: superset
         prev = got
     assert O.select(fci, np.ones((1, fci.shape[0])), 1e-6).shape[0] == 0
+
+
+# ---------------------------------------------------------------- screened Epstein-Nesbet PT2 (Sec. II.B, Eq. 7)
+
+def test_pt2_matches_dense_hamiltonian(oracle_mod):
+    """dE2(eps2) equals the screened sum read off the dense full-CI matrix:
+    num_a = sum_i H_ai c_i over the terms with |H_ai c_i| >= eps2, a outside
+    V, dE2 = sum_a num_a^2 / (E_V - H_aa); from one determinant with eps2 -> 0
+    it is the textbook second-order Epstein-Nesbet energy; the full space has
+    none."""
+    n, na, nb = 8, 3, 2
+    h, eri, ec = S.integrals(n, 10, 4242)
+    fci = S.fci_dets(n, na, nb)
+    O = oracle_mod.System(h, eri, ec)
+    H = O.dense_h(fci)
+    rng = np.random.default_rng(11)
+    vidx = np.sort(rng.choice(fci.shape[0], 30, replace=False))
+    c = rng.standard_normal(vidx.size)
+    c /= np.linalg.norm(c)
+    e_var = float(c @ H[np.ix_(vidx, vidx)] @ c)
+    out = np.setdiff1d(np.arange(fci.shape[0]), vidx)
+    for eps2 in (1e-2, 1e-3, 1e-12):
+        T = H[np.ix_(out, vidx)] * c[None, :]
+        T[np.abs(T) < eps2] = 0.0
+        num = T.sum(axis=1)
+        keep = np.any(T != 0.0, axis=1)
+        want = float(np.sum(num[keep] ** 2 / (e_var - np.diag(H)[out][keep])))
+        got, npert = O.pt2(fci[vidx], c, e_var, eps2)
+        assert abs(got - want) <= 1e-12 * max(1.0, abs(want))
+        assert npert == int(keep.sum())
+    hf = 0
+    e0 = H[hf, hf]
+    others = np.arange(1, fci.shape[0])
+    want = float(np.sum(H[others, hf] ** 2 / (e0 - np.diag(H)[others])))
+    got, _ = O.pt2(fci[:1], np.ones(1), e0, 1e-300)
+    assert abs(got - want) <= 1e-12 * abs(want)
+    assert O.pt2(fci, np.ones(fci.shape[0]) / np.sqrt(fci.shape[0]), 0.0, 1e-8) == (0.0, 0)
