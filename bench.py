@@ -618,8 +618,39 @@ def run_select(args):
                       "oracle": {"sample_dets": int(samp.size), "seconds": t_or,
                                  "dets_screened_per_s": samp.size / t_or, "cores": 1,
                                  "kind": "brute force over every single and double excitation"}})
+    # screened second-order Epstein-Nesbet energy of the ground state (Sec. II.B, Eq. 7)
+    e0, _, _ = P.shci_davidson(H, 1, TOL, MAX_ITER, vecs=vecs[:1])
+    pt = []
+    for eps2 in (args.eps2 or [1e-5]):
+        t = time.perf_counter()
+        e2, npert = P.shci_pt2(H, vecs[0].contiguous(), float(e0[0]), eps2)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t
+        st = P.shci_get_stats(H)
+        pt.append({"eps2": eps2, "e_var": float(e0[0]), "dE2": e2, "n_pert": npert, "terms": st["pt2_terms"],
+                   "batches": st["pt2_batches"], "seconds": dt, "device_ms": st["pt2_ms"]})
+    # the same screened energy on a 600-determinant space of the same shape: GPU and oracle side by side
+    h6, eri6, ec6, d6 = S.make_system(cfg, 600)
+    c6 = P.Context(0, torch.cuda.current_stream())
+    P.shci_load_integrals(c6.handle, cfg.n_orb, ec6, _dev(torch, h6), _dev(torch, eri6))
+    P.shci_build_connectivity(c6.handle, cfg.n_alpha, cfg.n_beta, _dev(torch, d6), P.SHCI_STORED)
+    v6 = torch.empty((1, d6.shape[0]), dtype=torch.float64, device="cuda")
+    e6, _, _ = P.shci_davidson(c6.handle, 1, TOL, MAX_ITER, vecs=v6)
+    P.shci_pt2(c6.handle, v6[0].contiguous(), float(e6[0]), 1e-5)     # lists built
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    g6, _ = P.shci_pt2(c6.handle, v6[0].contiguous(), float(e6[0]), 1e-5)
+    torch.cuda.synchronize()
+    t_g6 = time.perf_counter() - t
+    t = time.perf_counter()
+    o6, _ = O.System(h6, eri6, ec6).pt2(d6, v6[0].cpu().numpy(), float(e6[0]), 1e-5)
+    t_o6 = time.perf_counter() - t
+    c6.close()
     print(json.dumps({"workload": workload_desc(cfg) + ", heat-bath selection with the converged 2-root "
-                                                       "coefficients", "lines": lines}))
+                                                       "coefficients; screened PT2 of the ground state",
+                      "lines": lines, "pt2": pt,
+                      "pt2_600_dets": {"gpu_s": t_g6, "oracle_s": t_o6, "oracle_cores": 1, "dE2_gpu": g6,
+                                       "dE2_oracle": o6, "eps2": 1e-5}}))
     ctx.close()
 
 
@@ -715,6 +746,7 @@ def main():
     ap.add_argument("--batch-budget-gb", type=float, default=180.0)
     ap.add_argument("--eps1", type=float, action="append", help="selection thresholds (select workload)")
     ap.add_argument("--select-sample", type=int, default=200, help="determinants of V the oracle screens")
+    ap.add_argument("--eps2", type=float, action="append", help="PT2 screening thresholds (select workload)")
     args = ap.parse_args()
     if args.workload != "main":
         {"fci": run_fci, "large": run_large, "adjoint": run_adjoint, "batch": run_batch,

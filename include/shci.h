@@ -181,6 +181,22 @@ int shci_davidson_history(shci_ctx *ctx, int cap, double *theta, double *rnorm, 
 int shci_select(shci_ctx *ctx, int k_roots, const double *c, double eps1, int64_t cap, uint64_t *new_dets,
                 int64_t *n_new, int mem_space);
 
+/* Screened second-order Epstein-Nesbet energy (Sec. II.B, Eq. 7):
+ *   dE2 = sum_{a not in V} (sum_i^{(eps2)} H_ai c_i)^2 / (E_V - H_aa),
+ * the inner sum keeping the terms with |H_ai c_i| >= eps2 (FP64), found with
+ * the same sorted double-excitation lists as shci_select and exact singles.
+ * c: [n_det] coefficients of V (mem_space), e_var: the variational energy
+ * E_V (with e_core).  The determinants a are processed in n_batches hash
+ * batches (each batch repeats the screen and keeps its own a), so that one
+ * batch's terms fit device memory; n_batches = 0 picks the number from the
+ * free memory.  *e2 (host) receives dE2, *n_pert (host, may be NULL) the
+ * number of determinants a with at least one kept term.  Batches are summed
+ * in order and each batch in a fixed order: the result does not depend on
+ * timing.  Needs a completed shci_build_connectivity (either mode); eps2
+ * positive and finite; n_orb <= 128. */
+int shci_pt2(shci_ctx *ctx, const double *c, double e_var, double eps2, int n_batches, double *e2, int64_t *n_pert,
+             int mem_space);
+
 /* Adjoint of a variational eigenvalue (no counterpart in the paper, which
  * has no derivatives): for a normalised real eigenvector c of H on V,
  * E = c^T H c and, by Hellmann-Feynman, dE/dX = c^T (dH/dX) c.  Writes
@@ -276,6 +292,9 @@ typedef struct {
     double davidson_phase_ms[8];
     double select_ms;           /* last shci_select, device time (lists included when built) */
     int64_t select_candidates;  /* last shci_select: candidates before removing repeats and V */
+    double pt2_ms;              /* last shci_pt2, device time (lists included when built) */
+    int pt2_batches;            /* last shci_pt2: hash batches used */
+    int64_t pt2_terms;          /* last shci_pt2: terms H_ai c_i kept by the eps2 screen */
 } shci_stats_t;
 
 /* Fill *out.  Kernel times are recorded only while timing is enabled. */

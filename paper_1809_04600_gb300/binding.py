@@ -37,7 +37,7 @@ EXPORTED = [
     "shci_create", "shci_destroy", "shci_last_error", "shci_load_integrals", "shci_build_connectivity",
     "shci_get_diag", "shci_get_pairs", "shci_get_row", "shci_sigma", "shci_sigma_noalloc", "shci_energy_backward",
     "shci_batch_create", "shci_batch_davidson", "shci_batch_get_stats", "shci_batch_destroy", "shci_davidson",
-    "shci_davidson_history", "shci_select", "shci_get_stats", "shci_set_timing",
+    "shci_davidson_history", "shci_select", "shci_pt2", "shci_get_stats", "shci_set_timing",
 ]
 
 
@@ -55,6 +55,7 @@ class shci_stats_t(ctypes.Structure):
         ("sigma_vectors", ctypes.c_int64), ("kernel_launches", ctypes.c_int64), ("davidson_iters", ctypes.c_int),
         ("mode", ctypes.c_int), ("n_words", ctypes.c_int), ("davidson_phase_ms", ctypes.c_double * 8),
         ("select_ms", ctypes.c_double), ("select_candidates", ctypes.c_int64),
+        ("pt2_ms", ctypes.c_double), ("pt2_batches", ctypes.c_int), ("pt2_terms", ctypes.c_int64),
     ]
 
 
@@ -108,6 +109,7 @@ def load_library(path: str = LIB_PATH):
         "shci_davidson": (i32, [vp, i32, f64, i32, vp, vp, vp, i32, ctypes.POINTER(i32)]),
         "shci_davidson_history": (i32, [vp, i32, vp, vp, vp, ctypes.POINTER(i32)]),
         "shci_select": (i32, [vp, i32, vp, f64, i64, vp, ctypes.POINTER(i64), i32]),
+        "shci_pt2": (i32, [vp, vp, f64, f64, i32, ctypes.POINTER(f64), ctypes.POINTER(i64), i32]),
         "shci_get_stats": (i32, [vp, ctypes.POINTER(shci_stats_t)]),
         "shci_set_timing": (i32, [vp, i32]),
     }
@@ -292,6 +294,17 @@ def shci_select(ctx, c, eps1, cap=None):
         if n.value <= cap:
             return out[:n.value]
         cap = int(n.value)
+
+
+def shci_pt2(ctx, c, e_var, eps2, n_batches=0):
+    """(dE2, n_pert): the eps2-screened second-order Epstein-Nesbet energy of
+    the root c [n_det] (host or device) with variational energy e_var."""
+    pc, mc, kc = _ptr(c, np.float64)
+    e2 = ctypes.c_double(0.0)
+    npert = ctypes.c_int64(0)
+    _check(ctx, load_library().shci_pt2(ctx, pc, float(e_var), float(eps2), int(n_batches), ctypes.byref(e2),
+                                        ctypes.byref(npert), mc))
+    return e2.value, npert.value
 
 
 def shci_energy_backward(ctx, c, grad_out_scale, dE_dh, dE_deri_packed):

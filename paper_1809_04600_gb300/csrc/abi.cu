@@ -223,6 +223,14 @@ int shci_select(shci_ctx *c, int k, const double *coef, double eps1, int64_t cap
     });
 }
 
+int shci_pt2(shci_ctx *c, const double *coef, double e_var, double eps2, int n_batches, double *e2,
+             int64_t *n_pert, int mem) {
+    return guarded(c, [&] {
+        shci::pt2(c, coef, e_var, eps2, n_batches, e2, n_pert, mem);
+        return SHCI_OK;
+    });
+}
+
 int shci_get_stats(shci_ctx *c, shci_stats_t *out) {
     return guarded(c, [&] {
         if (!out) throw ShciError{SHCI_ERR_INVALID, "null pointer"};

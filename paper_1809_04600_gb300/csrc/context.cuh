@@ -121,6 +121,8 @@ void sigma(shci_ctx *c, int k, const double *x, double *y, bool inter);
 // select.cu: heat-bath selection of new determinants (Sec. II)
 void select_dets(shci_ctx *c, int k, const double *coef, double eps1, int64_t cap, uint64_t *out, int64_t *n_out,
                  int mem);
+void pt2(shci_ctx *c, const double *coef, double e_var, double eps2, int nbatch, double *e2, int64_t *n_pert,
+         int mem);
 
 // davidson.cu
 int davidson(shci_ctx *c, int k, double tol, int max_iter, const double *guess, double *energies,

@@ -131,7 +131,24 @@ struct SelArgs {
     unsigned long long *cnt;                // count pass: candidates per determinant
     const int64_t *off;                     // fill pass: first slot of each determinant
     uint64_t *out;                          // fill pass: [total][2W]
+    // second-order energy: the terms H_ai c_i of determinants a in hash batch `batch` of `nbatch`
+    int nbatch, batch;
+    double *terms;                          // fill pass: [total]
 };
+
+// batch of a determinant (a SplitMix64-style mix of its words)
+template <int W>
+__device__ __forceinline__ int det_batch(const Str<W> &a, const Str<W> &b, int nbatch) {
+    uint64_t z = 0x9E3779B97F4A7C15ull;
+#pragma unroll
+    for (int k = 0; k < 2 * W; k++) {
+        z ^= k < W ? a.w[k] : b.w[k - W];
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+    }
+    return (int)(z % (uint64_t)nbatch);
+}
 
 // orbital of the x-th (0-based) set bit of s
 template <int W>
@@ -181,9 +198,13 @@ __device__ __forceinline__ double key_bound(float kf) {
     return kf < FLT_MIN ? (double)FLT_MIN : (double)kf * (1.0 + 0x1p-22);
 }
 
-template <int W, bool FILL>
-__device__ __forceinline__ void sel_emit(const SelArgs &S, unsigned long long &cnt, int64_t base, unsigned *cursor,
+// Record a candidate (a, b).  Second-order mode (PT): only determinants of
+// the current hash batch, with the term H_ai c_i (signed, exact Slater-Condon).
+template <int W, bool FILL, bool PT>
+__device__ __forceinline__ void sel_emit(const SelArgs &S, const DevInts &I, unsigned long long &cnt, int64_t base,
+                                         unsigned *cursor, const Str<W> &A, const Str<W> &B, double ci,
                                          const Str<W> &a, const Str<W> &b) {
+    if (PT && S.nbatch > 1 && det_batch<W>(a, b, S.nbatch) != S.batch) return;
     if (!FILL) {
         cnt++;
         return;
@@ -195,15 +216,16 @@ __device__ __forceinline__ void sel_emit(const SelArgs &S, unsigned long long &c
         o[k] = a.w[k];
         o[W + k] = b.w[k];
     }
+    if (PT) S.terms[pos] = hij_offdiag<W>(I, A, B, a, b) * ci;
 }
 
 // walk one sorted list from slot; `spin` 0: both moves in a (same spin alpha),
 // 1: both in b (same spin beta), 2: p -> r in a and q -> s in b
-template <int W, bool FILL>
-__device__ __forceinline__ void sel_walk(const SelArgs &S, const int64_t *off, const uint32_t *rs, const double *val,
-                                         const float *kf, int slot, int p, int q, int spin, double cmax,
-                                         const Str<W> &A, const Str<W> &B, unsigned long long &cnt, int64_t base,
-                                         unsigned *cursor) {
+template <int W, bool FILL, bool PT>
+__device__ __forceinline__ void sel_walk(const SelArgs &S, const DevInts &I, const int64_t *off, const uint32_t *rs,
+                                         const double *val, const float *kf, int slot, int p, int q, int spin,
+                                         double cmax, double ci, const Str<W> &A, const Str<W> &B,
+                                         unsigned long long &cnt, int64_t base, unsigned *cursor) {
     const int64_t e0 = __ldg(&off[slot]), e1 = __ldg(&off[slot + 1]);
     for (int64_t e = e0; e < e1; e++) {
         if (key_bound(__ldg(&kf[e])) * cmax < S.eps1) break;
@@ -221,14 +243,14 @@ __device__ __forceinline__ void sel_walk(const SelArgs &S, const int64_t *off, c
             flip_bit(a, p); flip_bit(a, r); flip_bit(b, q); flip_bit(b, s);
         }
         if (!(__ldg(&val[e]) * cmax >= S.eps1)) continue;
-        sel_emit<W, FILL>(S, cnt, base, cursor, a, b);
+        sel_emit<W, FILL, PT>(S, I, cnt, base, cursor, A, B, ci, a, b);
     }
 }
 
 // One warp per determinant; the lanes share its units of work: every single
 // move (alpha then beta) and every occupied pair (alpha-alpha, beta-beta,
 // alpha-beta), whose sorted list the lane walks.
-template <int W, bool FILL>
+template <int W, bool FILL, bool PT>
 __global__ void __launch_bounds__(SEL_THREADS) k_select(SelArgs S, DevInts I) {
     __shared__ unsigned cursor[SEL_THREADS / 32];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -238,8 +260,13 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select(SelArgs S, DevInts I) {
     const int64_t units = u_sa + u_sb + u_paa + u_pbb + u_pab;
     const int64_t warps = (int64_t)gridDim.x * (SEL_THREADS / 32);
     for (int64_t i = ((int64_t)blockIdx.x * SEL_THREADS + threadIdx.x) >> 5; i < S.n_det; i += warps) {
-        double cmax = 0.0;
-        for (int l = 0; l < S.k; l++) cmax = fmax(cmax, fabs(__ldg(&S.c[(int64_t)l * S.n_det + i])));
+        double cmax = 0.0, ci = 0.0;
+        if (PT) {
+            ci = __ldg(&S.c[i]);
+            cmax = fabs(ci);
+        } else {
+            for (int l = 0; l < S.k; l++) cmax = fmax(cmax, fabs(__ldg(&S.c[(int64_t)l * S.n_det + i])));
+        }
         const Str<W> A = load_str<W>(S.dets, 2 * i), B = load_str<W>(S.dets, 2 * i + 1);
         unsigned long long cnt = 0;
         const int64_t base = FILL ? __ldg(&S.off[i]) : 0;
@@ -260,8 +287,8 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select(SelArgs S, DevInts I) {
                     flip_bit(sj, r);
                     const double hv = single_exc<W>(I, si, sj, alpha ? B : A);
                     if (!(fabs(hv) * cmax >= S.eps1)) continue;
-                    if (alpha) sel_emit<W, FILL>(S, cnt, base, &cursor[wib], sj, B);
-                    else sel_emit<W, FILL>(S, cnt, base, &cursor[wib], A, sj);
+                    if (alpha) sel_emit<W, FILL, PT>(S, I, cnt, base, &cursor[wib], A, B, ci, sj, B);
+                    else sel_emit<W, FILL, PT>(S, I, cnt, base, &cursor[wib], A, B, ci, A, sj);
                     continue;
                 }
                 v -= u_sa + u_sb;
@@ -275,14 +302,14 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select(SelArgs S, DevInts I) {
                     const int x = (int)(v - (int64_t)y * (y - 1) / 2);
                     const Str<W> &si = alpha ? A : B;
                     const int p = nth_set(si, x), q = nth_set(si, y);
-                    sel_walk<W, FILL>(S, S.ss_off, S.ss_rs, S.ss_v, S.ss_kf, p * n + q, p, q, alpha ? 0 : 1, cmax, A,
-                                      B, cnt, base, &cursor[wib]);
+                    sel_walk<W, FILL, PT>(S, I, S.ss_off, S.ss_rs, S.ss_v, S.ss_kf, p * n + q, p, q, alpha ? 0 : 1,
+                                          cmax, ci, A, B, cnt, base, &cursor[wib]);
                     continue;
                 }
                 v -= u_paa + u_pbb;                                  // opposite-spin pair
                 const int p = nth_set(A, (int)(v / nb)), q = nth_set(B, (int)(v % nb));
-                sel_walk<W, FILL>(S, S.os_off, S.os_rs, S.os_v, S.os_kf, p * n + q, p, q, 2, cmax, A, B, cnt, base,
-                                  &cursor[wib]);
+                sel_walk<W, FILL, PT>(S, I, S.os_off, S.os_rs, S.os_v, S.os_kf, p * n + q, p, q, 2, cmax, ci, A, B,
+                                      cnt, base, &cursor[wib]);
             }
         }
         if (!FILL) {
@@ -362,7 +389,7 @@ static void select_w(shci_ctx *c, int k, const double *cd, double eps1, DevBuf<u
     DevBuf<unsigned long long> cnt;
     cnt.alloc((size_t)n + 1);
     S.cnt = cnt.p;
-    k_select<W, false><<<blocks, SEL_THREADS, 0, st>>>(S, I);
+    k_select<W, false, false><<<blocks, SEL_THREADS, 0, st>>>(S, I);
     KERNEL_CHECK();
     DevBuf<int64_t> off, tmp;
     off.alloc((size_t)n + 1);
@@ -380,7 +407,7 @@ static void select_w(shci_ctx *c, int k, const double *cd, double eps1, DevBuf<u
     cand.alloc((size_t)total * KW);
     S.off = off.p;
     S.out = cand.p;
-    k_select<W, true><<<blocks, SEL_THREADS, 0, st>>>(S, I);
+    k_select<W, true, false><<<blocks, SEL_THREADS, 0, st>>>(S, I);
     KERNEL_CHECK();
     g_kernel_launches += 1;
     DevBuf<uint32_t> dummy;
@@ -406,6 +433,225 @@ static void select_w(shci_ctx *c, int k, const double *cd, double eps1, DevBuf<u
     KERNEL_CHECK();
     g_kernel_launches += 2;
     CUDA_TRY(cudaStreamSynchronize(st));
+}
+
+// ---------------------------------------------------------------- second-order energy
+
+__global__ void k_iota(uint32_t *__restrict__ v, int64_t n) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        v[e] = (uint32_t)e;
+}
+
+// Over the sorted candidates of one batch: for each first entry of a run of
+// equal determinants a outside V, num = sum of the run's terms (in generation
+// order, i.e. by determinant i of V), and num^2 / (E_V - H_aa); per-block
+// sums of the contributions and of the determinants.
+template <int W>
+__global__ void __launch_bounds__(SEL_THREADS) k_pt_reduce(const uint64_t *__restrict__ cand,
+                                                          const uint32_t *__restrict__ idx,
+                                                          const double *__restrict__ terms, int64_t total,
+                                                          const uint64_t *__restrict__ vs, int64_t nv, DevInts I,
+                                                          double e_var, double *__restrict__ part,
+                                                          unsigned long long *__restrict__ npart) {
+    constexpr int KW = 2 * W;
+    double acc = 0.0;
+    unsigned long long cnt = 0;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t *x = cand + e * KW;
+        if (e > 0 && cmp_words<KW>(cand + (e - 1) * KW, x) == 0) continue;
+        int64_t lo = 0, hi = nv;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (cmp_words<KW>(vs + mid * KW, x) < 0) lo = mid + 1;
+            else hi = mid;
+        }
+        if (lo < nv && cmp_words<KW>(vs + lo * KW, x) == 0) continue;
+        double num = 0.0;
+        for (int64_t f = e; f < total && cmp_words<KW>(cand + f * KW, x) == 0; f++) num += terms[idx[f]];
+        Str<W> a, b;
+#pragma unroll
+        for (int k = 0; k < W; k++) {
+            a.w[k] = x[k];
+            b.w[k] = x[W + k];
+        }
+        acc += num * num / (e_var - hii<W>(I, a, b));
+        cnt++;
+    }
+    __shared__ double red[SEL_THREADS / 32];
+    __shared__ unsigned long long redc[SEL_THREADS / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    }
+    if (lane == 0) {
+        red[w] = acc;
+        redc[w] = cnt;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        unsigned long long sc = 0;
+        for (int x = 0; x < SEL_THREADS / 32; x++) {
+            s += red[x];
+            sc += redc[x];
+        }
+        part[blockIdx.x] = s;
+        npart[blockIdx.x] = sc;
+    }
+}
+
+template <int W>
+static double pt2_w(shci_ctx *c, const double *cd, double e_var, double eps2, int nbatch, int64_t &n_pert,
+                    int &nbatch_used, int64_t &candidates) {
+    cudaStream_t st = c->st;
+    constexpr int KW = 2 * W;
+    const int64_t n = c->n_det;
+    SelArgs S{};
+    S.n_det = n;
+    S.dets = c->dets.p;
+    S.k = 1;
+    S.c = cd;
+    S.eps1 = eps2;
+    S.n = c->n_orb;
+    S.na = c->n_alpha;
+    S.nb = c->n_beta;
+    S.ss_off = c->hb_same.off.p;
+    S.ss_rs = c->hb_same.rs.p;
+    S.ss_v = c->hb_same.val.p;
+    S.ss_kf = c->hb_same.kf.p;
+    S.os_off = c->hb_opp.off.p;
+    S.os_rs = c->hb_opp.rs.p;
+    S.os_v = c->hb_opp.val.p;
+    S.os_kf = c->hb_opp.kf.p;
+    const DevInts I = dev_ints(c);
+    const int blocks = c->n_sm * (2048 / SEL_THREADS);
+    DevBuf<unsigned long long> cnt;
+    cnt.alloc((size_t)n + 1);
+    S.cnt = cnt.p;
+    DevBuf<int64_t> off, tmp;
+    off.alloc((size_t)n + 1);
+    tmp.alloc((size_t)scan_tmp_len(n + 1));
+    auto count_pass = [&]() -> int64_t {
+        k_select<W, false, true><<<blocks, SEL_THREADS, 0, st>>>(S, I);
+        KERNEL_CHECK();
+        g_kernel_launches += 1;
+        exclusive_scan<int64_t>(reinterpret_cast<const int64_t *>(cnt.p), off.p, n, tmp.p, st);
+        int64_t total = 0;
+        CUDA_TRY(cudaMemcpyAsync(&total, off.p + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+        return total;
+    };
+    // batches: enough that one batch's candidates and their sort fit a quarter of free memory
+    constexpr double BYTES_PER_CAND = 2.0 * 8 * KW + 8 + 2 * 4;
+    if (nbatch <= 0) {
+        S.nbatch = 1;
+        S.batch = 0;
+        const int64_t all = count_pass();
+        size_t fr = 0, tot = 0;
+        CUDA_TRY(cudaMemGetInfo(&fr, &tot));
+        const double budget = 0.25 * (double)fr;
+        nbatch = (int)std::max<double>(1.0, std::ceil((double)all * BYTES_PER_CAND / budget));
+        nbatch = std::max(nbatch, (int)((all + 0xFFFFFFFEll) / 0xFFFFFFFFll));
+    }
+    nbatch_used = nbatch;
+    // V sorted as multi-word integers
+    DevBuf<uint64_t> vs;
+    DevBuf<uint32_t> vdummy;
+    vs.alloc((size_t)n * KW);
+    vdummy.alloc((size_t)n);
+    CUDA_TRY(cudaMemcpyAsync(vs.p, c->dets.p, sizeof(uint64_t) * n * KW, cudaMemcpyDeviceToDevice, st));
+    radix_sort<KW>(vs.p, vdummy.p, n, c->sw, st);
+    const int rblocks = c->n_sm * 4;
+    DevBuf<double> part;
+    DevBuf<unsigned long long> npart;
+    part.alloc((size_t)rblocks);
+    npart.alloc((size_t)rblocks);
+    std::vector<double> hp(rblocks);
+    std::vector<unsigned long long> hn(rblocks);
+    double e2 = 0.0;
+    n_pert = 0;
+    candidates = 0;
+    for (int b = 0; b < nbatch; b++) {
+        S.nbatch = nbatch;
+        S.batch = b;
+        const int64_t total = count_pass();
+        candidates += total;
+        if (total == 0) continue;
+        if (total > 0xFFFFFFFFll) throw ShciError{SHCI_ERR_INVALID, "too many candidates in one batch: more batches"};
+        DevBuf<uint64_t> cand;
+        DevBuf<double> terms;
+        DevBuf<uint32_t> idx;
+        cand.alloc((size_t)total * KW);
+        terms.alloc((size_t)total);
+        idx.alloc((size_t)total);
+        S.off = off.p;
+        S.out = cand.p;
+        S.terms = terms.p;
+        k_select<W, true, true><<<blocks, SEL_THREADS, 0, st>>>(S, I);
+        KERNEL_CHECK();
+        const int gb = (int)std::min<int64_t>(ceil_div(total, SEL_THREADS), (int64_t)c->n_sm * 16);
+        k_iota<<<gb, SEL_THREADS, 0, st>>>(idx.p, total);
+        KERNEL_CHECK();
+        g_kernel_launches += 2;
+        radix_sort<KW>(cand.p, idx.p, total, c->sw, st);
+        k_pt_reduce<W><<<rblocks, SEL_THREADS, 0, st>>>(cand.p, idx.p, terms.p, total, vs.p, n, I, e_var, part.p,
+                                                        npart.p);
+        KERNEL_CHECK();
+        g_kernel_launches += 1;
+        CUDA_TRY(cudaMemcpyAsync(hp.data(), part.p, sizeof(double) * rblocks, cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaMemcpyAsync(hn.data(), npart.p, sizeof(unsigned long long) * rblocks, cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+        for (int x = 0; x < rblocks; x++) {
+            e2 += hp[x];
+            n_pert += (int64_t)hn[x];
+        }
+    }
+    return e2;
+}
+
+void pt2(shci_ctx *c, const double *coef, double e_var, double eps2, int nbatch, double *e2, int64_t *n_pert,
+         int mem) {
+    if (!c->built) throw ShciError{SHCI_ERR_STATE, "build the connectivity before the second-order energy"};
+    if (!(eps2 > 0.0) || !std::isfinite(eps2)) throw ShciError{SHCI_ERR_INVALID, "eps2 must be positive and finite"};
+    if (!std::isfinite(e_var)) throw ShciError{SHCI_ERR_INVALID, "e_var must be finite"};
+    if (!coef || !e2) throw ShciError{SHCI_ERR_INVALID, "null pointer"};
+    if (nbatch < 0 || nbatch > 1 << 20) throw ShciError{SHCI_ERR_INVALID, "n_batches must be in [0, 2^20]"};
+    if (mem != SHCI_MEM_HOST && mem != SHCI_MEM_DEVICE) throw ShciError{SHCI_ERR_INVALID, "unknown mem_space"};
+    if (c->n_orb > 128) throw ShciError{SHCI_ERR_INVALID, "up to 128 orbitals"};
+    cudaStream_t st = c->st;
+    cudaEvent_t e0, e1;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    CUDA_TRY(cudaEventRecord(e0, st));
+    if (!c->hb_valid) {
+        build_hb_list(c, 1, c->hb_same);
+        build_hb_list(c, 0, c->hb_opp);
+        c->hb_valid = true;
+    }
+    const double *cd = coef;
+    DevBuf<double> cbuf;
+    if (mem == SHCI_MEM_HOST) {
+        cbuf.alloc((size_t)c->n_det);
+        CUDA_TRY(cudaMemcpyAsync(cbuf.p, coef, sizeof(double) * c->n_det, cudaMemcpyHostToDevice, st));
+        cd = cbuf.p;
+    }
+    int64_t np = 0, cands = 0;
+    int used = 0;
+    const double v = c->W == 1 ? pt2_w<1>(c, cd, e_var, eps2, nbatch, np, used, cands)
+                               : pt2_w<2>(c, cd, e_var, eps2, nbatch, np, used, cands);
+    *e2 = v;
+    if (n_pert) *n_pert = np;
+    CUDA_TRY(cudaEventRecord(e1, st));
+    CUDA_TRY(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->stats.pt2_ms = ms;
+    c->stats.pt2_batches = used;
+    c->stats.pt2_terms = cands;
 }
 
 void select_dets(shci_ctx *c, int k, const double *coef, double eps1, int64_t cap, uint64_t *out, int64_t *n_out,

@@ -102,3 +102,67 @@ def test_full_space_selects_nothing_and_bad_arguments(P, oracle_mod):
     with pytest.raises(P.ShciError):
         P.shci_select(B.ctx.handle, G.dev(np.ones((9, fci.shape[0]))), 1e-3)   # k out of range
     B.close()
+
+
+# ---------------------------------------------------------------- screened Epstein-Nesbet PT2 (Sec. II.B, Eq. 7)
+
+def _pt2_check(P, O, B, dets, c, e_var, eps2, n_batches=0):
+    """GPU dE2 against the oracle's.  Terms within 1e-9 of eps2 may be kept on
+    one side and dropped on the other: the GPU value must match the oracle
+    at eps2 (1 - 1e-9) or at eps2 (1 + 1e-9), to 1e-10 relative."""
+    got, npert = P.shci_pt2(B.ctx.handle, G.dev(c), e_var, eps2, n_batches)
+    lo = O.pt2(dets, c, e_var, eps2 * (1 - 1e-9))
+    hi = O.pt2(dets, c, e_var, eps2 * (1 + 1e-9))
+    ok = [abs(got - r[0]) <= 1e-10 * max(1e-6, abs(r[0])) and npert == r[1] for r in (lo, hi)]
+    assert any(ok), (got, npert, lo, hi)
+    st = P.shci_get_stats(B.ctx.handle)
+    assert st["pt2_ms"] > 0.0 and st["pt2_batches"] >= 1 and st["pt2_terms"] >= npert
+    return got, npert
+
+
+def test_pt2_full_ci_subset_and_batches(P, oracle_mod):
+    n, na, nb = 8, 3, 2
+    h, eri, ec = S.integrals(n, 10, 4242)
+    fci = S.fci_dets(n, na, nb)
+    rng = np.random.default_rng(11)
+    v = fci[np.sort(rng.choice(fci.shape[0], 30, replace=False))]
+    O = oracle_mod.System(h, eri, ec)
+    Hv = O.dense_h(v)
+    c = rng.standard_normal(v.shape[0])
+    c /= np.linalg.norm(c)
+    e_var = float(c @ Hv @ c)
+    B = G.Built(P, h, eri, ec, v, na, nb)
+    for eps2 in (1e-2, 1e-4, 1e-10):
+        ref, npert = _pt2_check(P, O, B, v, c, e_var, eps2)
+        for nbt in (1, 3, 7):                        # the batching does not change the sum
+            got, np2 = P.shci_pt2(B.ctx.handle, G.dev(c), e_var, eps2, nbt)
+            assert np2 == npert and abs(got - ref) <= 1e-13 * abs(ref)
+        assert P.shci_get_stats(B.ctx.handle)["pt2_batches"] == 7
+    B.close()
+    Bf = G.Built(P, h, eri, ec, fci, na, nb)
+    assert P.shci_pt2(Bf.ctx.handle, G.dev(np.ones(fci.shape[0])), -1.0, 1e-8) == (0.0, 0)
+    for bad in (0.0, -1.0, float("nan")):
+        with pytest.raises(P.ShciError):
+            P.shci_pt2(Bf.ctx.handle, G.dev(np.ones(fci.shape[0])), -1.0, bad)
+    Bf.close()
+
+
+def test_pt2_selected_space_ground_state(P, oracle_mod):
+    cfg, h, eri, ec, dets = G.system("sel_24o_6a6b_1m", 600)
+    O = oracle_mod.System(h, eri, ec)
+    B = G.Built(P, h, eri, ec, dets, 6, 6)
+    e, vecs, it = B.davidson(1, tol=1e-10)
+    got, npert = _pt2_check(P, O, B, dets, vecs[0], float(e[0]), 1e-5)
+    assert got < 0.0 and npert > 0
+    # host coefficients, same value
+    assert P.shci_pt2(B.ctx.handle, np.ascontiguousarray(vecs[0]), float(e[0]), 1e-5)[0] == got
+    B.close()
+
+
+def test_pt2_two_word_strings(P, oracle_mod):
+    cfg, h, eri, ec, dets = G.system("sel_76o_14a14b_50m", 12)
+    O = oracle_mod.System(h, eri, ec)
+    B = G.Built(P, h, eri, ec, dets, 14, 14)
+    e, vecs, it = B.davidson(1, tol=1e-10)
+    _pt2_check(P, O, B, dets, vecs[0], float(e[0]), 3e-3)
+    B.close()
