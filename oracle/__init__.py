@@ -98,6 +98,10 @@ def _load():
         lib.oracle_pt2.restype = ctypes.c_int
         lib.oracle_pt2.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, _f64p, _f64p, ctypes.c_int64,
                                    _u64p, _f64p, ctypes.c_double, ctypes.c_double, _f64p, _i64p]
+        lib.oracle_pt2_sample.restype = ctypes.c_int
+        lib.oracle_pt2_sample.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, _f64p, _f64p,
+                                          ctypes.c_int64, _u64p, _f64p, ctypes.c_double, ctypes.c_double,
+                                          ctypes.c_double, ctypes.c_int64, ctypes.c_int64, _i64p, _i64p, _f64p]
         lib.oracle_num_threads.restype = ctypes.c_int
         lib.oracle_num_threads.argtypes = []
         _lib = lib
@@ -209,6 +213,24 @@ class System:
         if rc != 0:
             raise RuntimeError("oracle_pt2 failed (%d)" % rc)
         return float(e2[0]), int(npert[0])
+
+    def pt2_sample(self, dets, c, e_var, eps2, eps2_d, draws):
+        """One sample of the stochastic second-order energy of Sec. II.B (Eq. 9)
+        at eps2 and at eps2_d, for the drawn indices `draws` (n_d of them, with
+        repeats) of V sampled with p_i proportional to |c_i| (Eq. 10)."""
+        dets = _u64(dets)
+        c = _f64(np.ravel(c))
+        draws = np.asarray(draws, np.int64)
+        sidx, sw = np.unique(draws, return_counts=True)
+        sidx, sw = _i64(sidx), _i64(sw)
+        out = np.zeros(2)
+        rc = _load().oracle_pt2_sample(self.n, n_words(dets), self.e_core, _p(self.h, _f64p), _p(self.eri, _f64p),
+                                       dets.shape[0], _p(dets, _u64p), _p(c, _f64p), float(e_var), float(eps2),
+                                       float(eps2_d), draws.size, sidx.size, _p(sidx, _i64p), _p(sw, _i64p),
+                                       _p(out, _f64p))
+        if rc != 0:
+            raise RuntimeError("oracle_pt2_sample failed (%d)" % rc)
+        return float(out[0]), float(out[1])
 
     # ---------------------------------------------------------- sigma
     def sigma_rows(self, dets, c, rows) -> np.ndarray:

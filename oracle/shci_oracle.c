@@ -752,3 +752,118 @@ int oracle_pt2(int n, int W, double e_core, const double *h, const double *eri, 
     *n_pert = runs;
     return 0;
 }
+
+/* ------------------------------------------------------------ stochastic PT2 estimator */
+
+/* records: 2W determinant words, then t1, t2, |H_ai c_i| (bits), generation index */
+static int cmp_st_records(const void *a, const void *b)
+{
+    const uint64_t *x = (const uint64_t *)a, *y = (const uint64_t *)b;
+    for (int w = g_sel_words - 1; w >= 0; w--) {
+        if (x[w] != y[w]) return x[w] < y[w] ? -1 : 1;
+    }
+    return (x[g_sel_words + 3] > y[g_sel_words + 3]) - (x[g_sel_words + 3] < y[g_sel_words + 3]);
+}
+
+/*
+ * One sample of the stochastic second-order energy of Sec. II.B (Eq. 9): the
+ * sample holds n_dist distinct determinants sidx[] of V with copy counts sw[]
+ * (sum n_d), drawn with p_i = |c_i| / sum_j |c_j| (Eq. 10).  For every a
+ * outside V:
+ *   S1 = sum_i w_i c_i H_ai / p_i,
+ *   S2 = sum_i (w_i (n_d - 1) / p_i - w_i^2 / p_i^2) c_i^2 H_ai^2,
+ * both over the sampled i with |H_ai c_i| >= eps, and the sample's value is
+ *   sum_a (S1^2 + S2) / (E_V - H_aa) / (n_d (n_d - 1)).
+ * out[0]: eps = eps2; out[1]: eps = eps2_d (the same sample, Eq. 8).
+ * Returns 0, -1 on OOM, -2 on duplicates in V, -3 on a bad sample.
+ */
+int oracle_pt2_sample(int n, int W, double e_core, const double *h, const double *eri, int64_t n_det,
+                      const uint64_t *dets, const double *c, double e_var, double eps2, double eps2_d, int64_t n_d,
+                      int64_t n_dist, const int64_t *sidx, const int64_t *sw, double *out)
+{
+    if (n_d < 2) return -3;
+    oints I = {n, W, e_core, h, eri};
+    dtable t;
+    int rc = dtable_init(&t, n_det, W, dets);
+    if (rc) { free(t.slot); return rc; }
+    double csum = 0.0;
+    for (int64_t i = 0; i < n_det; i++) csum += fabs(c[i]);
+    const int W2 = 2 * W, nso = 2 * n, R = 2 * W + 4;
+    int64_t m = 0, mcap = 1024;
+    uint64_t *buf = (uint64_t *)malloc(sizeof(uint64_t) * R * mcap);
+    if (!buf) { free(t.slot); return -1; }
+    uint64_t x[8];
+    for (int64_t u = 0; u < n_dist; u++) {
+        const int64_t i = sidx[u];
+        if (i < 0 || i >= n_det || sw[u] < 1) { free(buf); free(t.slot); return -3; }
+        const double pi = fabs(c[i]) / csum, wi = (double)sw[u];
+        if (!(pi > 0.0)) { free(buf); free(t.slot); return -3; }
+        const double f1 = wi / pi, f2 = wi * (double)(n_d - 1) / pi - wi * wi / (pi * pi);
+        const uint64_t *d = dets + i * W2;
+        for (int q = 0; q < nso; q++) {
+            if (!occ(&I, d, q)) continue;
+            for (int pass = 0; pass < 2; pass++) {
+                for (int s = (pass ? q + 1 : nso); s < (pass ? nso : nso + 1); s++) {
+                    if (pass && !occ(&I, d, s)) continue;
+                    for (int p = 0; p < nso; p++) {
+                        if (occ(&I, d, p)) continue;
+                        for (int r = (pass ? p + 1 : nso); r < (pass ? nso : nso + 1); r++) {
+                            if (pass && occ(&I, d, r)) continue;
+                            if (!pass && so_spin(&I, p) != so_spin(&I, q)) continue;
+                            if (pass && so_spin(&I, q) + so_spin(&I, s) != so_spin(&I, p) + so_spin(&I, r))
+                                continue;
+                            memcpy(x, d, 8 * W2);
+                            put(&I, x, q, 0);
+                            put(&I, x, p, 1);
+                            if (pass) { put(&I, x, s, 0); put(&I, x, r, 1); }
+                            if (dtable_find(&t, x) >= 0) continue;
+                            const double hv = matrix_element(&I, x, d);
+                            const double mag = fabs(hv) * fabs(c[i]);
+                            if (!(mag >= eps2)) continue;
+                            const double t1 = f1 * c[i] * hv, t2 = f2 * c[i] * c[i] * hv * hv;
+                            if (m == mcap) {
+                                mcap *= 2;
+                                uint64_t *nb = (uint64_t *)realloc(buf, sizeof(uint64_t) * R * mcap);
+                                if (!nb) { free(buf); free(t.slot); return -1; }
+                                buf = nb;
+                            }
+                            memcpy(buf + m * R, x, 8 * W2);
+                            memcpy(buf + m * R + W2, &t1, 8);
+                            memcpy(buf + m * R + W2 + 1, &t2, 8);
+                            memcpy(buf + m * R + W2 + 2, &mag, 8);
+                            buf[m * R + W2 + 3] = (uint64_t)m;
+                            m++;
+                        }
+                    }
+                }
+            }
+        }
+    }
+    free(t.slot);
+    g_sel_words = W2;
+    qsort(buf, (size_t)m, sizeof(uint64_t) * R, cmp_st_records);
+    double sum = 0.0, sum_d = 0.0;
+    for (int64_t e = 0; e < m;) {
+        int64_t f = e;
+        double s1 = 0.0, s2 = 0.0, s1d = 0.0, s2d = 0.0;
+        while (f < m && memcmp(buf + f * R, buf + e * R, 8 * W2) == 0) {
+            double t1, t2, mag;
+            memcpy(&t1, buf + f * R + W2, 8);
+            memcpy(&t2, buf + f * R + W2 + 1, 8);
+            memcpy(&mag, buf + f * R + W2 + 2, 8);
+            s1 += t1;
+            s2 += t2;
+            if (mag >= eps2_d) { s1d += t1; s2d += t2; }
+            f++;
+        }
+        const double den = e_var - diag_element(&I, buf + e * R);
+        sum += (s1 * s1 + s2) / den;
+        sum_d += (s1d * s1d + s2d) / den;
+        e = f;
+    }
+    free(buf);
+    const double norm = 1.0 / ((double)n_d * (double)(n_d - 1));
+    out[0] = sum * norm;
+    out[1] = sum_d * norm;
+    return 0;
+}

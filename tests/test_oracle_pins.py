@@ -402,3 +402,35 @@ def test_pt2_matches_dense_hamiltonian(oracle_mod):
     got, _ = O.pt2(fci[:1], np.ones(1), e0, 1e-300)
     assert abs(got - want) <= 1e-12 * abs(want)
     assert O.pt2(fci, np.ones(fci.shape[0]) / np.sqrt(fci.shape[0]), 0.0, 1e-8) == (0.0, 0)
+
+
+def test_stochastic_pt2_is_unbiased_exactly(oracle_mod):
+    """The sample estimator of Sec. II.B (Eq. 9) averaged over every possible
+    sample of n_d draws (multinomial weights, p_i = |c_i| / sum |c|, Eq. 10)
+    equals the deterministic screened energy (Eq. 7) at both thresholds: the
+    exact expectation over all multisets, not a statistical estimate."""
+    import math
+    n, na, nb = 6, 2, 2
+    h, eri, ec = S.integrals(n, 8, 77)
+    fci = S.fci_dets(n, na, nb)
+    O = oracle_mod.System(h, eri, ec)
+    rng = np.random.default_rng(5)
+    vidx = np.sort(rng.choice(fci.shape[0], 4, replace=False))
+    v = fci[vidx]
+    c = rng.standard_normal(4)
+    c /= np.linalg.norm(c)
+    e_var = float(c @ O.dense_h(v) @ c)
+    p = np.abs(c) / np.abs(c).sum()
+    eps2, eps2_d = 1e-3, 5e-2
+    for n_d in (2, 3, 4):
+        exp_all = exp_d = 0.0
+        for combo in itertools.combinations_with_replacement(range(4), n_d):
+            w = np.bincount(combo, minlength=4)
+            prob = math.factorial(n_d) / np.prod([math.factorial(k) for k in w]) * np.prod(p ** w)
+            s_all, s_d = O.pt2_sample(v, c, e_var, eps2, eps2_d, np.array(combo))
+            exp_all += prob * s_all
+            exp_d += prob * s_d
+        det_all, _ = O.pt2(v, c, e_var, eps2)
+        det_d, _ = O.pt2(v, c, e_var, eps2_d)
+        assert abs(exp_all - det_all) <= 1e-12 * abs(det_all)
+        assert abs(exp_d - det_d) <= 1e-12 * abs(det_d)
