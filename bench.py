@@ -629,6 +629,24 @@ def run_select(args):
         st = P.shci_get_stats(H)
         pt.append({"eps2": eps2, "e_var": float(e0[0]), "dE2": e2, "n_pert": npert, "terms": st["pt2_terms"],
                    "batches": st["pt2_batches"], "seconds": dt, "device_ms": st["pt2_ms"]})
+    # semistochastic (Eq. 8): deterministic at eps2_d plus sampled eps2 - eps2_d, beside the deterministic eps2
+    semi = None
+    if args.semi_eps2:
+        eps2, eps2_d = args.semi_eps2, (args.eps2 or [1e-5])[0]
+        t = time.perf_counter()
+        est, err = P.shci_pt2_semistochastic(H, vecs[0].contiguous(), float(e0[0]), eps2, eps2_d, args.semi_nd,
+                                             args.semi_samples, 2024)
+        torch.cuda.synchronize()
+        t_semi = time.perf_counter() - t
+        t = time.perf_counter()
+        ref, npert = P.shci_pt2(H, vecs[0].contiguous(), float(e0[0]), eps2)
+        torch.cuda.synchronize()
+        t_det = time.perf_counter() - t
+        st = P.shci_get_stats(H)
+        semi = {"eps2": eps2, "eps2_d": eps2_d, "n_d": args.semi_nd, "n_samples": args.semi_samples,
+                "dE2_semistochastic": est, "std_error": err, "seconds": t_semi,
+                "dE2_deterministic": ref, "deterministic_seconds": t_det, "deterministic_batches": st["pt2_batches"],
+                "deterministic_terms": st["pt2_terms"], "n_pert": npert}
     # the same screened energy on a 600-determinant space of the same shape: GPU and oracle side by side
     h6, eri6, ec6, d6 = S.make_system(cfg, 600)
     c6 = P.Context(0, torch.cuda.current_stream())
@@ -648,7 +666,7 @@ def run_select(args):
     c6.close()
     print(json.dumps({"workload": workload_desc(cfg) + ", heat-bath selection with the converged 2-root "
                                                        "coefficients; screened PT2 of the ground state",
-                      "lines": lines, "pt2": pt,
+                      "lines": lines, "pt2": pt, "semistochastic": semi,
                       "pt2_600_dets": {"gpu_s": t_g6, "oracle_s": t_o6, "oracle_cores": 1, "dE2_gpu": g6,
                                        "dE2_oracle": o6, "eps2": 1e-5}}))
     ctx.close()
@@ -747,6 +765,9 @@ def main():
     ap.add_argument("--eps1", type=float, action="append", help="selection thresholds (select workload)")
     ap.add_argument("--select-sample", type=int, default=200, help="determinants of V the oracle screens")
     ap.add_argument("--eps2", type=float, action="append", help="PT2 screening thresholds (select workload)")
+    ap.add_argument("--semi-eps2", type=float, default=1e-6, help="semistochastic eps2 (0: skip)")
+    ap.add_argument("--semi-nd", type=int, default=20000, help="draws per semistochastic sample")
+    ap.add_argument("--semi-samples", type=int, default=16, help="semistochastic samples")
     args = ap.parse_args()
     if args.workload != "main":
         {"fci": run_fci, "large": run_large, "adjoint": run_adjoint, "batch": run_batch,

@@ -197,6 +197,37 @@ int shci_select(shci_ctx *ctx, int k_roots, const double *c, double eps1, int64_
 int shci_pt2(shci_ctx *ctx, const double *c, double e_var, double eps2, int n_batches, double *e2, int64_t *n_pert,
              int mem_space);
 
+/* Draws for the stochastic second-order energy: n_draws indices of V drawn
+ * independently with p_i = |c_i| / sum_j |c_j| (Sec. II.B, Eq. 10) by Walker's
+ * alias method (table by Vose's two-list construction).  Draw d uses the
+ * SplitMix64 output for the counter seed + (d + 1) * 0x9E3779B97F4A7C15: the
+ * high 32 bits pick a column, the low 32 bits a uniform in [0, 1).  c:
+ * [n_det], draws: [n_draws] int64, both in mem_space. */
+int shci_alias_draw(shci_ctx *ctx, const double *c, int64_t n_draws, uint64_t seed, int64_t *draws, int mem_space);
+
+/* The stochastic second-order energy of Sec. II.B (Eq. 9) for n_samples
+ * samples of n_d draws each (draws: [n_samples][n_d] indices of V with
+ * repeats, in mem_space; c: [n_det] in mem_space, p_i as in shci_alias_draw):
+ * for every a outside V, S1 = sum_i w_i c_i H_ai / p_i and
+ * S2 = sum_i (w_i (n_d - 1) / p_i - w_i^2 / p_i^2) c_i^2 H_ai^2 over the
+ * distinct sampled i (w_i copies) with |H_ai c_i| >= eps, and the sample's
+ * value is sum_a (S1^2 + S2) / (E_V - H_aa) / (n_d (n_d - 1)).  out (host,
+ * [n_samples][2]) receives the value at eps = eps2 and at eps = eps2_d
+ * (0 < eps2 <= eps2_d).  Every draw must index a determinant with c_i != 0;
+ * n_d >= 2. */
+int shci_pt2_samples(shci_ctx *ctx, const double *c, double e_var, double eps2, double eps2_d, int64_t n_d,
+                     int n_samples, const int64_t *draws, double *out, int mem_space);
+
+/* Semistochastic second-order energy (Sec. II.B, Eq. 8): the deterministic
+ * energy at eps2_d (shci_pt2) plus the mean over n_samples samples of n_d
+ * alias draws (shci_alias_draw with `seed`) of the difference of the
+ * stochastic values at eps2 and at eps2_d (shci_pt2_samples; the same
+ * samples, so their noise largely cancels).  *e2 receives the estimate and
+ * *e2_err (may be NULL) its standard error over the samples (0 for one
+ * sample).  eps2_d = eps2 gives the deterministic energy exactly. */
+int shci_pt2_semistochastic(shci_ctx *ctx, const double *c, double e_var, double eps2, double eps2_d, int64_t n_d,
+                            int n_samples, uint64_t seed, double *e2, double *e2_err, int mem_space);
+
 /* Adjoint of a variational eigenvalue (no counterpart in the paper, which
  * has no derivatives): for a normalised real eigenvector c of H on V,
  * E = c^T H c and, by Hellmann-Feynman, dE/dX = c^T (dH/dX) c.  Writes

@@ -37,7 +37,8 @@ EXPORTED = [
     "shci_create", "shci_destroy", "shci_last_error", "shci_load_integrals", "shci_build_connectivity",
     "shci_get_diag", "shci_get_pairs", "shci_get_row", "shci_sigma", "shci_sigma_noalloc", "shci_energy_backward",
     "shci_batch_create", "shci_batch_davidson", "shci_batch_get_stats", "shci_batch_destroy", "shci_davidson",
-    "shci_davidson_history", "shci_select", "shci_pt2", "shci_get_stats", "shci_set_timing",
+    "shci_davidson_history", "shci_select", "shci_pt2", "shci_alias_draw", "shci_pt2_samples",
+    "shci_pt2_semistochastic", "shci_get_stats", "shci_set_timing",
 ]
 
 
@@ -110,6 +111,10 @@ def load_library(path: str = LIB_PATH):
         "shci_davidson_history": (i32, [vp, i32, vp, vp, vp, ctypes.POINTER(i32)]),
         "shci_select": (i32, [vp, i32, vp, f64, i64, vp, ctypes.POINTER(i64), i32]),
         "shci_pt2": (i32, [vp, vp, f64, f64, i32, ctypes.POINTER(f64), ctypes.POINTER(i64), i32]),
+        "shci_alias_draw": (i32, [vp, vp, i64, ctypes.c_uint64, vp, i32]),
+        "shci_pt2_samples": (i32, [vp, vp, f64, f64, f64, i64, i32, vp, vp, i32]),
+        "shci_pt2_semistochastic": (i32, [vp, vp, f64, f64, f64, i64, i32, ctypes.c_uint64, ctypes.POINTER(f64),
+                                          ctypes.POINTER(f64), i32]),
         "shci_get_stats": (i32, [vp, ctypes.POINTER(shci_stats_t)]),
         "shci_set_timing": (i32, [vp, i32]),
     }
@@ -305,6 +310,44 @@ def shci_pt2(ctx, c, e_var, eps2, n_batches=0):
     _check(ctx, load_library().shci_pt2(ctx, pc, float(e_var), float(eps2), int(n_batches), ctypes.byref(e2),
                                         ctypes.byref(npert), mc))
     return e2.value, npert.value
+
+
+def shci_alias_draw(ctx, c, n_draws, seed):
+    """n_draws indices of V drawn with p_i = |c_i| / sum |c| (alias method), in c's memory space."""
+    pc, mc, kc = _ptr(c, np.float64)
+    if mc == SHCI_MEM_DEVICE:
+        import torch
+        out = torch.empty(int(n_draws), dtype=torch.int64, device=c.device)
+    else:
+        out = np.empty(int(n_draws), np.int64)
+    po, mo, ko = _ptr(out, np.int64)
+    _check(ctx, load_library().shci_alias_draw(ctx, pc, int(n_draws), int(seed) & ((1 << 64) - 1), po, mc))
+    return out
+
+
+def shci_pt2_samples(ctx, c, e_var, eps2, eps2_d, draws):
+    """[n_samples, 2]: the stochastic second-order energy of each sample (rows
+    of draws, [n_samples, n_d]) at eps2 and at eps2_d."""
+    pc, mc, kc = _ptr(c, np.float64)
+    pd, md, kd = _ptr(draws, np.int64)
+    if mc != md:
+        raise ValueError("c and draws must live in the same memory space")
+    n_samples, n_d = int(draws.shape[0]), int(draws.shape[1])
+    out = np.empty((n_samples, 2))
+    _check(ctx, load_library().shci_pt2_samples(ctx, pc, float(e_var), float(eps2), float(eps2_d), n_d, n_samples,
+                                                pd, out.ctypes.data, mc))
+    return out
+
+
+def shci_pt2_semistochastic(ctx, c, e_var, eps2, eps2_d, n_d, n_samples, seed):
+    """(dE2, standard error): deterministic at eps2_d plus the sampled difference between eps2 and eps2_d."""
+    pc, mc, kc = _ptr(c, np.float64)
+    e2 = ctypes.c_double(0.0)
+    err = ctypes.c_double(0.0)
+    _check(ctx, load_library().shci_pt2_semistochastic(ctx, pc, float(e_var), float(eps2), float(eps2_d), int(n_d),
+                                                       int(n_samples), int(seed) & ((1 << 64) - 1),
+                                                       ctypes.byref(e2), ctypes.byref(err), mc))
+    return e2.value, err.value
 
 
 def shci_energy_backward(ctx, c, grad_out_scale, dE_dh, dE_deri_packed):

@@ -231,6 +231,29 @@ int shci_pt2(shci_ctx *c, const double *coef, double e_var, double eps2, int n_b
     });
 }
 
+int shci_alias_draw(shci_ctx *c, const double *coef, int64_t n_draws, uint64_t seed, int64_t *draws, int mem) {
+    return guarded(c, [&] {
+        shci::alias_draw(c, coef, n_draws, seed, draws, mem);
+        return SHCI_OK;
+    });
+}
+
+int shci_pt2_samples(shci_ctx *c, const double *coef, double e_var, double eps2, double eps2_d, int64_t n_d,
+                     int n_samples, const int64_t *draws, double *out, int mem) {
+    return guarded(c, [&] {
+        shci::pt2_samples(c, coef, e_var, eps2, eps2_d, n_d, n_samples, draws, out, mem);
+        return SHCI_OK;
+    });
+}
+
+int shci_pt2_semistochastic(shci_ctx *c, const double *coef, double e_var, double eps2, double eps2_d, int64_t n_d,
+                            int n_samples, uint64_t seed, double *e2, double *e2_err, int mem) {
+    return guarded(c, [&] {
+        shci::pt2_semistochastic(c, coef, e_var, eps2, eps2_d, n_d, n_samples, seed, e2, e2_err, mem);
+        return SHCI_OK;
+    });
+}
+
 int shci_get_stats(shci_ctx *c, shci_stats_t *out) {
     return guarded(c, [&] {
         if (!out) throw ShciError{SHCI_ERR_INVALID, "null pointer"};

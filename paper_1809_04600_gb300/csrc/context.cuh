@@ -123,6 +123,11 @@ void select_dets(shci_ctx *c, int k, const double *coef, double eps1, int64_t ca
                  int mem);
 void pt2(shci_ctx *c, const double *coef, double e_var, double eps2, int nbatch, double *e2, int64_t *n_pert,
          int mem);
+void alias_draw(shci_ctx *c, const double *coef, int64_t n_draws, uint64_t seed, int64_t *out, int mem);
+void pt2_samples(shci_ctx *c, const double *coef, double e_var, double eps2, double eps2_d, int64_t n_d,
+                 int n_samples, const int64_t *draws, double *out, int mem);
+void pt2_semistochastic(shci_ctx *c, const double *coef, double e_var, double eps2, double eps2_d, int64_t n_d,
+                        int n_samples, uint64_t seed, double *e2, double *e2_err, int mem);
 
 // davidson.cu
 int davidson(shci_ctx *c, int k, double tol, int max_iter, const double *guess, double *energies,

@@ -134,6 +134,10 @@ struct SelArgs {
     // second-order energy: the terms H_ai c_i of determinants a in hash batch `batch` of `nbatch`
     int nbatch, batch;
     double *terms;                          // fill pass: [total]
+    // stochastic estimator (Eq. 9): per sampled determinant w/p and
+    // w (n_d - 1) / p - w^2 / p^2; second term and |H_ai c_i| per candidate
+    const double *f1, *f2;
+    double *terms2, *mags;
 };
 
 // batch of a determinant (a SplitMix64-style mix of its words)
@@ -203,7 +207,7 @@ __device__ __forceinline__ double key_bound(float kf) {
 template <int W, bool FILL, bool PT>
 __device__ __forceinline__ void sel_emit(const SelArgs &S, const DevInts &I, unsigned long long &cnt, int64_t base,
                                          unsigned *cursor, const Str<W> &A, const Str<W> &B, double ci,
-                                         const Str<W> &a, const Str<W> &b) {
+                                         double f1, double f2, const Str<W> &a, const Str<W> &b) {
     if (PT && S.nbatch > 1 && det_batch<W>(a, b, S.nbatch) != S.batch) return;
     if (!FILL) {
         cnt++;
@@ -216,7 +220,16 @@ __device__ __forceinline__ void sel_emit(const SelArgs &S, const DevInts &I, uns
         o[k] = a.w[k];
         o[W + k] = b.w[k];
     }
-    if (PT) S.terms[pos] = hij_offdiag<W>(I, A, B, a, b) * ci;
+    if (PT) {
+        const double hv = hij_offdiag<W>(I, A, B, a, b);
+        if (S.f1) {
+            S.terms[pos] = f1 * ci * hv;
+            S.terms2[pos] = f2 * ci * ci * hv * hv;
+            S.mags[pos] = fabs(hv) * fabs(ci);
+        } else {
+            S.terms[pos] = hv * ci;
+        }
+    }
 }
 
 // walk one sorted list from slot; `spin` 0: both moves in a (same spin alpha),
@@ -224,8 +237,8 @@ __device__ __forceinline__ void sel_emit(const SelArgs &S, const DevInts &I, uns
 template <int W, bool FILL, bool PT>
 __device__ __forceinline__ void sel_walk(const SelArgs &S, const DevInts &I, const int64_t *off, const uint32_t *rs,
                                          const double *val, const float *kf, int slot, int p, int q, int spin,
-                                         double cmax, double ci, const Str<W> &A, const Str<W> &B,
-                                         unsigned long long &cnt, int64_t base, unsigned *cursor) {
+                                         double cmax, double ci, double f1, double f2, const Str<W> &A,
+                                         const Str<W> &B, unsigned long long &cnt, int64_t base, unsigned *cursor) {
     const int64_t e0 = __ldg(&off[slot]), e1 = __ldg(&off[slot + 1]);
     for (int64_t e = e0; e < e1; e++) {
         if (key_bound(__ldg(&kf[e])) * cmax < S.eps1) break;
@@ -243,7 +256,7 @@ __device__ __forceinline__ void sel_walk(const SelArgs &S, const DevInts &I, con
             flip_bit(a, p); flip_bit(a, r); flip_bit(b, q); flip_bit(b, s);
         }
         if (!(__ldg(&val[e]) * cmax >= S.eps1)) continue;
-        sel_emit<W, FILL, PT>(S, I, cnt, base, cursor, A, B, ci, a, b);
+        sel_emit<W, FILL, PT>(S, I, cnt, base, cursor, A, B, ci, f1, f2, a, b);
     }
 }
 
@@ -260,10 +273,14 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select(SelArgs S, DevInts I) {
     const int64_t units = u_sa + u_sb + u_paa + u_pbb + u_pab;
     const int64_t warps = (int64_t)gridDim.x * (SEL_THREADS / 32);
     for (int64_t i = ((int64_t)blockIdx.x * SEL_THREADS + threadIdx.x) >> 5; i < S.n_det; i += warps) {
-        double cmax = 0.0, ci = 0.0;
+        double cmax = 0.0, ci = 0.0, f1 = 0.0, f2 = 0.0;
         if (PT) {
             ci = __ldg(&S.c[i]);
             cmax = fabs(ci);
+            if (S.f1) {
+                f1 = __ldg(&S.f1[i]);
+                f2 = __ldg(&S.f2[i]);
+            }
         } else {
             for (int l = 0; l < S.k; l++) cmax = fmax(cmax, fabs(__ldg(&S.c[(int64_t)l * S.n_det + i])));
         }
@@ -287,8 +304,8 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select(SelArgs S, DevInts I) {
                     flip_bit(sj, r);
                     const double hv = single_exc<W>(I, si, sj, alpha ? B : A);
                     if (!(fabs(hv) * cmax >= S.eps1)) continue;
-                    if (alpha) sel_emit<W, FILL, PT>(S, I, cnt, base, &cursor[wib], A, B, ci, sj, B);
-                    else sel_emit<W, FILL, PT>(S, I, cnt, base, &cursor[wib], A, B, ci, A, sj);
+                    if (alpha) sel_emit<W, FILL, PT>(S, I, cnt, base, &cursor[wib], A, B, ci, f1, f2, sj, B);
+                    else sel_emit<W, FILL, PT>(S, I, cnt, base, &cursor[wib], A, B, ci, f1, f2, A, sj);
                     continue;
                 }
                 v -= u_sa + u_sb;
@@ -303,13 +320,13 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select(SelArgs S, DevInts I) {
                     const Str<W> &si = alpha ? A : B;
                     const int p = nth_set(si, x), q = nth_set(si, y);
                     sel_walk<W, FILL, PT>(S, I, S.ss_off, S.ss_rs, S.ss_v, S.ss_kf, p * n + q, p, q, alpha ? 0 : 1,
-                                          cmax, ci, A, B, cnt, base, &cursor[wib]);
+                                          cmax, ci, f1, f2, A, B, cnt, base, &cursor[wib]);
                     continue;
                 }
                 v -= u_paa + u_pbb;                                  // opposite-spin pair
                 const int p = nth_set(A, (int)(v / nb)), q = nth_set(B, (int)(v % nb));
-                sel_walk<W, FILL, PT>(S, I, S.os_off, S.os_rs, S.os_v, S.os_kf, p * n + q, p, q, 2, cmax, ci, A, B,
-                                      cnt, base, &cursor[wib]);
+                sel_walk<W, FILL, PT>(S, I, S.os_off, S.os_rs, S.os_v, S.os_kf, p * n + q, p, q, 2, cmax, ci, f1, f2,
+                                      A, B, cnt, base, &cursor[wib]);
             }
         }
         if (!FILL) {
@@ -611,6 +628,392 @@ static double pt2_w(shci_ctx *c, const double *cd, double e_var, double eps2, in
     return e2;
 }
 
+// ---------------------------------------------------------------- stochastic second-order energy
+
+// sum |c_i| in a fixed order: per-block partials, then one block over them
+__global__ void k_abs_partial(const double *__restrict__ c, int64_t n, double *__restrict__ part) {
+    double s = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        s += fabs(c[i]);
+    __shared__ double red[SEL_THREADS / 32];
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < SEL_THREADS / 32; w++) t += red[w];
+        part[blockIdx.x] = t;
+    }
+}
+
+__global__ void k_sum_in_order(const double *__restrict__ part, int m, double *__restrict__ out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double t = 0.0;
+    for (int b = 0; b < m; b++) t += part[b];
+    *out = t;
+}
+
+// Walker's alias table for p_i = |c_i| / sum (Eq. 10), built by Vose's
+// two-list method; one thread, O(n).  small/large: scratch stacks of n.
+__global__ void k_alias_table(const double *__restrict__ c, int64_t n, const double *__restrict__ sum,
+                              double *__restrict__ prob, int64_t *__restrict__ alias, double *__restrict__ q,
+                              int64_t *__restrict__ small, int64_t *__restrict__ large) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const double scale = (double)n / *sum;
+    int64_t ns = 0, nl = 0;
+    for (int64_t i = 0; i < n; i++) {
+        q[i] = fabs(c[i]) * scale;
+        alias[i] = i;
+        if (q[i] < 1.0) small[ns++] = i;
+        else large[nl++] = i;
+    }
+    while (ns > 0 && nl > 0) {
+        const int64_t l = small[--ns], g = large[--nl];
+        prob[l] = q[l];
+        alias[l] = g;
+        q[g] = (q[g] + q[l]) - 1.0;
+        if (q[g] < 1.0) small[ns++] = g;
+        else large[nl++] = g;
+    }
+    while (nl > 0) prob[large[--nl]] = 1.0;
+    while (ns > 0) prob[small[--ns]] = 1.0;      // rounding leftovers
+}
+
+// draw d: r = SplitMix64 output for the counter seed + (d + 1) * golden
+// gamma; column = high 32 bits * n >> 32, uniform u = low 32 bits / 2^32;
+// the column itself when u < prob[column], else its alias
+__global__ void k_alias_draw(const double *__restrict__ prob, const int64_t *__restrict__ alias, int64_t n,
+                             uint64_t seed, int64_t n_draws, int64_t *__restrict__ out) {
+    for (int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; d < n_draws;
+         d += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t z = seed + (uint64_t)(d + 1) * 0x9E3779B97F4A7C15ull;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        const int64_t col = (int64_t)(((z >> 32) * (uint64_t)n) >> 32);
+        const double u = (double)(uint32_t)z * 0x1p-32;
+        out[d] = u < prob[col] ? col : alias[col];
+    }
+}
+
+static double abs_sum(shci_ctx *c, const double *cd, int64_t n) {
+    cudaStream_t st = c->st;
+    const int nb = (int)std::min<int64_t>(ceil_div(n, SEL_THREADS), (int64_t)c->n_sm * 4);
+    DevBuf<double> part, tot;
+    part.alloc((size_t)nb);
+    tot.alloc(1);
+    k_abs_partial<<<nb, SEL_THREADS, 0, st>>>(cd, n, part.p);
+    k_sum_in_order<<<1, 32, 0, st>>>(part.p, nb, tot.p);
+    KERNEL_CHECK();
+    g_kernel_launches += 2;
+    double h = 0.0;
+    CUDA_TRY(cudaMemcpyAsync(&h, tot.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    return h;
+}
+
+// sample prep: run heads of the sorted draws -> distinct index, count, and the
+// per-determinant compact arrays (strings, c_i, w/p, w (n_d - 1)/p - w^2/p^2)
+template <int W>
+__global__ void k_sample_prep(const uint64_t *__restrict__ sorted, int64_t n_d, const int64_t *__restrict__ pos,
+                              const uint64_t *__restrict__ dets, const double *__restrict__ c, double csum,
+                              uint64_t *__restrict__ sdets, double *__restrict__ sc, double *__restrict__ f1,
+                              double *__restrict__ f2) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n_d; e += (int64_t)gridDim.x * blockDim.x) {
+        if (e > 0 && sorted[e - 1] == sorted[e]) continue;
+        int64_t f = e + 1;
+        while (f < n_d && sorted[f] == sorted[e]) f++;
+        const int64_t i = (int64_t)sorted[e], u = pos[e];
+        const double w = (double)(f - e), p = fabs(c[i]) / csum;
+#pragma unroll
+        for (int k = 0; k < 2 * W; k++) sdets[u * 2 * W + k] = dets[i * 2 * W + k];
+        sc[u] = c[i];
+        f1[u] = w / p;
+        f2[u] = w * (double)(n_d - 1) / p - w * w / (p * p);
+    }
+}
+
+__global__ void k_run_heads(const uint64_t *__restrict__ sorted, int64_t n, int64_t *__restrict__ flag) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        flag[e] = (e == 0 || sorted[e - 1] != sorted[e]) ? 1 : 0;
+}
+
+// the runs of one sample: (S1^2 + S2) / (E_V - H_aa) at eps2 (all kept terms)
+// and at eps2_d (terms with |H_ai c_i| >= eps2_d); per-block partials
+template <int W>
+__global__ void __launch_bounds__(SEL_THREADS) k_pts_reduce(const uint64_t *__restrict__ cand,
+                                                           const uint32_t *__restrict__ idx,
+                                                           const double *__restrict__ t1,
+                                                           const double *__restrict__ t2,
+                                                           const double *__restrict__ mag, int64_t total,
+                                                           const uint64_t *__restrict__ vs, int64_t nv, DevInts I,
+                                                           double e_var, double eps2_d, double *__restrict__ part) {
+    constexpr int KW = 2 * W;
+    double acc = 0.0, accd = 0.0;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t *x = cand + e * KW;
+        if (e > 0 && cmp_words<KW>(cand + (e - 1) * KW, x) == 0) continue;
+        int64_t lo = 0, hi = nv;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (cmp_words<KW>(vs + mid * KW, x) < 0) lo = mid + 1;
+            else hi = mid;
+        }
+        if (lo < nv && cmp_words<KW>(vs + lo * KW, x) == 0) continue;
+        double s1 = 0.0, s2 = 0.0, s1d = 0.0, s2d = 0.0;
+        for (int64_t f = e; f < total && cmp_words<KW>(cand + f * KW, x) == 0; f++) {
+            const uint32_t j = idx[f];
+            s1 += t1[j];
+            s2 += t2[j];
+            if (mag[j] >= eps2_d) {
+                s1d += t1[j];
+                s2d += t2[j];
+            }
+        }
+        Str<W> a, b;
+#pragma unroll
+        for (int k = 0; k < W; k++) {
+            a.w[k] = x[k];
+            b.w[k] = x[W + k];
+        }
+        const double den = e_var - hii<W>(I, a, b);
+        acc += (s1 * s1 + s2) / den;
+        accd += (s1d * s1d + s2d) / den;
+    }
+    __shared__ double red[2][SEL_THREADS / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        accd += __shfl_xor_sync(0xffffffffu, accd, o);
+    }
+    if (lane == 0) {
+        red[0][w] = acc;
+        red[1][w] = accd;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s0 = 0.0, s1 = 0.0;
+        for (int x = 0; x < SEL_THREADS / 32; x++) {
+            s0 += red[0][x];
+            s1 += red[1][x];
+        }
+        part[2 * blockIdx.x] = s0;
+        part[2 * blockIdx.x + 1] = s1;
+    }
+}
+
+template <int W>
+static void pt2_samples_w(shci_ctx *c, const double *cd, double e_var, double eps2, double eps2_d, int64_t n_d,
+                          int n_samples, const int64_t *draws, double *out) {
+    cudaStream_t st = c->st;
+    constexpr int KW = 2 * W;
+    const int64_t n = c->n_det;
+    const double csum = abs_sum(c, cd, n);
+    if (!(csum > 0.0)) throw ShciError{SHCI_ERR_INVALID, "all coefficients are zero"};
+    DevBuf<uint64_t> vs;
+    DevBuf<uint32_t> vdummy;
+    vs.alloc((size_t)n * KW);
+    vdummy.alloc((size_t)std::max<int64_t>(n, n_d));
+    CUDA_TRY(cudaMemcpyAsync(vs.p, c->dets.p, sizeof(uint64_t) * n * KW, cudaMemcpyDeviceToDevice, st));
+    radix_sort<KW>(vs.p, vdummy.p, n, c->sw, st);
+    const DevInts I = dev_ints(c);
+    const int blocks = c->n_sm * (2048 / SEL_THREADS);
+    const int rblocks = c->n_sm * 4;
+    DevBuf<uint64_t> sorted, sdets;
+    DevBuf<int64_t> flag, pos, tmp, off, tmp2;
+    DevBuf<double> sc, f1, f2, part;
+    DevBuf<unsigned long long> cnt;
+    sorted.alloc((size_t)n_d);
+    flag.alloc((size_t)n_d + 1);
+    pos.alloc((size_t)n_d + 1);
+    tmp.alloc((size_t)scan_tmp_len(n_d + 1));
+    sdets.alloc((size_t)n_d * KW);
+    sc.alloc((size_t)n_d);
+    f1.alloc((size_t)n_d);
+    f2.alloc((size_t)n_d);
+    cnt.alloc((size_t)n_d + 1);
+    off.alloc((size_t)n_d + 1);
+    tmp2.alloc((size_t)scan_tmp_len(n_d + 1));
+    part.alloc((size_t)2 * rblocks);
+    std::vector<double> hp(2 * rblocks);
+    const int gb = (int)std::min<int64_t>(ceil_div(n_d, SEL_THREADS), (int64_t)c->n_sm * 16);
+    for (int smp = 0; smp < n_samples; smp++) {
+        CUDA_TRY(cudaMemcpyAsync(sorted.p, draws + (int64_t)smp * n_d, sizeof(int64_t) * n_d,
+                                 cudaMemcpyDeviceToDevice, st));
+        radix_sort<1>(sorted.p, vdummy.p, n_d, c->sw, st);
+        k_run_heads<<<gb, SEL_THREADS, 0, st>>>(sorted.p, n_d, flag.p);
+        exclusive_scan<int64_t>(flag.p, pos.p, n_d, tmp.p, st);
+        int64_t n_dist = 0;
+        CUDA_TRY(cudaMemcpyAsync(&n_dist, pos.p + n_d, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        k_sample_prep<W><<<gb, SEL_THREADS, 0, st>>>(sorted.p, n_d, pos.p, c->dets.p, cd, csum, sdets.p, sc.p, f1.p,
+                                                     f2.p);
+        KERNEL_CHECK();
+        g_kernel_launches += 2;
+        CUDA_TRY(cudaStreamSynchronize(st));
+        SelArgs S{};
+        S.n_det = n_dist;
+        S.dets = sdets.p;
+        S.k = 1;
+        S.c = sc.p;
+        S.eps1 = eps2;
+        S.n = c->n_orb;
+        S.na = c->n_alpha;
+        S.nb = c->n_beta;
+        S.ss_off = c->hb_same.off.p;
+        S.ss_rs = c->hb_same.rs.p;
+        S.ss_v = c->hb_same.val.p;
+        S.ss_kf = c->hb_same.kf.p;
+        S.os_off = c->hb_opp.off.p;
+        S.os_rs = c->hb_opp.rs.p;
+        S.os_v = c->hb_opp.val.p;
+        S.os_kf = c->hb_opp.kf.p;
+        S.nbatch = 1;
+        S.f1 = f1.p;
+        S.f2 = f2.p;
+        S.cnt = cnt.p;
+        k_select<W, false, true><<<blocks, SEL_THREADS, 0, st>>>(S, I);
+        KERNEL_CHECK();
+        exclusive_scan<int64_t>(reinterpret_cast<const int64_t *>(cnt.p), off.p, n_dist, tmp2.p, st);
+        int64_t total = 0;
+        CUDA_TRY(cudaMemcpyAsync(&total, off.p + n_dist, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+        g_kernel_launches += 1;
+        const double norm = 1.0 / ((double)n_d * (double)(n_d - 1));
+        if (total == 0) {
+            out[2 * smp] = 0.0;
+            out[2 * smp + 1] = 0.0;
+            continue;
+        }
+        if (total > 0xFFFFFFFFll) throw ShciError{SHCI_ERR_INVALID, "too many terms in one sample: raise eps2"};
+        DevBuf<uint64_t> cand;
+        DevBuf<double> t1, t2, mg;
+        DevBuf<uint32_t> idx;
+        cand.alloc((size_t)total * KW);
+        t1.alloc((size_t)total);
+        t2.alloc((size_t)total);
+        mg.alloc((size_t)total);
+        idx.alloc((size_t)total);
+        S.off = off.p;
+        S.out = cand.p;
+        S.terms = t1.p;
+        S.terms2 = t2.p;
+        S.mags = mg.p;
+        k_select<W, true, true><<<blocks, SEL_THREADS, 0, st>>>(S, I);
+        KERNEL_CHECK();
+        const int gt = (int)std::min<int64_t>(ceil_div(total, SEL_THREADS), (int64_t)c->n_sm * 16);
+        k_iota<<<gt, SEL_THREADS, 0, st>>>(idx.p, total);
+        KERNEL_CHECK();
+        radix_sort<KW>(cand.p, idx.p, total, c->sw, st);
+        k_pts_reduce<W><<<rblocks, SEL_THREADS, 0, st>>>(cand.p, idx.p, t1.p, t2.p, mg.p, total, vs.p, n, I, e_var,
+                                                         eps2_d, part.p);
+        KERNEL_CHECK();
+        g_kernel_launches += 3;
+        CUDA_TRY(cudaMemcpyAsync(hp.data(), part.p, sizeof(double) * 2 * rblocks, cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+        double a0 = 0.0, a1 = 0.0;
+        for (int x = 0; x < rblocks; x++) {
+            a0 += hp[2 * x];
+            a1 += hp[2 * x + 1];
+        }
+        out[2 * smp] = a0 * norm;
+        out[2 * smp + 1] = a1 * norm;
+    }
+}
+
+static void ensure_lists(shci_ctx *c) {
+    if (!c->hb_valid) {
+        build_hb_list(c, 1, c->hb_same);
+        build_hb_list(c, 0, c->hb_opp);
+        c->hb_valid = true;
+    }
+}
+
+void pt2_samples(shci_ctx *c, const double *coef, double e_var, double eps2, double eps2_d, int64_t n_d,
+                 int n_samples, const int64_t *draws, double *out, int mem) {
+    if (!c->built) throw ShciError{SHCI_ERR_STATE, "build the connectivity first"};
+    if (!(eps2 > 0.0) || !std::isfinite(eps2) || !(eps2_d >= eps2) || !std::isfinite(eps2_d))
+        throw ShciError{SHCI_ERR_INVALID, "need 0 < eps2 <= eps2_d, finite"};
+    if (!std::isfinite(e_var)) throw ShciError{SHCI_ERR_INVALID, "e_var must be finite"};
+    if (n_d < 2 || n_samples < 1 || !coef || !draws || !out) throw ShciError{SHCI_ERR_INVALID, "bad sample arguments"};
+    if (mem != SHCI_MEM_HOST && mem != SHCI_MEM_DEVICE) throw ShciError{SHCI_ERR_INVALID, "unknown mem_space"};
+    if (c->n_orb > 128) throw ShciError{SHCI_ERR_INVALID, "up to 128 orbitals"};
+    cudaStream_t st = c->st;
+    ensure_lists(c);
+    const int64_t n = c->n_det;
+    const double *cd = coef;
+    const int64_t *dd = draws;
+    DevBuf<double> cbuf;
+    DevBuf<int64_t> dbuf;
+    if (mem == SHCI_MEM_HOST) {
+        cbuf.alloc((size_t)n);
+        CUDA_TRY(cudaMemcpyAsync(cbuf.p, coef, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+        cd = cbuf.p;
+        dbuf.alloc((size_t)n_samples * n_d);
+        CUDA_TRY(cudaMemcpyAsync(dbuf.p, draws, sizeof(int64_t) * n_samples * n_d, cudaMemcpyHostToDevice, st));
+        dd = dbuf.p;
+    }
+    // every draw must index a determinant of V with a nonzero coefficient
+    {
+        std::vector<int64_t> hd((size_t)n_samples * n_d);
+        std::vector<double> hc((size_t)n);
+        CUDA_TRY(cudaMemcpyAsync(hd.data(), dd, sizeof(int64_t) * hd.size(), cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaMemcpyAsync(hc.data(), cd, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+        for (int64_t v : hd)
+            if (v < 0 || v >= n || hc[(size_t)v] == 0.0)
+                throw ShciError{SHCI_ERR_INVALID, "a draw is out of range or has a zero coefficient"};
+    }
+    std::vector<double> res((size_t)2 * n_samples);
+    if (c->W == 1) pt2_samples_w<1>(c, cd, e_var, eps2, eps2_d, n_d, n_samples, dd, res.data());
+    else pt2_samples_w<2>(c, cd, e_var, eps2, eps2_d, n_d, n_samples, dd, res.data());
+    for (size_t e = 0; e < res.size(); e++) out[e] = res[e];
+}
+
+void alias_draw(shci_ctx *c, const double *coef, int64_t n_draws, uint64_t seed, int64_t *out, int mem) {
+    if (!c->built) throw ShciError{SHCI_ERR_STATE, "build the connectivity first"};
+    if (n_draws < 0 || !coef || (n_draws > 0 && !out)) throw ShciError{SHCI_ERR_INVALID, "bad draw arguments"};
+    if (mem != SHCI_MEM_HOST && mem != SHCI_MEM_DEVICE) throw ShciError{SHCI_ERR_INVALID, "unknown mem_space"};
+    cudaStream_t st = c->st;
+    const int64_t n = c->n_det;
+    if (n > 0xFFFFFFFFll) throw ShciError{SHCI_ERR_INVALID, "too many determinants for the sampler"};
+    const double *cd = coef;
+    DevBuf<double> cbuf;
+    if (mem == SHCI_MEM_HOST) {
+        cbuf.alloc((size_t)n);
+        CUDA_TRY(cudaMemcpyAsync(cbuf.p, coef, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+        cd = cbuf.p;
+    }
+    const double csum = abs_sum(c, cd, n);
+    if (!(csum > 0.0)) throw ShciError{SHCI_ERR_INVALID, "all coefficients are zero"};
+    DevBuf<double> prob, q, sum;
+    DevBuf<int64_t> alias, small, large, obuf;
+    prob.alloc((size_t)n);
+    q.alloc((size_t)n);
+    sum.alloc(1);
+    alias.alloc((size_t)n);
+    small.alloc((size_t)n);
+    large.alloc((size_t)n);
+    CUDA_TRY(cudaMemcpyAsync(sum.p, &csum, sizeof(double), cudaMemcpyHostToDevice, st));
+    k_alias_table<<<1, 32, 0, st>>>(cd, n, sum.p, prob.p, alias.p, q.p, small.p, large.p);
+    KERNEL_CHECK();
+    g_kernel_launches += 1;
+    if (n_draws == 0) return;
+    int64_t *o = out;
+    if (mem == SHCI_MEM_HOST) {
+        obuf.alloc((size_t)n_draws);
+        o = obuf.p;
+    }
+    const int gb = (int)std::min<int64_t>(ceil_div(n_draws, SEL_THREADS), (int64_t)c->n_sm * 16);
+    k_alias_draw<<<gb, SEL_THREADS, 0, st>>>(prob.p, alias.p, n, seed, n_draws, o);
+    KERNEL_CHECK();
+    g_kernel_launches += 1;
+    if (mem == SHCI_MEM_HOST)
+        CUDA_TRY(cudaMemcpyAsync(out, o, sizeof(int64_t) * n_draws, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+}
+
 void pt2(shci_ctx *c, const double *coef, double e_var, double eps2, int nbatch, double *e2, int64_t *n_pert,
          int mem) {
     if (!c->built) throw ShciError{SHCI_ERR_STATE, "build the connectivity before the second-order energy"};
@@ -625,11 +1028,7 @@ void pt2(shci_ctx *c, const double *coef, double e_var, double eps2, int nbatch,
     CUDA_TRY(cudaEventCreate(&e0));
     CUDA_TRY(cudaEventCreate(&e1));
     CUDA_TRY(cudaEventRecord(e0, st));
-    if (!c->hb_valid) {
-        build_hb_list(c, 1, c->hb_same);
-        build_hb_list(c, 0, c->hb_opp);
-        c->hb_valid = true;
-    }
+    ensure_lists(c);
     const double *cd = coef;
     DevBuf<double> cbuf;
     if (mem == SHCI_MEM_HOST) {
@@ -652,6 +1051,38 @@ void pt2(shci_ctx *c, const double *coef, double e_var, double eps2, int nbatch,
     c->stats.pt2_ms = ms;
     c->stats.pt2_batches = used;
     c->stats.pt2_terms = cands;
+}
+
+void pt2_semistochastic(shci_ctx *c, const double *coef, double e_var, double eps2, double eps2_d, int64_t n_d,
+                        int n_samples, uint64_t seed, double *e2, double *e2_err, int mem) {
+    if (!e2) throw ShciError{SHCI_ERR_INVALID, "null pointer"};
+    if (n_samples < 1 || n_d < 2) throw ShciError{SHCI_ERR_INVALID, "need n_samples >= 1 and n_d >= 2"};
+    // deterministic part at eps2_d (Eq. 8)
+    double e2d = 0.0;
+    pt2(c, coef, e_var, eps2_d, 0, &e2d, nullptr, mem);
+    // stochastic part: the same samples at eps2 and at eps2_d (Eq. 9)
+    DevBuf<int64_t> draws;
+    draws.alloc((size_t)n_samples * n_d);
+    const double *cd = coef;
+    DevBuf<double> cbuf;
+    if (mem == SHCI_MEM_HOST) {
+        cbuf.alloc((size_t)c->n_det);
+        CUDA_TRY(cudaMemcpyAsync(cbuf.p, coef, sizeof(double) * c->n_det, cudaMemcpyHostToDevice, c->st));
+        cd = cbuf.p;
+    }
+    alias_draw(c, cd, (int64_t)n_samples * n_d, seed, draws.p, SHCI_MEM_DEVICE);
+    std::vector<double> v((size_t)2 * n_samples);
+    pt2_samples(c, cd, e_var, eps2, eps2_d, n_d, n_samples, draws.p, v.data(), SHCI_MEM_DEVICE);
+    double mean = 0.0;
+    for (int sm = 0; sm < n_samples; sm++) mean += v[2 * sm] - v[2 * sm + 1];
+    mean /= n_samples;
+    double var = 0.0;
+    for (int sm = 0; sm < n_samples; sm++) {
+        const double d = v[2 * sm] - v[2 * sm + 1] - mean;
+        var += d * d;
+    }
+    *e2 = e2d + mean;
+    if (e2_err) *e2_err = n_samples > 1 ? std::sqrt(var / (n_samples - 1) / n_samples) : 0.0;
 }
 
 void select_dets(shci_ctx *c, int k, const double *coef, double eps1, int64_t cap, uint64_t *out, int64_t *n_out,

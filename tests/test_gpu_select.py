@@ -166,3 +166,80 @@ def test_pt2_two_word_strings(P, oracle_mod):
     e, vecs, it = B.davidson(1, tol=1e-10)
     _pt2_check(P, O, B, dets, vecs[0], float(e[0]), 3e-3)
     B.close()
+
+
+# ---------------------------------------------------------------- stochastic and semistochastic PT2 (Eqs. 8-10)
+
+def _draws(c, n_samples, n_d, seed):
+    """Samples of V drawn with p_i proportional to |c_i| (Eq. 10) by a seeded
+    generator: the random numbers are an input shared by both sides."""
+    p = np.abs(c) / np.abs(c).sum()
+    return np.random.default_rng(seed).choice(c.size, size=(n_samples, n_d), p=p).astype(np.int64)
+
+
+def _samples_check(P, O, B, dets, c, e_var, eps2, eps2_d, draws):
+    got = P.shci_pt2_samples(B.ctx.handle, G.dev(c), e_var, eps2, eps2_d, G.dev(draws))
+    for s in range(draws.shape[0]):
+        refs = [O.pt2_sample(dets, c, e_var, eps2 * f, eps2_d * f, draws[s]) for f in (1 - 1e-9, 1 + 1e-9)]
+        ok = [all(abs(got[s, j] - r[j]) <= 1e-10 * max(1e-8, abs(r[j])) for j in (0, 1)) for r in refs]
+        assert any(ok), (s, got[s], refs)
+    return got
+
+
+def test_pt2_samples_match_oracle(P, oracle_mod):
+    n, na, nb = 8, 3, 2
+    h, eri, ec = S.integrals(n, 10, 4242)
+    fci = S.fci_dets(n, na, nb)
+    rng = np.random.default_rng(11)
+    v = fci[np.sort(rng.choice(fci.shape[0], 30, replace=False))]
+    O = oracle_mod.System(h, eri, ec)
+    c = rng.standard_normal(v.shape[0])
+    c /= np.linalg.norm(c)
+    e_var = float(c @ O.dense_h(v) @ c)
+    B = G.Built(P, h, eri, ec, v, na, nb)
+    _samples_check(P, O, B, v, c, e_var, 1e-4, 1e-2, _draws(c, 4, 12, 1))
+    B.close()
+    cfg, h, eri, ec, dets = G.system("sel_24o_6a6b_1m", 600)
+    O = oracle_mod.System(h, eri, ec)
+    B = G.Built(P, h, eri, ec, dets, 6, 6)
+    e, vecs, it = B.davidson(1, tol=1e-10)
+    _samples_check(P, O, B, dets, vecs[0], float(e[0]), 1e-5, 1e-4, _draws(vecs[0], 2, 50, 2))
+    B.close()
+
+
+def test_alias_draws_follow_the_coefficients(P):
+    """p_i = |c_i| / sum |c| (Eq. 10): frequencies of 4e6 draws pass a chi-square
+    test at a 1e-6 false-alarm level; zero coefficients are never drawn; the
+    draws depend only on the seed."""
+    from scipy import stats
+    h, eri, ec = S.integrals(8, 10, 4242)
+    fci = S.fci_dets(8, 3, 2)[:50]
+    B = G.Built(P, h, eri, ec, fci, 3, 2)
+    c = np.random.default_rng(3).standard_normal(50)
+    c[[4, 17, 33]] = 0.0
+    n_draws = 4_000_000
+    d = P.shci_alias_draw(B.ctx.handle, G.dev(c), n_draws, 12345).cpu().numpy()
+    counts = np.bincount(d, minlength=50)
+    assert counts[[4, 17, 33]].sum() == 0 and d.min() >= 0 and d.max() < 50
+    p = np.abs(c) / np.abs(c).sum()
+    nz = p > 0
+    chi2 = float(np.sum((counts[nz] - n_draws * p[nz]) ** 2 / (n_draws * p[nz])))
+    assert chi2 < stats.chi2.ppf(1 - 1e-6, nz.sum() - 1)
+    d2 = P.shci_alias_draw(B.ctx.handle, np.ascontiguousarray(c), 1000, 12345)
+    np.testing.assert_array_equal(d2, d[:1000])
+    B.close()
+
+
+def test_semistochastic_pt2(P, oracle_mod):
+    """eps2_d = eps2 is the deterministic energy exactly; with eps2_d > eps2 the
+    estimate lies within 6 standard errors of the deterministic energy at eps2."""
+    cfg, h, eri, ec, dets = G.system("sel_24o_6a6b_1m", 600)
+    B = G.Built(P, h, eri, ec, dets, 6, 6)
+    e, vecs, it = B.davidson(1, tol=1e-10)
+    c = G.dev(vecs[0])
+    det, _ = P.shci_pt2(B.ctx.handle, c, float(e[0]), 1e-5)
+    same, err0 = P.shci_pt2_semistochastic(B.ctx.handle, c, float(e[0]), 1e-5, 1e-5, 100, 4, 7)
+    assert abs(same - det) <= 1e-13 * abs(det) and err0 == 0.0
+    est, err = P.shci_pt2_semistochastic(B.ctx.handle, c, float(e[0]), 1e-5, 1e-3, 200, 64, 7)
+    assert err > 0.0 and abs(est - det) <= 6.0 * err + 1e-12
+    B.close()
