@@ -575,7 +575,7 @@ def run_adjoint(args):
 
 
 def run_select(args):
-    """Heat-bath selection (Sec. II, Eq. 2) from the bench's 1e6-determinant
+    """Heat-bath selection (Sec. II.A, Eq. 2) from the bench's 1e6-determinant
     space with its converged 2-root coefficients: GPU time per selection, the
     candidates and new determinants, and the oracle's brute force on a sample
     of determinants of V on the host cores."""
@@ -647,6 +647,15 @@ def run_select(args):
                 "dE2_semistochastic": est, "std_error": err, "seconds": t_semi,
                 "dE2_deterministic": ref, "deterministic_seconds": t_det, "deterministic_batches": st["pt2_batches"],
                 "deterministic_terms": st["pt2_terms"], "n_pert": npert}
+        # the 3-step scheme (Sec. IV, Eq. 11) for the same eps2
+        t = time.perf_counter()
+        r3 = P.shci_pt2_3step(H, vecs[0].contiguous(), float(e0[0]), eps2, 3 * eps2, eps2_d, 1e-4, 16, 32,
+                              args.semi_nd, args.semi_samples, 2025)
+        torch.cuda.synchronize()
+        r3["seconds"] = time.perf_counter() - t
+        r3.update({"eps2": eps2, "eps2_psto": 3 * eps2, "eps2_dtm": eps2_d, "target_error": 1e-4,
+                   "batches_psto": 16, "batches_sto": 32})
+        semi["three_step"] = r3
     # the same screened energy on a 600-determinant space of the same shape: GPU and oracle side by side
     h6, eri6, ec6, d6 = S.make_system(cfg, 600)
     c6 = P.Context(0, torch.cuda.current_stream())

@@ -14,7 +14,7 @@
  * --------------------------------
  * - Determinants: uint64 rows of 2*W words, W = ceil(n_orb / 64): the alpha
  *   string's W words, then the beta string's W words.  Spatial orbital n of a
- *   string is bit (n & 63) of word (n >> 6) (Sec. IV.A).  n_orb <= 128.
+ *   string is bit (n & 63) of word (n >> 6) (Sec. V.A).  n_orb <= 128.
  * - Fermionic sign convention: |D> = prod_{alpha occupied, ascending} a+ *
  *   prod_{beta occupied, ascending} a+ |0>.  Eigenvalues and |H_ij| do not
  *   depend on this choice; signed results are self-consistent under it.
@@ -88,7 +88,7 @@ int shci_load_integrals(shci_ctx *ctx, int n_orb, double e_core, const double *h
 
 /* Build the connectivity of V = dets[0 .. n_det) (Sec. III): helper lists
  * (unique alpha/beta strings, per-string determinant lists, alpha-single
- * lists; Table I), the cached diagonal H_ii (Sec. IV.B) and, in SHCI_STORED
+ * lists; Table I), the cached diagonal H_ii (Sec. V.B) and, in SHCI_STORED
  * mode, every off-diagonal H_ij != structural zero in both triangles.
  * dets: [n_det][2W] uint64 as above, every alpha string with n_alpha bits and
  * every beta string with n_beta bits below n_orb; determinants must be
@@ -117,7 +117,7 @@ int shci_get_pairs(shci_ctx *ctx, int64_t cap, int64_t *i_out, int64_t *j_out,
  * SHCI_ERR_STATE unless built in SHCI_STORED mode. */
 int shci_get_row(shci_ctx *ctx, int64_t row, int64_t cap, int64_t *cols, double *vals, int64_t *n_out);
 
-/* sigma = H c for k vectors (k in [1, 8]), c and sigma [k][n_det] (Sec. IV.B:
+/* sigma = H c for k vectors (k in [1, 8]), c and sigma [k][n_det] (Sec. V.B:
  * the matrix-vector product of the Davidson step).  Uses the stored H, or the
  * on-the-fly product in SHCI_ON_THE_FLY mode.  c and sigma must not overlap. */
 int shci_sigma(shci_ctx *ctx, int k, const double *c, double *sigma, int mem_space);
@@ -164,7 +164,7 @@ int shci_davidson(shci_ctx *ctx, int k_roots, double tol, int max_iter, const do
  * cap < 0 or n_out is NULL. */
 int shci_davidson_history(shci_ctx *ctx, int cap, double *theta, double *rnorm, double *t_s, int *n_out);
 
-/* Heat-bath selection (Sec. II, Eq. 2): the determinants D_a outside V for
+/* Heat-bath selection (Sec. II.A, Eq. 2): the determinants D_a outside V for
  * which some D_i in V has |H_ai| * |c_i| >= eps1, |c_i| being the largest
  * |coefficient| of D_i over the k_roots vectors c[k_roots][n_det] (mem_space).
  * Double excitations come from per-orbital-pair lists of |H| sorted in
@@ -214,9 +214,40 @@ int shci_alias_draw(shci_ctx *ctx, const double *c, int64_t n_draws, uint64_t se
  * value is sum_a (S1^2 + S2) / (E_V - H_aa) / (n_d (n_d - 1)).  out (host,
  * [n_samples][2]) receives the value at eps = eps2 and at eps = eps2_d
  * (0 < eps2 <= eps2_d).  Every draw must index a determinant with c_i != 0;
- * n_d >= 2. */
+ * n_d >= 2.  With n_batches > 1 the sum over a is restricted to the hash
+ * batch batches[s] (host [n_samples], each in [0, n_batches)) of sample s,
+ * the partition of shci_pt2: the batches' values add up to the unrestricted
+ * value. */
 int shci_pt2_samples(shci_ctx *ctx, const double *c, double e_var, double eps2, double eps2_d, int64_t n_d,
-                     int n_samples, const int64_t *draws, double *out, int mem_space);
+                     int n_samples, const int64_t *draws, double *out, int mem_space, int n_batches,
+                     const int *batches);
+
+/* The 3-step perturbation scheme (Sec. IV, Eq. 11):
+ *   dE2(eps2) = [dE2^sto(eps2) - dE2^sto(eps2_psto)]
+ *             + [dE2^psto(eps2_psto) - dE2^psto(eps2_dtm)] + dE2^dtm(eps2_dtm).
+ * dtm: shci_pt2 at eps2_dtm.  psto: all of V at eps2_psto, the perturbative
+ * determinants in n_batches_psto (>= 16) hash batches taken in order; per
+ * determinant the correction (num_psto^2 - num_dtm^2) / (E_V - H_aa); after
+ * each batch the mean and variance of the corrections seen estimate the sum
+ * over all determinants (their number extrapolated from the batches done) and
+ * the standard deviation of the part not yet evaluated; the loop stops when
+ * that is below 0.4 target_error (target 0: every batch, exact).  sto:
+ * n_samples samples of n_d alias draws (shci_alias_draw with seed), each with
+ * one hash batch out of n_batches_sto drawn from the same counter stream
+ * (counters after the determinant draws), value times n_batches_sto; the mean
+ * and standard error of the differences eps2 - eps2_psto.  Needs
+ * 0 < eps2 <= eps2_psto <= eps2_dtm (equal thresholds skip a step). */
+typedef struct {
+    double e2, e2_err;         /* total and its standard error */
+    double dtm;                /* deterministic part */
+    double psto, psto_err;     /* pseudo-stochastic difference and its deviation */
+    double sto, sto_err;       /* stochastic difference and its standard error */
+    int psto_batches;          /* pseudo-stochastic batches evaluated */
+} shci_pt2_3step_t;
+
+int shci_pt2_3step(shci_ctx *ctx, const double *c, double e_var, double eps2, double eps2_psto, double eps2_dtm,
+                   double target_error, int n_batches_psto, int n_batches_sto, int64_t n_d, int n_samples,
+                   uint64_t seed, shci_pt2_3step_t *out, int mem_space);
 
 /* Semistochastic second-order energy (Sec. II.B, Eq. 8): the deterministic
  * energy at eps2_d (shci_pt2) plus the mean over n_samples samples of n_d

@@ -16,7 +16,7 @@ What it computes, and where the paper defines it:
 * ``pairs_generate`` -- brute force (b) of Sec. III: every single and double
   excitation of each determinant looked up in V.
 * ``sigma_rows`` / ``sigma_pairs`` -- sigma = H c (the matrix-vector product of
-  the Davidson step, Sec. IV.B), long-double accumulation.
+  the Davidson step, Sec. V.B), long-double accumulation.
 * ``lowest_eigenpairs`` -- the lowest roots of H on V (Sec. II.A): a dense
   symmetric eigensolver for small spaces, else a plain diagonally
   preconditioned Davidson iteration (Sec. II.A) on a sparse matrix the oracle
@@ -178,7 +178,7 @@ class System:
 
     # ---------------------------------------------------------- selection
     def select(self, dets, c, eps1, with_best=False):
-        """Determinants outside V selected by the criterion of Sec. II (Eq. 2):
+        """Determinants outside V selected by the criterion of Sec. II.A (Eq. 2):
         some D_i in V has |H_ai| * max_l |c_l[i]| >= eps1.  Brute force over
         every single and double excitation; rows sorted ascending with the
         last stored word most significant, no repeats.  with_best: also the

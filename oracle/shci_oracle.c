@@ -9,7 +9,7 @@
  *
  * Conventions (readings of the paper, which does not print them):
  *   - Determinants are bit-packed uint64 words, orbital n at bit (n & 63) of
- *     word (n >> 6) (Sec. IV.A); a determinant row is W alpha words then W
+ *     word (n >> 6) (Sec. V.A); a determinant row is W alpha words then W
  *     beta words.
  *   - Spin-orbital so in [0, 2n): so < n is alpha orbital so, so >= n is beta
  *     orbital so - n.  |D> = prod_{so ascending, occupied} a+_so |0>, i.e. all
@@ -569,7 +569,7 @@ static int cmp_det_desc_words(const void *a, const void *b)
 }
 
 /*
- * The selection criterion of Sec. II (Eq. 2): a determinant D_a outside V is
+ * The selection criterion of Sec. II.A (Eq. 2): a determinant D_a outside V is
  * selected when some D_i in V has |H_ai c_i| >= eps1, c_i taken as the largest
  * |coefficient| of D_i over the k given vectors c[k][n_det].  Brute force:
  * every single and double excitation of every D_i is generated, its H_ai

@@ -38,7 +38,7 @@ EXPORTED = [
     "shci_get_diag", "shci_get_pairs", "shci_get_row", "shci_sigma", "shci_sigma_noalloc", "shci_energy_backward",
     "shci_batch_create", "shci_batch_davidson", "shci_batch_get_stats", "shci_batch_destroy", "shci_davidson",
     "shci_davidson_history", "shci_select", "shci_pt2", "shci_alias_draw", "shci_pt2_samples",
-    "shci_pt2_semistochastic", "shci_get_stats", "shci_set_timing",
+    "shci_pt2_semistochastic", "shci_pt2_3step", "shci_get_stats", "shci_set_timing",
 ]
 
 
@@ -57,6 +57,14 @@ class shci_stats_t(ctypes.Structure):
         ("mode", ctypes.c_int), ("n_words", ctypes.c_int), ("davidson_phase_ms", ctypes.c_double * 8),
         ("select_ms", ctypes.c_double), ("select_candidates", ctypes.c_int64),
         ("pt2_ms", ctypes.c_double), ("pt2_batches", ctypes.c_int), ("pt2_terms", ctypes.c_int64),
+    ]
+
+
+class shci_pt2_3step_t(ctypes.Structure):
+    _fields_ = [
+        ("e2", ctypes.c_double), ("e2_err", ctypes.c_double), ("dtm", ctypes.c_double), ("psto", ctypes.c_double),
+        ("psto_err", ctypes.c_double), ("sto", ctypes.c_double), ("sto_err", ctypes.c_double),
+        ("psto_batches", ctypes.c_int),
     ]
 
 
@@ -112,7 +120,9 @@ def load_library(path: str = LIB_PATH):
         "shci_select": (i32, [vp, i32, vp, f64, i64, vp, ctypes.POINTER(i64), i32]),
         "shci_pt2": (i32, [vp, vp, f64, f64, i32, ctypes.POINTER(f64), ctypes.POINTER(i64), i32]),
         "shci_alias_draw": (i32, [vp, vp, i64, ctypes.c_uint64, vp, i32]),
-        "shci_pt2_samples": (i32, [vp, vp, f64, f64, f64, i64, i32, vp, vp, i32]),
+        "shci_pt2_samples": (i32, [vp, vp, f64, f64, f64, i64, i32, vp, vp, i32, i32, vp]),
+        "shci_pt2_3step": (i32, [vp, vp, f64, f64, f64, f64, f64, i32, i32, i64, i32, ctypes.c_uint64,
+                                 ctypes.POINTER(shci_pt2_3step_t), i32]),
         "shci_pt2_semistochastic": (i32, [vp, vp, f64, f64, f64, i64, i32, ctypes.c_uint64, ctypes.POINTER(f64),
                                           ctypes.POINTER(f64), i32]),
         "shci_get_stats": (i32, [vp, ctypes.POINTER(shci_stats_t)]),
@@ -325,18 +335,32 @@ def shci_alias_draw(ctx, c, n_draws, seed):
     return out
 
 
-def shci_pt2_samples(ctx, c, e_var, eps2, eps2_d, draws):
+def shci_pt2_samples(ctx, c, e_var, eps2, eps2_d, draws, n_batches=1, batches=None):
     """[n_samples, 2]: the stochastic second-order energy of each sample (rows
-    of draws, [n_samples, n_d]) at eps2 and at eps2_d."""
+    of draws, [n_samples, n_d]) at eps2 and at eps2_d; with n_batches > 1 only
+    the hash batch batches[s] of each sample."""
     pc, mc, kc = _ptr(c, np.float64)
     pd, md, kd = _ptr(draws, np.int64)
     if mc != md:
         raise ValueError("c and draws must live in the same memory space")
     n_samples, n_d = int(draws.shape[0]), int(draws.shape[1])
     out = np.empty((n_samples, 2))
+    bt = None if batches is None else np.ascontiguousarray(batches, np.int32)
     _check(ctx, load_library().shci_pt2_samples(ctx, pc, float(e_var), float(eps2), float(eps2_d), n_d, n_samples,
-                                                pd, out.ctypes.data, mc))
+                                                pd, out.ctypes.data, mc, int(n_batches),
+                                                None if bt is None else bt.ctypes.data))
     return out
+
+
+def shci_pt2_3step(ctx, c, e_var, eps2, eps2_psto, eps2_dtm, target_error, n_batches_psto, n_batches_sto, n_d,
+                   n_samples, seed):
+    """The 3-step perturbation scheme: dict of the total, its error and the parts."""
+    pc, mc, kc = _ptr(c, np.float64)
+    o = shci_pt2_3step_t()
+    _check(ctx, load_library().shci_pt2_3step(ctx, pc, float(e_var), float(eps2), float(eps2_psto), float(eps2_dtm),
+                                              float(target_error), int(n_batches_psto), int(n_batches_sto), int(n_d),
+                                              int(n_samples), int(seed) & ((1 << 64) - 1), ctypes.byref(o), mc))
+    return {name: getattr(o, name) for name, _ in shci_pt2_3step_t._fields_}
 
 
 def shci_pt2_semistochastic(ctx, c, e_var, eps2, eps2_d, n_d, n_samples, seed):

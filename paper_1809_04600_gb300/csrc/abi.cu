@@ -239,9 +239,21 @@ int shci_alias_draw(shci_ctx *c, const double *coef, int64_t n_draws, uint64_t s
 }
 
 int shci_pt2_samples(shci_ctx *c, const double *coef, double e_var, double eps2, double eps2_d, int64_t n_d,
-                     int n_samples, const int64_t *draws, double *out, int mem) {
+                     int n_samples, const int64_t *draws, double *out, int mem, int n_batches, const int *batches) {
     return guarded(c, [&] {
-        shci::pt2_samples(c, coef, e_var, eps2, eps2_d, n_d, n_samples, draws, out, mem);
+        if (n_batches > 1 && !batches) throw ShciError{SHCI_ERR_INVALID, "batches must be given for n_batches > 1"};
+        shci::pt2_samples(c, coef, e_var, eps2, eps2_d, n_d, n_samples, draws, out, mem, n_batches < 1 ? 1 : n_batches,
+                          n_batches > 1 ? batches : nullptr);
+        return SHCI_OK;
+    });
+}
+
+int shci_pt2_3step(shci_ctx *c, const double *coef, double e_var, double eps2, double eps2_psto, double eps2_dtm,
+                   double target, int nb_psto, int nb_sto, int64_t n_d, int n_samples, uint64_t seed,
+                   shci_pt2_3step_t *out, int mem) {
+    return guarded(c, [&] {
+        shci::pt2_3step(c, coef, e_var, eps2, eps2_psto, eps2_dtm, target, nb_psto, nb_sto, n_d, n_samples, seed, out,
+                        mem);
         return SHCI_OK;
     });
 }

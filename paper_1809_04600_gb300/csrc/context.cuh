@@ -125,7 +125,10 @@ void pt2(shci_ctx *c, const double *coef, double e_var, double eps2, int nbatch,
          int mem);
 void alias_draw(shci_ctx *c, const double *coef, int64_t n_draws, uint64_t seed, int64_t *out, int mem);
 void pt2_samples(shci_ctx *c, const double *coef, double e_var, double eps2, double eps2_d, int64_t n_d,
-                 int n_samples, const int64_t *draws, double *out, int mem);
+                 int n_samples, const int64_t *draws, double *out, int mem, int nbatch, const int *batch_of_sample);
+void pt2_3step(shci_ctx *c, const double *coef, double e_var, double eps2, double eps2_psto, double eps2_dtm,
+               double target, int nbatch_psto, int nbatch_sto, int64_t n_d, int n_samples, uint64_t seed,
+               shci_pt2_3step_t *out, int mem);
 void pt2_semistochastic(shci_ctx *c, const double *coef, double e_var, double eps2, double eps2_d, int64_t n_d,
                         int n_samples, uint64_t seed, double *e2, double *e2_err, int mem);
 

@@ -1,5 +1,5 @@
 // Diagonally preconditioned Davidson for the lowest roots of H on V
-// (Sec. II.A; the cached diagonal of Sec. IV.B is the preconditioner).
+// (Sec. II.A; the cached diagonal of Sec. V.B is the preconditioner).
 //
 // Everything runs on the device in FP64: the block sigma product, the
 // projected matrix V^T H V, its eigen-decomposition (warm-started threshold

@@ -1,4 +1,4 @@
-// Heat-bath selection of new determinants (Sec. II, Eq. 2): D_a outside V is
+// Heat-bath selection of new determinants (Sec. II.A, Eq. 2): D_a outside V is
 // selected when some D_i in V has |H_ai c_i| >= eps1.
 //
 // Double excitations are found the way the paper describes: for every pair
@@ -228,6 +228,7 @@ __device__ __forceinline__ void sel_emit(const SelArgs &S, const DevInts &I, uns
             S.mags[pos] = fabs(hv) * fabs(ci);
         } else {
             S.terms[pos] = hv * ci;
+            if (S.mags) S.mags[pos] = fabs(hv) * fabs(ci);
         }
     }
 }
@@ -806,7 +807,7 @@ __global__ void __launch_bounds__(SEL_THREADS) k_pts_reduce(const uint64_t *__re
 
 template <int W>
 static void pt2_samples_w(shci_ctx *c, const double *cd, double e_var, double eps2, double eps2_d, int64_t n_d,
-                          int n_samples, const int64_t *draws, double *out) {
+                          int n_samples, const int64_t *draws, double *out, int nbatch, const int *batch_of_sample) {
     cudaStream_t st = c->st;
     constexpr int KW = 2 * W;
     const int64_t n = c->n_det;
@@ -869,7 +870,8 @@ static void pt2_samples_w(shci_ctx *c, const double *cd, double e_var, double ep
         S.os_rs = c->hb_opp.rs.p;
         S.os_v = c->hb_opp.val.p;
         S.os_kf = c->hb_opp.kf.p;
-        S.nbatch = 1;
+        S.nbatch = nbatch;
+        S.batch = batch_of_sample ? batch_of_sample[smp] : 0;
         S.f1 = f1.p;
         S.f2 = f2.p;
         S.cnt = cnt.p;
@@ -931,7 +933,12 @@ static void ensure_lists(shci_ctx *c) {
 }
 
 void pt2_samples(shci_ctx *c, const double *coef, double e_var, double eps2, double eps2_d, int64_t n_d,
-                 int n_samples, const int64_t *draws, double *out, int mem) {
+                 int n_samples, const int64_t *draws, double *out, int mem, int nbatch, const int *batch_of_sample) {
+    if (nbatch < 1 || nbatch > 1 << 20) throw ShciError{SHCI_ERR_INVALID, "n_batches must be in [1, 2^20]"};
+    if (batch_of_sample)
+        for (int sm = 0; sm < n_samples; sm++)
+            if (batch_of_sample[sm] < 0 || batch_of_sample[sm] >= nbatch)
+                throw ShciError{SHCI_ERR_INVALID, "batch index out of range"};
     if (!c->built) throw ShciError{SHCI_ERR_STATE, "build the connectivity first"};
     if (!(eps2 > 0.0) || !std::isfinite(eps2) || !(eps2_d >= eps2) || !std::isfinite(eps2_d))
         throw ShciError{SHCI_ERR_INVALID, "need 0 < eps2 <= eps2_d, finite"};
@@ -966,8 +973,8 @@ void pt2_samples(shci_ctx *c, const double *coef, double e_var, double eps2, dou
                 throw ShciError{SHCI_ERR_INVALID, "a draw is out of range or has a zero coefficient"};
     }
     std::vector<double> res((size_t)2 * n_samples);
-    if (c->W == 1) pt2_samples_w<1>(c, cd, e_var, eps2, eps2_d, n_d, n_samples, dd, res.data());
-    else pt2_samples_w<2>(c, cd, e_var, eps2, eps2_d, n_d, n_samples, dd, res.data());
+    if (c->W == 1) pt2_samples_w<1>(c, cd, e_var, eps2, eps2_d, n_d, n_samples, dd, res.data(), nbatch, batch_of_sample);
+    else pt2_samples_w<2>(c, cd, e_var, eps2, eps2_d, n_d, n_samples, dd, res.data(), nbatch, batch_of_sample);
     for (size_t e = 0; e < res.size(); e++) out[e] = res[e];
 }
 
@@ -1053,6 +1060,254 @@ void pt2(shci_ctx *c, const double *coef, double e_var, double eps2, int nbatch,
     c->stats.pt2_terms = cands;
 }
 
+// pseudo-stochastic step: over the sorted terms of one batch at eps2_psto, for
+// each determinant a outside V the correction
+//   (num_psto^2 - num_dtm^2) / (E_V - H_aa),
+// num_dtm summing only the terms with |H_ai c_i| >= eps2_dtm; per-block sums of
+// the corrections, of their squares and the number of determinants
+template <int W>
+__global__ void __launch_bounds__(SEL_THREADS) k_psto_reduce(const uint64_t *__restrict__ cand,
+                                                            const uint32_t *__restrict__ idx,
+                                                            const double *__restrict__ t,
+                                                            const double *__restrict__ mag, int64_t total,
+                                                            const uint64_t *__restrict__ vs, int64_t nv, DevInts I,
+                                                            double e_var, double eps_dtm, double *__restrict__ part,
+                                                            unsigned long long *__restrict__ npart) {
+    constexpr int KW = 2 * W;
+    double acc = 0.0, acc2 = 0.0;
+    unsigned long long cnt = 0;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t *x = cand + e * KW;
+        if (e > 0 && cmp_words<KW>(cand + (e - 1) * KW, x) == 0) continue;
+        int64_t lo = 0, hi = nv;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (cmp_words<KW>(vs + mid * KW, x) < 0) lo = mid + 1;
+            else hi = mid;
+        }
+        if (lo < nv && cmp_words<KW>(vs + lo * KW, x) == 0) continue;
+        double na = 0.0, nd = 0.0;
+        for (int64_t f = e; f < total && cmp_words<KW>(cand + f * KW, x) == 0; f++) {
+            const uint32_t j = idx[f];
+            na += t[j];
+            if (mag[j] >= eps_dtm) nd += t[j];
+        }
+        Str<W> a, b;
+#pragma unroll
+        for (int k = 0; k < W; k++) {
+            a.w[k] = x[k];
+            b.w[k] = x[W + k];
+        }
+        const double corr = (na * na - nd * nd) / (e_var - hii<W>(I, a, b));
+        acc += corr;
+        acc2 += corr * corr;
+        cnt++;
+    }
+    __shared__ double red[2][SEL_THREADS / 32];
+    __shared__ unsigned long long redc[SEL_THREADS / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        acc2 += __shfl_xor_sync(0xffffffffu, acc2, o);
+        cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    }
+    if (lane == 0) {
+        red[0][w] = acc;
+        red[1][w] = acc2;
+        redc[w] = cnt;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s0 = 0.0, s1 = 0.0;
+        unsigned long long sc = 0;
+        for (int x = 0; x < SEL_THREADS / 32; x++) {
+            s0 += red[0][x];
+            s1 += red[1][x];
+            sc += redc[x];
+        }
+        part[2 * blockIdx.x] = s0;
+        part[2 * blockIdx.x + 1] = s1;
+        npart[blockIdx.x] = sc;
+    }
+}
+
+// Pseudo-stochastic step of the 3-step scheme: batches of the perturbative
+// determinants (hash partition, at least 16) in order; after each batch the
+// corrections seen so far give a mean and variance, the number of
+// perturbative determinants is extrapolated from the batches done, and the
+// loop stops when the standard deviation of the estimated sum of the
+// unevaluated ones is below 0.4 target (all batches: exact, zero deviation).
+template <int W>
+static void psto_w(shci_ctx *c, const double *cd, double e_var, double eps_psto, double eps_dtm, int nbatch,
+                   double target, double &est, double &err, int &done) {
+    cudaStream_t st = c->st;
+    constexpr int KW = 2 * W;
+    const int64_t n = c->n_det;
+    SelArgs S{};
+    S.n_det = n;
+    S.dets = c->dets.p;
+    S.k = 1;
+    S.c = cd;
+    S.eps1 = eps_psto;
+    S.n = c->n_orb;
+    S.na = c->n_alpha;
+    S.nb = c->n_beta;
+    S.ss_off = c->hb_same.off.p;
+    S.ss_rs = c->hb_same.rs.p;
+    S.ss_v = c->hb_same.val.p;
+    S.ss_kf = c->hb_same.kf.p;
+    S.os_off = c->hb_opp.off.p;
+    S.os_rs = c->hb_opp.rs.p;
+    S.os_v = c->hb_opp.val.p;
+    S.os_kf = c->hb_opp.kf.p;
+    S.nbatch = nbatch;
+    const DevInts I = dev_ints(c);
+    const int blocks = c->n_sm * (2048 / SEL_THREADS);
+    const int rblocks = c->n_sm * 4;
+    DevBuf<unsigned long long> cnt, npart;
+    DevBuf<int64_t> off, tmp;
+    DevBuf<double> part;
+    cnt.alloc((size_t)n + 1);
+    off.alloc((size_t)n + 1);
+    tmp.alloc((size_t)scan_tmp_len(n + 1));
+    part.alloc((size_t)2 * rblocks);
+    npart.alloc((size_t)rblocks);
+    S.cnt = cnt.p;
+    DevBuf<uint64_t> vs;
+    DevBuf<uint32_t> vdummy;
+    vs.alloc((size_t)n * KW);
+    vdummy.alloc((size_t)n);
+    CUDA_TRY(cudaMemcpyAsync(vs.p, c->dets.p, sizeof(uint64_t) * n * KW, cudaMemcpyDeviceToDevice, st));
+    radix_sort<KW>(vs.p, vdummy.p, n, c->sw, st);
+    std::vector<double> hp(2 * rblocks);
+    std::vector<unsigned long long> hn(rblocks);
+    double sum = 0.0, sum2 = 0.0;
+    int64_t count = 0;
+    est = 0.0;
+    err = 0.0;
+    done = 0;
+    for (int b = 0; b < nbatch; b++) {
+        S.batch = b;
+        k_select<W, false, true><<<blocks, SEL_THREADS, 0, st>>>(S, I);
+        KERNEL_CHECK();
+        exclusive_scan<int64_t>(reinterpret_cast<const int64_t *>(cnt.p), off.p, n, tmp.p, st);
+        int64_t total = 0;
+        CUDA_TRY(cudaMemcpyAsync(&total, off.p + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+        g_kernel_launches += 1;
+        if (total > 0xFFFFFFFFll) throw ShciError{SHCI_ERR_INVALID, "too many terms in one batch: more batches"};
+        if (total > 0) {
+            DevBuf<uint64_t> cand;
+            DevBuf<double> t, mg;
+            DevBuf<uint32_t> idx;
+            cand.alloc((size_t)total * KW);
+            t.alloc((size_t)total);
+            mg.alloc((size_t)total);
+            idx.alloc((size_t)total);
+            S.off = off.p;
+            S.out = cand.p;
+            S.terms = t.p;
+            S.mags = mg.p;
+            k_select<W, true, true><<<blocks, SEL_THREADS, 0, st>>>(S, I);
+            KERNEL_CHECK();
+            const int gt = (int)std::min<int64_t>(ceil_div(total, SEL_THREADS), (int64_t)c->n_sm * 16);
+            k_iota<<<gt, SEL_THREADS, 0, st>>>(idx.p, total);
+            KERNEL_CHECK();
+            radix_sort<KW>(cand.p, idx.p, total, c->sw, st);
+            k_psto_reduce<W><<<rblocks, SEL_THREADS, 0, st>>>(cand.p, idx.p, t.p, mg.p, total, vs.p, n, I, e_var,
+                                                              eps_dtm, part.p, npart.p);
+            KERNEL_CHECK();
+            g_kernel_launches += 3;
+            CUDA_TRY(cudaMemcpyAsync(hp.data(), part.p, sizeof(double) * 2 * rblocks, cudaMemcpyDeviceToHost, st));
+            CUDA_TRY(cudaMemcpyAsync(hn.data(), npart.p, sizeof(unsigned long long) * rblocks,
+                                     cudaMemcpyDeviceToHost, st));
+            CUDA_TRY(cudaStreamSynchronize(st));
+            for (int x = 0; x < rblocks; x++) {
+                sum += hp[2 * x];
+                sum2 += hp[2 * x + 1];
+                count += (int64_t)hn[x];
+            }
+            S.mags = nullptr;
+        }
+        done = b + 1;
+        if (done == nbatch) {
+            est = sum;
+            err = 0.0;
+            break;
+        }
+        const double n_est = (double)count * nbatch / done;             // perturbative determinants, all batches
+        const double rest = n_est - (double)count;
+        const double mean = count > 0 ? sum / count : 0.0;
+        const double var = count > 1 ? std::max(0.0, (sum2 - count * mean * mean) / (count - 1)) : 0.0;
+        est = sum + mean * rest;
+        err = std::sqrt(var * rest);
+        if (count > 1 && err < 0.4 * target) break;
+    }
+}
+
+void pt2_3step(shci_ctx *c, const double *coef, double e_var, double eps2, double eps2_psto, double eps2_dtm,
+               double target, int nbatch_psto, int nbatch_sto, int64_t n_d, int n_samples, uint64_t seed,
+               shci_pt2_3step_t *out, int mem) {
+    if (!out) throw ShciError{SHCI_ERR_INVALID, "null pointer"};
+    if (!(eps2 > 0.0 && eps2 <= eps2_psto && eps2_psto <= eps2_dtm) || !std::isfinite(eps2_dtm))
+        throw ShciError{SHCI_ERR_INVALID, "need 0 < eps2 <= eps2_psto <= eps2_dtm, finite"};
+    if (!(target >= 0.0)) throw ShciError{SHCI_ERR_INVALID, "target error must be >= 0"};
+    if (nbatch_psto < 16 || nbatch_psto > 1 << 20 || nbatch_sto < 1 || nbatch_sto > 1 << 20)
+        throw ShciError{SHCI_ERR_INVALID, "need 16 <= pseudo-stochastic batches and 1 <= stochastic batches"};
+    if (n_samples < 1 || n_d < 2) throw ShciError{SHCI_ERR_INVALID, "need n_samples >= 1 and n_d >= 2"};
+    if (mem != SHCI_MEM_HOST && mem != SHCI_MEM_DEVICE) throw ShciError{SHCI_ERR_INVALID, "unknown mem_space"};
+    cudaStream_t st = c->st;
+    const double *cd = coef;
+    DevBuf<double> cbuf;
+    if (mem == SHCI_MEM_HOST) {
+        cbuf.alloc((size_t)c->n_det);
+        CUDA_TRY(cudaMemcpyAsync(cbuf.p, coef, sizeof(double) * c->n_det, cudaMemcpyHostToDevice, st));
+        cd = cbuf.p;
+    }
+    *out = shci_pt2_3step_t{};
+    // 1: deterministic at eps2_dtm (hash batches as memory requires)
+    pt2(c, cd, e_var, eps2_dtm, 0, &out->dtm, nullptr, SHCI_MEM_DEVICE);
+    // 2: pseudo-stochastic at eps2_psto, minus its eps2_dtm part
+    ensure_lists(c);
+    if (eps2_psto < eps2_dtm) {
+        if (c->W == 1) psto_w<1>(c, cd, e_var, eps2_psto, eps2_dtm, nbatch_psto, target, out->psto, out->psto_err,
+                                 out->psto_batches);
+        else psto_w<2>(c, cd, e_var, eps2_psto, eps2_dtm, nbatch_psto, target, out->psto, out->psto_err,
+                       out->psto_batches);
+    }
+    // 3: stochastic at eps2, minus its eps2_psto part; one batch per sample, drawn
+    // from the SplitMix64 stream after the determinant draws, times the batch count
+    if (eps2 < eps2_psto) {
+        DevBuf<int64_t> draws;
+        draws.alloc((size_t)n_samples * n_d);
+        alias_draw(c, cd, (int64_t)n_samples * n_d, seed, draws.p, SHCI_MEM_DEVICE);
+        std::vector<int> bsel(n_samples);
+        for (int sm = 0; sm < n_samples; sm++) {
+            uint64_t z = seed + (uint64_t)((int64_t)n_samples * n_d + sm + 1) * 0x9E3779B97F4A7C15ull;
+            z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+            z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+            z ^= z >> 31;
+            bsel[sm] = (int)(((z >> 32) * (uint64_t)nbatch_sto) >> 32);
+        }
+        std::vector<double> v((size_t)2 * n_samples);
+        pt2_samples(c, cd, e_var, eps2, eps2_psto, n_d, n_samples, draws.p, v.data(), SHCI_MEM_DEVICE, nbatch_sto,
+                    bsel.data());
+        double mean = 0.0;
+        for (int sm = 0; sm < n_samples; sm++) mean += nbatch_sto * (v[2 * sm] - v[2 * sm + 1]);
+        mean /= n_samples;
+        double var = 0.0;
+        for (int sm = 0; sm < n_samples; sm++) {
+            const double d = nbatch_sto * (v[2 * sm] - v[2 * sm + 1]) - mean;
+            var += d * d;
+        }
+        out->sto = mean;
+        out->sto_err = n_samples > 1 ? std::sqrt(var / (n_samples - 1) / n_samples) : 0.0;
+    }
+    out->e2 = out->dtm + out->psto + out->sto;
+    out->e2_err = std::sqrt(out->psto_err * out->psto_err + out->sto_err * out->sto_err);
+}
+
 void pt2_semistochastic(shci_ctx *c, const double *coef, double e_var, double eps2, double eps2_d, int64_t n_d,
                         int n_samples, uint64_t seed, double *e2, double *e2_err, int mem) {
     if (!e2) throw ShciError{SHCI_ERR_INVALID, "null pointer"};
@@ -1072,7 +1327,7 @@ void pt2_semistochastic(shci_ctx *c, const double *coef, double e_var, double ep
     }
     alias_draw(c, cd, (int64_t)n_samples * n_d, seed, draws.p, SHCI_MEM_DEVICE);
     std::vector<double> v((size_t)2 * n_samples);
-    pt2_samples(c, cd, e_var, eps2, eps2_d, n_d, n_samples, draws.p, v.data(), SHCI_MEM_DEVICE);
+    pt2_samples(c, cd, e_var, eps2, eps2_d, n_d, n_samples, draws.p, v.data(), SHCI_MEM_DEVICE, 1, nullptr);
     double mean = 0.0;
     for (int sm = 0; sm < n_samples; sm++) mean += v[2 * sm] - v[2 * sm + 1];
     mean /= n_samples;

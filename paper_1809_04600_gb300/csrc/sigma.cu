@@ -1,4 +1,4 @@
-// sigma = H c: the matrix-vector product of each Davidson step (Sec. IV.B).
+// sigma = H c: the matrix-vector product of each Davidson step (Sec. V.B).
 //
 // Stored mode keeps both triangles of H as CSR rows (diagonal separate), so a
 // row's product is a pure gather: one FP64 FMA per stored nonzero per vector
@@ -130,7 +130,7 @@ void sigma(shci_ctx *c, int k, const double *x, double *y, bool inter) {
 }
 
 // On-the-fly sigma (the "direct" method the paper proposes for larger spaces,
-// Sec. VI): every product re-enumerates the connected pairs with the helper
+// Sec. VIII): every product re-enumerates the connected pairs with the helper
 // lists and recomputes H_ij, so H is never stored.  Pass 1 (rows grouped by
 // alpha string) writes y = diag * x + same-spin-beta and opposite-spin terms;
 // pass 2 (rows grouped by beta string) adds the same-spin-alpha terms.

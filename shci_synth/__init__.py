@@ -14,7 +14,7 @@ Layouts (the library's input contract):
                   p >= q and slot = PQ*(PQ+1)/2 + RS for PQ >= RS (8-fold symmetry).
 * determinants    uint64 [n_det, 2*W], alpha words then beta words; spatial
                   orbital n of a spin string is bit (n & 63) of word (n >> 6)
-                  (the bit-packed representation of Sec. IV.A), W = ceil(n_orb/64).
+                  (the bit-packed representation of Sec. V.A), W = ceil(n_orb/64).
 
 The paper's molecular integrals (Cu, Cr2) are not available; the generators
 below are stand-ins with the paper's shapes (orbital counts, electron counts,

@@ -1,4 +1,4 @@
-"""Heat-bath selection (Sec. II, Eq. 2) on the GPU against the oracle's brute
+"""Heat-bath selection (Sec. II.A, Eq. 2) on the GPU against the oracle's brute
 force: the selected sets are compared as sets of determinants, bit-exact.
 The GPU tests |H_ai| |c_i| >= eps1 in FP64 with matrix elements summed in
 another order than the oracle's, so products within 1e-9 of eps1 may fall
@@ -242,4 +242,39 @@ def test_semistochastic_pt2(P, oracle_mod):
     assert abs(same - det) <= 1e-13 * abs(det) and err0 == 0.0
     est, err = P.shci_pt2_semistochastic(B.ctx.handle, c, float(e[0]), 1e-5, 1e-3, 200, 64, 7)
     assert err > 0.0 and abs(est - det) <= 6.0 * err + 1e-12
+    B.close()
+
+
+# ---------------------------------------------------------------- 3-step perturbation scheme (Sec. IV, Eq. 11)
+
+def test_pt2_sample_batches_add_up(P, oracle_mod):
+    """A sample's value restricted to each hash batch adds up to its
+    unrestricted value (the batches partition the perturbative determinants)."""
+    cfg, h, eri, ec, dets = G.system("sel_24o_6a6b_1m", 600)
+    B = G.Built(P, h, eri, ec, dets, 6, 6)
+    e, vecs, it = B.davidson(1, tol=1e-10)
+    c = G.dev(vecs[0])
+    draws = G.dev(_draws(vecs[0], 2, 40, 9))
+    full = P.shci_pt2_samples(B.ctx.handle, c, float(e[0]), 1e-5, 1e-4, draws)
+    parts = sum(P.shci_pt2_samples(B.ctx.handle, c, float(e[0]), 1e-5, 1e-4, draws, 5, [b, b]) for b in range(5))
+    np.testing.assert_allclose(parts, full, rtol=1e-12, atol=0)
+    B.close()
+
+
+def test_pt2_three_step(P, oracle_mod):
+    cfg, h, eri, ec, dets = G.system("sel_24o_6a6b_1m", 600)
+    B = G.Built(P, h, eri, ec, dets, 6, 6)
+    e, vecs, it = B.davidson(1, tol=1e-10)
+    c, ev = G.dev(vecs[0]), float(e[0])
+    ref = {eps: P.shci_pt2(B.ctx.handle, c, ev, eps)[0] for eps in (1e-6, 1e-5, 1e-4)}
+    # every pseudo-stochastic batch (target 0) and no stochastic step: deterministic, exact
+    r = P.shci_pt2_3step(B.ctx.handle, c, ev, 1e-5, 1e-5, 1e-4, 0.0, 16, 8, 100, 4, 3)
+    assert r["psto_batches"] == 16 and r["psto_err"] == 0.0 and r["sto"] == 0.0 and r["sto_err"] == 0.0
+    assert abs(r["dtm"] - ref[1e-4]) <= 1e-13 * abs(ref[1e-4])
+    assert abs(r["psto"] - (ref[1e-5] - ref[1e-4])) <= 1e-12 * abs(ref[1e-5])
+    assert abs(r["e2"] - ref[1e-5]) <= 1e-12 * abs(ref[1e-5])
+    # all three steps: within 6 standard errors of the deterministic energy at eps2
+    r = P.shci_pt2_3step(B.ctx.handle, c, ev, 1e-6, 1e-5, 1e-4, 2e-4, 16, 8, 200, 48, 5)
+    assert 1 <= r["psto_batches"] <= 16 and r["e2_err"] > 0.0
+    assert abs(r["e2"] - ref[1e-6]) <= 6.0 * r["e2_err"] + 1e-12
     B.close()

@@ -313,7 +313,7 @@ def test_planted_mistake_is_caught(oracle_mod, tmp_path, name):
     assert np.max(np.abs(got - ref)) > 1e-6, "planted mistake was not detected"
 
 
-# ---------------------------------------------------------------- heat-bath selection (Sec. II, Eq. 2)
+# ---------------------------------------------------------------- heat-bath selection (Sec. II.A, Eq. 2)
 
 def _excitation_degree(a, b):
     return int(sum(bin(int(x) ^ int(y)).count("1") for x, y in zip(a, b))) // 2
