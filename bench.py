@@ -681,6 +681,95 @@ def run_select(args):
     ctx.close()
 
 
+def run_extend(args):
+    """Incremental Hamiltonian update (Sec. III, Algorithms 1 and 2) on the
+    bench's 1e6-determinant space, which is in generation order: V_old = the
+    first (1 - f) n determinants (built, stored H), then the last f n appended.
+    Per fraction f, the device time of the incremental update against a full
+    build of the grown space (the same call with the switch forced); the grown
+    matrix's pair count against a direct build's and sampled rows against the
+    oracle's brute force.  Then one variational iteration: select with eps1
+    from the converged coefficients, grow V with the selected determinants,
+    and solve again."""
+    torch, P = _gpu_setup()
+    import oracle
+    cfg = S.config(args.config)
+    h, eri, ec, dets = S.make_system(cfg)
+    n = dets.shape[0]
+    ctx = P.Context(0, torch.cuda.current_stream())
+    H = ctx.handle
+    P.shci_load_integrals(H, cfg.n_orb, ec, _dev(torch, h), _dev(torch, eri))
+    dd = _dev(torch, dets)
+    nnz_direct = 0
+    for _ in range(2):
+        nnz_direct = P.shci_build_connectivity(H, cfg.n_alpha, cfg.n_beta, dd, P.SHCI_STORED)
+    build_ms = P.shci_get_stats(H)["build_ms"]
+    O = oracle.System(h, eri, ec)
+    lines = []
+    for f in (args.extend_frac or [0.02, 0.05, 0.1, 0.2, 0.4]):
+        n_old = n - int(round(f * n))
+        line = {"fraction_new": f, "n_old": n_old, "n_new": n - n_old}
+        for arm, ff in (("rebuild", 1e-9), ("incremental", 1.0)):
+            ms = []
+            for _ in range(max(1, args.steps)):
+                P.shci_build_connectivity(H, cfg.n_alpha, cfg.n_beta, dd[:n_old], P.SHCI_STORED)
+                nnz = P.shci_extend_connectivity(H, dd[n_old:], ff)
+                st = P.shci_get_stats(H)
+                if nnz != nnz_direct or st["extend_incremental"] != (arm == "incremental"):
+                    raise RuntimeError("extend: %s arm gave %d pairs, a direct build %d" % (arm, nnz, nnz_direct))
+                ms.append(st["extend_ms"])
+            line[arm + "_ms"] = float(np.median(ms))
+            line[arm + "_candidates"] = st["candidates"]
+        line["speedup"] = line["rebuild_ms"] / line["incremental_ms"]
+        # rows of the incrementally grown matrix (old and new) against the oracle
+        rng = np.random.default_rng(int(f * 1000))
+        rows = np.concatenate([rng.choice(n_old, 3, replace=False), n_old + rng.choice(n - n_old, 3, replace=False)])
+        err, same = 0.0, True
+        for i in rows:
+            gc, gv = P.shci_get_row(H, int(i))          # ascending columns
+            oc, ov = O.row(dets, int(i))
+            same &= bool(np.array_equal(gc, np.asarray(oc)))
+            if same and len(oc):
+                err = max(err, float(np.max(np.abs(gv - np.asarray(ov)))))
+        line["oracle_rows"] = int(rows.size)
+        line["oracle_rows_same_columns"] = same
+        line["oracle_rows_max_abs_err"] = err
+        lines.append(line)
+    # one variational iteration from the full space: solve, select, grow, solve
+    P.shci_build_connectivity(H, cfg.n_alpha, cfg.n_beta, dd, P.SHCI_STORED)
+    vecs = torch.empty((cfg.roots, n), dtype=torch.float64, device="cuda")
+    e0, _, _ = P.shci_davidson(H, cfg.roots, TOL, MAX_ITER, vecs=vecs)
+    it = {"eps1": args.extend_eps1, "n_det": n, "energies": [float(x) for x in e0]}
+    new = P.shci_select(H, vecs, args.extend_eps1)
+    torch.cuda.synchronize()
+    it["new_dets"] = int(new.shape[0])
+    if new.shape[0]:
+        t = time.perf_counter()
+        nnz = P.shci_extend_connectivity(H, new, 1.0)
+        torch.cuda.synchronize()
+        st = P.shci_get_stats(H)
+        it.update({"incremental_ms": st["extend_ms"], "incremental_wall_s": time.perf_counter() - t,
+                   "nnz_upper": nnz})
+        grown = torch.cat([dd, new])
+        for _ in range(2):
+            nnz2 = P.shci_build_connectivity(H, cfg.n_alpha, cfg.n_beta, grown, P.SHCI_STORED)
+        it["rebuild_ms"] = P.shci_get_stats(H)["build_ms"]
+        it["direct_build_same_nnz"] = nnz2 == nnz
+        guess = torch.zeros((cfg.roots, grown.shape[0]), dtype=torch.float64, device="cuda")
+        guess[:, :n] = vecs
+        v2 = torch.empty_like(guess)
+        t = time.perf_counter()
+        e1, iters, _ = P.shci_davidson(H, cfg.roots, TOL, MAX_ITER, guess=guess, vecs=v2)
+        torch.cuda.synchronize()
+        it.update({"n_det_grown": int(grown.shape[0]), "energies_grown": [float(x) for x in e1],
+                   "davidson_s": time.perf_counter() - t, "davidson_iters": iters})
+    print(json.dumps({"workload": workload_desc(cfg) + ", in generation order; the last f n determinants "
+                                                       "appended to the first (1 - f) n",
+                      "direct_build_ms": build_ms, "nnz_upper": nnz_direct, "lines": lines,
+                      "variational_iteration": it}))
+    ctx.close()
+
+
 BATCH_PHASES = ("start", "sigma_stored_and_alpha_items", "sigma_beta_items", "gram_columns", "eigensolver",
                 "ritz_residuals", "convergence_restart", "basis_rotation", "second_pass_coef", "second_projection",
                 "cholqr1_coef", "cholqr_apply", "cholqr2_coef", "next_block", "bookkeeping")
@@ -768,7 +857,8 @@ def main():
                     help="profiling only: a smaller space of the same shape (not a bench line)")
     ap.add_argument("--sigma-only", type=int, default=0,
                     help="profiling only: build once, then launch the sigma kernel this many times")
-    ap.add_argument("--workload", default="main", choices=["main", "fci", "large", "adjoint", "batch", "select"],
+    ap.add_argument("--workload", default="main",
+                    choices=["main", "fci", "large", "adjoint", "batch", "select", "extend"],
                     help="main: the bench line; others print the measurement line of another workload")
     ap.add_argument("--batch-budget-gb", type=float, default=180.0)
     ap.add_argument("--eps1", type=float, action="append", help="selection thresholds (select workload)")
@@ -777,10 +867,13 @@ def main():
     ap.add_argument("--semi-eps2", type=float, default=1e-6, help="semistochastic eps2 (0: skip)")
     ap.add_argument("--semi-nd", type=int, default=20000, help="draws per semistochastic sample")
     ap.add_argument("--semi-samples", type=int, default=16, help="semistochastic samples")
+    ap.add_argument("--extend-frac", type=float, action="append",
+                    help="fractions of new determinants (extend workload)")
+    ap.add_argument("--extend-eps1", type=float, default=1e-3, help="selection threshold (extend workload)")
     args = ap.parse_args()
     if args.workload != "main":
         {"fci": run_fci, "large": run_large, "adjoint": run_adjoint, "batch": run_batch,
-         "select": run_select}[args.workload](args)
+         "select": run_select, "extend": run_extend}[args.workload](args)
     elif args.sigma_only:
         run_sigma_only(args)
     elif args.impl == "reference":

@@ -100,6 +100,28 @@ int shci_build_connectivity(shci_ctx *ctx, int n_alpha, int n_beta, int64_t n_de
                             const uint64_t *dets, int mem_space, int mode,
                             int64_t *nnz_upper_out);
 
+/* Grow V by n_new determinants (Sec. III): V becomes dets[0 .. n_old) followed
+ * by new_dets[0 .. n_new) (same layout and rules as shci_build_connectivity;
+ * they must differ from V's and from one another), new determinant j taking
+ * index n_old + j.  The helper lists and the diagonal are rebuilt for the
+ * whole of V.  When n_new < full_fraction * (n_old + n_new) the update is
+ * incremental: only the old-new and new-new elements are evaluated (each old
+ * row screens only the new members of its candidate lists, held in
+ * determinant order for this pass), and the stored rows of old determinants
+ * are copied with their new elements appended, so row i of the stored matrix
+ * holds its old elements first.  Otherwise V is rebuilt from scratch
+ * (per-string lists in beta order, occupancy-bitmap lookups).  The paper's
+ * switch between the two list orders sits at 20 %; full_fraction <= 0 takes
+ * 0.2.  The mode of the last build is kept (SHCI_AUTO re-decides against the
+ * memory left); SHCI_ON_THE_FLY contexts get the count only.  n_new = 0 is a
+ * no-op.  On any error the context is left unbuilt (SHCI_ERR_STATE until the
+ * next shci_build_connectivity).  *nnz_upper_out (may be NULL) as for
+ * shci_build_connectivity.  SHCI_ERR_STATE without a completed build;
+ * SHCI_ERR_INVALID for n_new < 0, a NULL pointer with n_new > 0 or
+ * n_old + n_new > 2^31 - 1. */
+int shci_extend_connectivity(shci_ctx *ctx, int64_t n_new, const uint64_t *new_dets, int mem_space,
+                             double full_fraction, int64_t *nnz_upper_out);
+
 /* The cached diagonal H_ii, [n_det]. */
 int shci_get_diag(shci_ctx *ctx, double *diag, int mem_space);
 
@@ -146,7 +168,9 @@ int shci_sigma_noalloc(shci_ctx *ctx, int k, const double *c, double *sigma);
  * converge (its Ritz value and residual are still checked every iteration).
  * guess: NULL (start from the unit vectors of the k_roots lowest H_ii) or
  * [k_roots][n_det] starting vectors (orthonormalised by the call), in
- * mem_space.  energies: host [k_roots], ascending.  vecs: [k_roots][n_det]
+ * mem_space.  Like any Davidson iteration it can settle on an excited root
+ * when the start overlaps the lowest ones poorly, and it keeps every symmetry
+ * of H that the start has: a guess steers it.  energies: host [k_roots], ascending.  vecs: [k_roots][n_det]
  * orthonormal Ritz vectors in mem_space, or NULL.  iters_out may be NULL.
  * Returns SHCI_ERR_NOT_CONVERGED (with the last estimates written) after
  * max_iter iterations. */
@@ -357,6 +381,9 @@ typedef struct {
     double pt2_ms;              /* last shci_pt2, device time (lists included when built) */
     int pt2_batches;            /* last shci_pt2: hash batches used */
     int64_t pt2_terms;          /* last shci_pt2: terms H_ai c_i kept by the eps2 screen */
+    double extend_ms;           /* last shci_extend_connectivity, device time */
+    int extend_incremental;     /* last shci_extend_connectivity: 1 incremental, 0 rebuilt */
+    int64_t extend_n_old;       /* last shci_extend_connectivity: determinants before it */
 } shci_stats_t;
 
 /* Fill *out.  Kernel times are recorded only while timing is enabled. */

@@ -12,6 +12,7 @@ from .binding import (  # noqa: F401
     shci_get_pairs, shci_get_row, shci_get_stats, shci_last_error, shci_load_integrals, shci_set_timing, shci_sigma,
 )
 from .binding import shci_energy_backward, shci_pt2, shci_select, shci_sigma_noalloc  # noqa: F401
+from .binding import shci_extend_connectivity  # noqa: F401
 from .binding import shci_alias_draw, shci_pt2_3step, shci_pt2_samples, shci_pt2_semistochastic  # noqa: F401
 from .binding import (  # noqa: F401
     shci_batch_create, shci_batch_davidson, shci_batch_destroy, shci_batch_get_stats,

@@ -35,7 +35,7 @@ _STATUS = {1: "INVALID", 2: "OOM", 3: "CUDA", 4: "NOT_CONVERGED", 5: "TIMEOUT", 
 # every symbol include/shci.h declares (checked by the tests)
 EXPORTED = [
     "shci_create", "shci_destroy", "shci_last_error", "shci_load_integrals", "shci_build_connectivity",
-    "shci_get_diag", "shci_get_pairs", "shci_get_row", "shci_sigma", "shci_sigma_noalloc", "shci_energy_backward",
+    "shci_extend_connectivity", "shci_get_diag", "shci_get_pairs", "shci_get_row", "shci_sigma", "shci_sigma_noalloc", "shci_energy_backward",
     "shci_batch_create", "shci_batch_davidson", "shci_batch_get_stats", "shci_batch_destroy", "shci_davidson",
     "shci_davidson_history", "shci_select", "shci_pt2", "shci_alias_draw", "shci_pt2_samples",
     "shci_pt2_semistochastic", "shci_pt2_3step", "shci_get_stats", "shci_set_timing",
@@ -57,6 +57,7 @@ class shci_stats_t(ctypes.Structure):
         ("mode", ctypes.c_int), ("n_words", ctypes.c_int), ("davidson_phase_ms", ctypes.c_double * 8),
         ("select_ms", ctypes.c_double), ("select_candidates", ctypes.c_int64),
         ("pt2_ms", ctypes.c_double), ("pt2_batches", ctypes.c_int), ("pt2_terms", ctypes.c_int64),
+        ("extend_ms", ctypes.c_double), ("extend_incremental", ctypes.c_int), ("extend_n_old", ctypes.c_int64),
     ]
 
 
@@ -105,6 +106,7 @@ def load_library(path: str = LIB_PATH):
         "shci_last_error": (ctypes.c_char_p, [vp]),
         "shci_load_integrals": (i32, [vp, i32, f64, vp, vp, i32]),
         "shci_build_connectivity": (i32, [vp, i32, i32, i64, vp, i32, i32, ctypes.POINTER(i64)]),
+        "shci_extend_connectivity": (i32, [vp, i64, vp, i32, f64, ctypes.POINTER(i64)]),
         "shci_get_diag": (i32, [vp, vp, i32]),
         "shci_get_pairs": (i32, [vp, i64, vp, vp, vp, ctypes.POINTER(i64)]),
         "shci_get_row": (i32, [vp, i64, i64, vp, vp, ctypes.POINTER(i64)]),
@@ -202,6 +204,16 @@ def shci_build_connectivity(ctx, n_alpha, n_beta, dets, mode=SHCI_STORED) -> int
     nnz = ctypes.c_int64(0)
     _check(ctx, load_library().shci_build_connectivity(ctx, int(n_alpha), int(n_beta), int(n_det), pd, md,
                                                        int(mode), ctypes.byref(nnz)))
+    return nnz.value
+
+
+def shci_extend_connectivity(ctx, new_dets, full_fraction=0.2) -> int:
+    """Append new_dets [n_new][2W] to V and update the connectivity (incremental
+    below full_fraction of the grown V, else rebuilt); returns nnz_upper."""
+    pd, md, kd = _ptr(new_dets, np.uint64)
+    nnz = ctypes.c_int64(0)
+    _check(ctx, load_library().shci_extend_connectivity(ctx, int(new_dets.shape[0]), pd, md, float(full_fraction),
+                                                        ctypes.byref(nnz)))
     return nnz.value
 
 

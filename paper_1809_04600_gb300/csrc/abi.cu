@@ -105,6 +105,15 @@ int shci_build_connectivity(shci_ctx *c, int n_alpha, int n_beta, int64_t n_det,
     });
 }
 
+int shci_extend_connectivity(shci_ctx *c, int64_t n_new, const uint64_t *new_dets, int mem, double full_fraction,
+                             int64_t *nnz_upper_out) {
+    return guarded(c, [&] {
+        shci::extend(c, n_new, new_dets, mem, full_fraction);
+        if (nnz_upper_out) *nnz_upper_out = c->nnz_upper;
+        return SHCI_OK;
+    });
+}
+
 int shci_get_diag(shci_ctx *c, double *diag, int mem) {
     return guarded(c, [&] {
         if (!c->built) throw ShciError{SHCI_ERR_STATE, "not built"};

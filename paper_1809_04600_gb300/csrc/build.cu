@@ -152,11 +152,12 @@ __global__ void k_unique_write(const uint64_t *__restrict__ keys, const uint32_t
     }
 }
 
-// composite key (major << 32 | minor) per determinant
+// composite key (major << 32 | minor) per determinant; minor == nullptr takes
+// the determinant index
 __global__ void k_composite(const int32_t *__restrict__ major, const int32_t *__restrict__ minor, int64_t n,
                             uint64_t *__restrict__ keys, uint32_t *__restrict__ vals) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        keys[i] = ((uint64_t)(uint32_t)major[i] << 32) | (uint32_t)minor[i];
+        keys[i] = ((uint64_t)(uint32_t)major[i] << 32) | (minor ? (uint32_t)minor[i] : (uint32_t)i);
         vals[i] = (uint32_t)i;
     }
 }
@@ -177,6 +178,50 @@ __global__ void k_group_build(const uint64_t *__restrict__ keys, const uint32_t 
 #pragma unroll
         for (int w = 0; w < W; w++) mstr[i * W + w] = dets[(int64_t)d * 2 * W + other_spin * W + w];
         if (i == n - 1) off[n_groups] = n;
+    }
+}
+
+// groups whose members are in determinant order: the offset of each group's
+// first member with index >= n_old (the group's end when it has none)
+__global__ void k_new_start_init(const int64_t *__restrict__ off, int64_t n_groups, int64_t *__restrict__ g_new) {
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n_groups; g += (int64_t)gridDim.x * blockDim.x)
+        g_new[g] = off[g + 1];
+}
+
+__global__ void k_new_start(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ vals, int64_t n,
+                            int64_t n_old, int64_t *__restrict__ g_new) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+        if ((int64_t)vals[p] < n_old) continue;
+        const uint64_t g = keys[p] >> 32;
+        if (p == 0 || (keys[p - 1] >> 32) != g || (int64_t)vals[p - 1] < n_old) g_new[g] = p;
+    }
+}
+
+// incremental update: row lengths and the offsets of the two new parts of each
+// row (old elements first, then the beta-grouped and alpha-grouped new ones)
+__global__ void k_extend_rows(const int64_t *__restrict__ old_rowptr, int64_t n_old, const int64_t *__restrict__ cnt_b,
+                              const int64_t *__restrict__ cnt_a, int64_t n, int64_t *__restrict__ len,
+                              int64_t *__restrict__ off_b, int64_t *__restrict__ off_a) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t old = i < n_old ? old_rowptr[i + 1] - old_rowptr[i] : 0;
+        off_b[i] = old;
+        off_a[i] = old + cnt_b[i];
+        len[i] = old + cnt_b[i] + cnt_a[i];
+    }
+}
+
+// incremental update: old rows to the head of their new slots, one warp per row
+__global__ void k_copy_rows(const int64_t *__restrict__ old_rowptr, const int32_t *__restrict__ old_col,
+                            const double *__restrict__ old_val, int64_t n_old, const int64_t *__restrict__ rowptr,
+                            int32_t *__restrict__ col, double *__restrict__ val) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t i = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); i < n_old; i += warps) {
+        const int64_t src = old_rowptr[i], len = old_rowptr[i + 1] - src, dst = rowptr[i];
+        for (int64_t e = lane; e < len; e += 32) {
+            col[dst + e] = __ldcs(&old_col[src + e]);
+            val[dst + e] = __ldcs(&old_val[src + e]);
+        }
     }
 }
 
@@ -284,6 +329,49 @@ static void make_items(shci_ctx *c, const int64_t *off, int64_t n_groups, DevBuf
 }
 
 
+// incremental update: work items over the old (part 0) or new (part 1) members
+// of each determinant-ordered group, with the member offset each item ends at
+struct PartItems {
+    DevBuf<int32_t> group, first, end;
+    int64_t n = 0;
+};
+
+static void make_items_part(shci_ctx *c, const int64_t *off, const int64_t *g_new, int64_t n_groups, int part,
+                            PartItems &P) {
+    cudaStream_t st = c->st;
+    DevBuf<int64_t> cnt, start, tmp;
+    cnt.alloc((size_t)n_groups + 1);
+    start.alloc((size_t)n_groups + 1);
+    tmp.alloc((size_t)scan_tmp_len(n_groups + 1));
+    unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n_groups, 256), 4096));
+    k_items_count_part<<<g, 256, 0, st>>>(off, g_new, n_groups, part, cnt.p);
+    exclusive_scan<int64_t>(cnt.p, start.p, n_groups, tmp.p, st);
+    CUDA_TRY(cudaMemcpyAsync(&P.n, start.p + n_groups, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    if (P.n > 0x7FFFFFFFll) throw ShciError{SHCI_ERR_INVALID, "too many work items"};
+    P.group.alloc((size_t)std::max<int64_t>(P.n, 1));
+    P.first.alloc((size_t)std::max<int64_t>(P.n, 1));
+    P.end.alloc((size_t)std::max<int64_t>(P.n, 1));
+    k_items_fill_part<<<g, 256, 0, st>>>(off, g_new, start.p, n_groups, part, P.group.p, P.first.p, P.end.p);
+    KERNEL_CHECK();
+    g_kernel_launches += 2;
+}
+
+// one count or fill pass of the incremental update over the given items, rows
+// taken from the determinant-ordered member lists rdet / rstr
+template <int W, int MODE>
+static void extend_pass(shci_ctx *c, EnumArgs E, const DevInts &I, bool alpha_part, const PartItems &items,
+                        const int32_t *rdet, const uint64_t *rstr) {
+    if (items.n == 0) return;
+    E.item_group = items.group.p;
+    E.item_first = items.first.p;
+    E.item_end = items.end.p;
+    E.n_items = items.n;
+    E.row_det = rdet;
+    E.row_str = rstr;
+    launch_enum<W, MODE, 0>(c, E, I, alpha_part);
+}
+
 // ====================================================================== host pipeline
 
 static inline unsigned grid_for(int64_t n, int threads = 256) {
@@ -329,6 +417,31 @@ static void group_by(shci_ctx *c, const int32_t *major, const int32_t *minor, in
                                                   n_groups, off.p, mdet.p, mstr.p, c->counter.p);
     KERNEL_CHECK();
     LAUNCHED(2);
+}
+
+// Groups by `major` with members in determinant order (the incremental
+// update's list order, Sec. III): members and their other-spin strings into
+// mdet / mstr, and the offset of each group's first new member into g_new.
+// The offsets equal those of group_by over the same strings.
+template <int W>
+static void group_by_index(shci_ctx *c, const int32_t *major, int64_t n_groups, int other_spin, int64_t n_old,
+                           DevBuf<int64_t> &off, DevBuf<int32_t> &mdet, DevBuf<uint64_t> &mstr,
+                           DevBuf<int64_t> &g_new) {
+    const int64_t n = c->n_det;
+    cudaStream_t st = c->st;
+    k_composite<<<grid_for(n), 256, 0, st>>>(major, nullptr, n, c->sort_keys.p, c->sort_vals.p);
+    KERNEL_CHECK();
+    radix_sort<1>(c->sort_keys.p, c->sort_vals.p, n, c->sw, st);
+    off.alloc((size_t)n_groups + 1);
+    mdet.alloc((size_t)n);
+    mstr.alloc((size_t)n * W);
+    g_new.alloc((size_t)n_groups);
+    k_group_build<W><<<grid_for(n), 256, 0, st>>>(c->sort_keys.p, c->sort_vals.p, n, c->dets.p, other_spin,
+                                                  n_groups, off.p, mdet.p, mstr.p, c->counter.p);
+    k_new_start_init<<<grid_for(n_groups), 256, 0, st>>>(off.p, n_groups, g_new.p);
+    k_new_start<<<grid_for(n), 256, 0, st>>>(c->sort_keys.p, c->sort_vals.p, n, n_old, g_new.p);
+    KERNEL_CHECK();
+    LAUNCHED(4);
 }
 
 // Single-excitation lists (Table I's alpha-singles, and the beta mirror) over
@@ -437,8 +550,21 @@ static void opposite_spin_setup(shci_ctx *c) {
     if (!(c->opp_factor >= 0.0f)) c->opp_factor = 0.5f;
 }
 
+// SHCI_AUTO: store H when its nnz elements (12 bytes each) fit 80 % of the free
+// device memory and the context's budget
+static int decide_mode(shci_ctx *c, int mode, int64_t nnz) {
+    if (mode != SHCI_AUTO) return mode;
+    size_t free_b = 0, total_b = 0;
+    CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+    double need = (double)nnz * 12.0;
+    double cap = 0.8 * (double)free_b;
+    if (c->stored_budget >= 0.0) cap = std::min(cap, c->stored_budget);
+    return need < cap ? SHCI_STORED : SHCI_ON_THE_FLY;
+}
+
+// validation, helper lists (Table I), the diagonal and the work items of V
 template <int W>
-static void build_w(shci_ctx *c, int mode) {
+static void lists_w(shci_ctx *c) {
     cudaStream_t st = c->st;
     const int64_t n = c->n_det;
     c->counter.alloc(4);
@@ -472,6 +598,14 @@ static void build_w(shci_ctx *c, int mode) {
     // work items: chunks of ENUM_NW rows of one alpha (beta) group
     make_items(c, c->ga_off.p, c->Ua, c->item_a_group, c->item_a_first, c->n_items_a);
     make_items(c, c->gb_off.p, c->Ub, c->item_b_group, c->item_b_first, c->n_items_b);
+}
+
+template <int W>
+static void build_w(shci_ctx *c, int mode) {
+    cudaStream_t st = c->st;
+    const int64_t n = c->n_det;
+    lists_w<W>(c);
+    DevInts I = dev_ints(c);
 
     // count pass: entries of the beta-grouped part and of the alpha-grouped part of each row
     DevBuf<unsigned long long> cand;
@@ -499,14 +633,7 @@ static void build_w(shci_ctx *c, int mode) {
     c->nnz_full = nnz;
     c->nnz_upper = nnz / 2;
     c->candidates = (int64_t)ncand;
-    if (mode == SHCI_AUTO) {
-        size_t free_b = 0, total_b = 0;
-        CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
-        double need = (double)nnz * 12.0;
-        double cap = 0.8 * (double)free_b;
-        if (c->stored_budget >= 0.0) cap = std::min(cap, c->stored_budget);
-        mode = need < cap ? SHCI_STORED : SHCI_ON_THE_FLY;
-    }
+    mode = decide_mode(c, mode, nnz);
     c->mode = mode;
     if (mode == SHCI_STORED) {
         c->col.alloc((size_t)std::max<int64_t>(nnz, 1));
@@ -525,6 +652,156 @@ static void build_w(shci_ctx *c, int mode) {
     CUDA_TRY(cudaStreamSynchronize(st));
 }
 
+// Incremental update after V grew from n_old determinants (Sec. III,
+// Algorithms 1 and 2).  The lists are rebuilt for all of V; a second copy of
+// the per-string groups with members in determinant order puts each group's
+// new members in a suffix.  New rows take every candidate from the usual
+// lists (group scans or bitmap lookups, as in a full build); old rows take
+// only the new candidates, the suffixes of the determinant-ordered groups
+// (j >= s), each warp reading its row's suffixes directly.  The old rows are
+// copied into the grown matrix ahead of their new elements.
+template <int W>
+static void extend_w(shci_ctx *c, int64_t n_old) {
+    cudaStream_t st = c->st;
+    const int64_t n = c->n_det;
+    lists_w<W>(c);
+    DevInts I = dev_ints(c);
+    DevBuf<int64_t> off_tmp, ga_new, gb_new;
+    DevBuf<int32_t> gad, gbd;
+    DevBuf<uint64_t> gas, gbs;
+    group_by_index<W>(c, c->ia.p, c->Ua, 1, n_old, off_tmp, gad, gas, ga_new);
+    group_by_index<W>(c, c->ib.p, c->Ub, 0, n_old, off_tmp, gbd, gbs, gb_new);
+    PartItems ia_old, ia_new, ib_old, ib_new;
+    make_items_part(c, c->ga_off.p, ga_new.p, c->Ua, 0, ia_old);
+    make_items_part(c, c->ga_off.p, ga_new.p, c->Ua, 1, ia_new);
+    make_items_part(c, c->gb_off.p, gb_new.p, c->Ub, 0, ib_old);
+    make_items_part(c, c->gb_off.p, gb_new.p, c->Ub, 1, ib_new);
+    // new rows: every candidate, the context's lists
+    EnumArgs An = enum_args(c);
+    // old rows: new candidates only, determinant-ordered lists
+    EnumArgs Ao = enum_args(c);
+    Ao.ga_det = gad.p;
+    Ao.ga_str = gas.p;
+    Ao.gb_det = gbd.p;
+    Ao.gb_str = gbs.p;
+    Ao.opp_lookup = 0;
+    Ao.opp_hybrid = 0;
+    Ao.n_old = n_old;
+    Ao.ga_new = ga_new.p;
+    Ao.gb_new = gb_new.p;
+
+    // count pass: new elements of each row, beta-grouped and alpha-grouped
+    DevBuf<unsigned long long> cand;
+    cand.alloc(1);
+    CUDA_TRY(cudaMemsetAsync(cand.p, 0, sizeof(unsigned long long), st));
+    DevBuf<int64_t> cnt_a, len, off_a, off_b, rowptr;
+    c->cnt_b.alloc((size_t)n);
+    cnt_a.alloc((size_t)n);
+    len.alloc((size_t)n + 1);
+    off_a.alloc((size_t)n);
+    off_b.alloc((size_t)n);
+    rowptr.alloc((size_t)n + 1);
+    c->i64c.alloc((size_t)scan_tmp_len(n + 1));
+    An.cand = Ao.cand = cand.p;
+    An.cnt = Ao.cnt = c->cnt_b.p;
+    extend_pass<W, ENUM_COUNT_INC>(c, An, I, false, ib_new, gbd.p, gbs.p);
+    extend_pass<W, ENUM_COUNT_INC>(c, Ao, I, false, ib_old, gbd.p, gbs.p);
+    An.cnt = Ao.cnt = cnt_a.p;
+    extend_pass<W, ENUM_COUNT_INC>(c, An, I, true, ia_new, gad.p, gas.p);
+    extend_pass<W, ENUM_COUNT_INC>(c, Ao, I, true, ia_old, gad.p, gas.p);
+    k_extend_rows<<<grid_for(n), 256, 0, st>>>(c->rowptr.p, n_old, c->cnt_b.p, cnt_a.p, n, len.p, off_b.p, off_a.p);
+    KERNEL_CHECK();
+    LAUNCHED(1);
+    exclusive_scan<int64_t>(len.p, rowptr.p, n, c->i64c.p, st);
+    int64_t nnz = 0;
+    unsigned long long ncand = 0;
+    CUDA_TRY(cudaMemcpyAsync(&nnz, rowptr.p + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(&ncand, cand.p, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    c->candidates = (int64_t)ncand;
+    // a stored matrix stays stored unless SHCI_AUTO finds no room for the grown one
+    int mode = c->mode;
+    if (mode == SHCI_STORED && c->mode_req == SHCI_AUTO) mode = decide_mode(c, SHCI_AUTO, nnz);
+    if (mode == SHCI_STORED) {
+        DevBuf<int32_t> col;
+        DevBuf<double> val;
+        col.alloc((size_t)std::max<int64_t>(nnz, 1));
+        val.alloc((size_t)std::max<int64_t>(nnz, 1));
+        const unsigned gw = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n_old, 8), (int64_t)c->n_sm * 8));
+        k_copy_rows<<<gw, 256, 0, st>>>(c->rowptr.p, c->col.p, c->val.p, n_old, rowptr.p, col.p, val.p);
+        KERNEL_CHECK();
+        LAUNCHED(1);
+        for (EnumArgs *E : {&An, &Ao}) {
+            E->rowptr = rowptr.p;
+            E->col = col.p;
+            E->val = val.p;
+            E->part_off = off_b.p;
+        }
+        extend_pass<W, ENUM_FILL_INC>(c, An, I, false, ib_new, gbd.p, gbs.p);
+        extend_pass<W, ENUM_FILL_INC>(c, Ao, I, false, ib_old, gbd.p, gbs.p);
+        An.part_off = Ao.part_off = off_a.p;
+        extend_pass<W, ENUM_FILL_INC>(c, An, I, true, ia_new, gad.p, gas.p);
+        extend_pass<W, ENUM_FILL_INC>(c, Ao, I, true, ia_old, gad.p, gas.p);
+        c->col.swap(col);
+        c->val.swap(val);
+    } else {
+        c->col.reset();
+        c->val.reset();
+    }
+    c->mode = mode;
+    c->rowptr.swap(rowptr);
+    c->nnz_full = nnz;
+    c->nnz_upper = nnz / 2;
+    CUDA_TRY(cudaStreamSynchronize(st));
+}
+
+void extend(shci_ctx *c, int64_t n_new, const uint64_t *new_dets, int mem, double full_fraction) {
+    if (!c->built) throw ShciError{SHCI_ERR_STATE, "build the connectivity before extending it"};
+    if (mem != SHCI_MEM_HOST && mem != SHCI_MEM_DEVICE) throw ShciError{SHCI_ERR_INVALID, "unknown mem_space"};
+    if (n_new < 0) throw ShciError{SHCI_ERR_INVALID, "n_new must be >= 0"};
+    if (n_new == 0) return;
+    if (!new_dets) throw ShciError{SHCI_ERR_INVALID, "null determinant pointer"};
+    const int64_t n_old = c->n_det, n = n_old + n_new;
+    if (n > 0x7FFFFFFFll) throw ShciError{SHCI_ERR_INVALID, "n_old + n_new must be <= 2^31-1"};
+    if (!(full_fraction > 0.0)) full_fraction = 0.2;
+    const int W = c->W;
+    c->built = false;
+    {
+        DevBuf<uint64_t> grown;
+        grown.alloc((size_t)n * 2 * W);
+        CUDA_TRY(cudaMemcpyAsync(grown.p, c->dets.p, sizeof(uint64_t) * n_old * 2 * W, cudaMemcpyDeviceToDevice,
+                                 c->st));
+        CUDA_TRY(cudaMemcpyAsync(grown.p + n_old * 2 * W, new_dets, sizeof(uint64_t) * n_new * 2 * W,
+                                 mem == SHCI_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, c->st));
+        CUDA_TRY(cudaStreamSynchronize(c->st));
+        c->dets.swap(grown);
+    }
+    c->n_det = n;
+    const bool incremental = (double)n_new < full_fraction * (double)n;
+    cudaEvent_t e0, e1;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    CUDA_TRY(cudaEventRecord(e0, c->st));
+    if (incremental) {
+        if (W == 1) extend_w<1>(c, n_old);
+        else extend_w<2>(c, n_old);
+    } else {
+        const int mode = c->mode_req == SHCI_AUTO ? SHCI_AUTO : c->mode;
+        if (W == 1) build_w<1>(c, mode);
+        else build_w<2>(c, mode);
+    }
+    CUDA_TRY(cudaEventRecord(e1, c->st));
+    CUDA_TRY(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->stats.extend_ms = ms;
+    c->stats.extend_incremental = incremental ? 1 : 0;
+    c->stats.extend_n_old = n_old;
+    c->built = true;
+}
+
 void build(shci_ctx *c, int n_alpha, int n_beta, int64_t n_det, const uint64_t *dets, int mem, int mode) {
     if (!c->have_ints) throw ShciError{SHCI_ERR_STATE, "load integrals before building"};
     if (n_det < 1 || n_det > 0x7FFFFFFFll) throw ShciError{SHCI_ERR_INVALID, "n_det must be in [1, 2^31-1]"};
@@ -536,6 +813,7 @@ void build(shci_ctx *c, int n_alpha, int n_beta, int64_t n_det, const uint64_t *
     if (mem != SHCI_MEM_HOST && mem != SHCI_MEM_DEVICE) throw ShciError{SHCI_ERR_INVALID, "unknown mem_space"};
     const int W = (c->n_orb + 63) / 64;
     c->built = false;
+    c->mode_req = mode;
     c->W = W;
     c->n_alpha = n_alpha;
     c->n_beta = n_beta;

@@ -3,6 +3,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <string>
+#include <utility>
 #include <vector>
 #include <cuda_runtime.h>
 
@@ -62,6 +63,10 @@ struct DevBuf {
         n = count;
     }
     T *get() const { return p; }
+    void swap(DevBuf &o) {
+        std::swap(p, o.p);
+        std::swap(n, o.n);
+    }
 };
 
 // ---------------------------------------------------------------- device helpers

@@ -49,6 +49,7 @@ struct shci_ctx {
     // variational space and helper lists (Table I)
     bool built = false;
     int mode = SHCI_STORED;
+    int mode_req = SHCI_AUTO;              // the mode the last build was asked for
     int W = 1, n_alpha = 0, n_beta = 0;
     int64_t n_det = 0;
     DevBuf<uint64_t> dets;                 // [n][2W]
@@ -73,9 +74,10 @@ struct shci_ctx {
     // enumeration work items: chunks of rows of one alpha (beta) group
     DevBuf<int32_t> item_a_group, item_a_first, item_b_group, item_b_first;
     int64_t n_items_a = 0, n_items_b = 0;
-    DevBuf<int64_t> cnt_b;                 // entries of the beta-grouped part of each row
+    DevBuf<int64_t> cnt_b;                 // entries of the beta-grouped part of each row (build scratch)
 
-    // stored H, both triangles, diagonal separate
+    // stored H, both triangles, diagonal separate; after an incremental
+    // update a row holds its old elements first, then the new ones
     DevBuf<int64_t> rowptr;
     DevBuf<int32_t> col;
     DevBuf<double> val;
@@ -112,6 +114,7 @@ namespace shci {
 // integrals.cu / build.cu
 void load_integrals(shci_ctx *c, int n_orb, double e_core, const double *h, const double *eri, int mem);
 void build(shci_ctx *c, int n_alpha, int n_beta, int64_t n_det, const uint64_t *dets, int mem, int mode);
+void extend(shci_ctx *c, int64_t n_new, const uint64_t *new_dets, int mem, double full_fraction);
 void export_pairs(shci_ctx *c, int64_t cap, int64_t *i_out, int64_t *j_out, double *v_out, int64_t *n_out);
 
 // sigma.cu: y = H x for k vectors; `inter` selects the interleaved [n][k]

@@ -36,9 +36,11 @@ inline EnumArgs enum_args(const shci_ctx *c) {
 template <int W, int MODE, int K>
 void launch_enum(shci_ctx *c, EnumArgs A, const DevInts &I, bool alpha_part) {
     CUDA_TRY(cudaMemsetAsync(c->counter.p + 1, 0, sizeof(int), c->st));
-    A.item_group = alpha_part ? c->item_a_group.p : c->item_b_group.p;
-    A.item_first = alpha_part ? c->item_a_first.p : c->item_b_first.p;
-    A.n_items = alpha_part ? c->n_items_a : c->n_items_b;
+    if (!A.item_group) {                    // the context's items unless the caller gave its own
+        A.item_group = alpha_part ? c->item_a_group.p : c->item_b_group.p;
+        A.item_first = alpha_part ? c->item_a_first.p : c->item_b_first.p;
+        A.n_items = alpha_part ? c->n_items_a : c->n_items_b;
+    }
     const int blocks = c->n_sm * (2048 / ENUM_THREADS);
     if (alpha_part) k_enum_alpha<W, MODE, K><<<blocks, ENUM_THREADS, 0, c->st>>>(A, I);
     else k_enum_beta<W, MODE, K><<<blocks, ENUM_THREADS, 0, c->st>>>(A, I);

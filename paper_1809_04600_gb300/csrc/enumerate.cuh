@@ -27,7 +27,17 @@ constexpr int ENUM_THREADS = 32 * ENUM_NW;
 constexpr int ENUM_TILE = 1024;             // candidates staged per tile
 constexpr int ENUM_QCAP = 64;               // per-warp queue of found pairs
 
-enum { ENUM_COUNT = 0, ENUM_FILL = 1, ENUM_SIGMA = 2, ENUM_GRAD = 3 };
+// ENUM_COUNT_INC / ENUM_FILL_INC: count / fill for the incremental update
+// (rows from separate member lists and item ranges; with n_old > 0 the items
+// hold old rows only, which take only the new candidates)
+enum { ENUM_COUNT = 0, ENUM_FILL = 1, ENUM_SIGMA = 2, ENUM_GRAD = 3, ENUM_COUNT_INC = 4, ENUM_FILL_INC = 5 };
+
+template <int MODE>
+struct ModeOf {
+    static constexpr bool count = MODE == ENUM_COUNT || MODE == ENUM_COUNT_INC;
+    static constexpr bool fill = MODE == ENUM_FILL || MODE == ENUM_FILL_INC;
+    static constexpr bool inc = MODE == ENUM_COUNT_INC || MODE == ENUM_FILL_INC;
+};
 
 constexpr int GRAD_REPLICAS = 32;           // gradient copies that spread the atomics
 
@@ -46,6 +56,17 @@ struct EnumArgs {
     int opp_lookup;
     int opp_hybrid;
     float opp_factor;
+    // incremental update (ENUM_COUNT_INC / ENUM_FILL_INC only): the items'
+    // rows come from row_det / row_str (the groups with members in
+    // determinant order) and end at member offset item_end[item]; with
+    // n_old > 0 every row is old (< n_old) and takes only the new members of
+    // its candidate groups, from ga_new / gb_new (offset of each group's first
+    // new member) on, read directly by each warp
+    const int32_t *row_det;
+    const uint64_t *row_str;
+    const int32_t *item_end;
+    int64_t n_old;
+    const int64_t *ga_new, *gb_new;
     const int32_t *ib;                      // beta string index of each determinant
     const int64_t *bs_off;                  // beta singles
     const int32_t *bs_idx;
@@ -287,7 +308,7 @@ __device__ __forceinline__ void flush(RowAcc<MODE, K> &R, const EnumArgs &A, con
         for (int k = 0; k < W; k++) sj.w[k] = Q.s[lane * W + k];
         const int32_t j = Q.j[lane];
         const double v = eval_pair<W>(I, si, other, sj, Q.ctx[lane]);
-        if (MODE == ENUM_FILL) {
+        if (ModeOf<MODE>::fill) {
             A.col[R.pos + lane] = j;
             A.val[R.pos + lane] = v;
         } else if (MODE == ENUM_SIGMA) {
@@ -305,7 +326,7 @@ __device__ __forceinline__ void flush(RowAcc<MODE, K> &R, const EnumArgs &A, con
             }
         }
     }
-    if (MODE == ENUM_FILL) R.pos += cnt;
+    if (ModeOf<MODE>::fill) R.pos += cnt;
 }
 
 // Record this round's matches: count them, or queue them and evaluate full
@@ -318,7 +339,7 @@ __device__ __forceinline__ void emit(RowAcc<MODE, K> &R, const EnumArgs &A, cons
     const unsigned mask = __ballot_sync(0xffffffffu, match);
     const int nm = __popc(mask);
     R.found += nm;
-    if (MODE == ENUM_COUNT || nm == 0) return;
+    if (ModeOf<MODE>::count || nm == 0) return;
     if (match) {
         const int slot = R.qn + __popc(mask & ((1u << lane) - 1u));
         Q.j[slot] = j;
@@ -374,7 +395,7 @@ __device__ __forceinline__ void row_begin(RowAcc<MODE, K> &R, const EnumArgs &A,
     R.i = i;
 #pragma unroll
     for (int q = 0; q < (K > 0 ? K : 1); q++) R.acc[q] = 0.0;
-    if (MODE == ENUM_FILL && valid) R.pos = A.rowptr[i] + (A.part_off ? A.part_off[i] : 0);
+    if (ModeOf<MODE>::fill && valid) R.pos = A.rowptr[i] + (A.part_off ? A.part_off[i] : 0);
     if (MODE == ENUM_GRAD) R.ci = valid ? A.x[i] : 0.0;
 }
 
@@ -382,7 +403,7 @@ template <int W, int MODE, int K>
 __device__ __forceinline__ void row_end(RowAcc<MODE, K> &R, const EnumArgs &A, const DevInts &I, WarpQueue<W> &Q,
                                         const Str<W> &si, const Str<W> &other, int64_t i, bool valid) {
     const int lane = threadIdx.x & 31;
-    if (MODE != ENUM_COUNT && R.qn > 0) {
+    if (!ModeOf<MODE>::count && R.qn > 0) {
         flush<W, MODE, K>(R, A, I, Q, si, other, R.qn);
         R.qn = 0;
         __syncwarp();
@@ -405,12 +426,39 @@ __device__ __forceinline__ void row_end(RowAcc<MODE, K> &R, const EnumArgs &A, c
                 else A.y[xi] = fma(A.diag[i], __ldcg(&A.x[xi]), R.acc[q]);
             }
         }
-    } else if (MODE == ENUM_COUNT) {
+    } else if (ModeOf<MODE>::count) {
         if (valid && lane == 0) A.cnt[i] = R.found;
     }
 }
 
 // ---------------------------------------------------------------- kernels
+
+// Incremental update, old rows (Sec. III, Algorithms 1 and 2: row i takes only
+// candidates j >= s, the first new determinant): the same-spin single and
+// double excitations among the new members of the row's own group,
+// [m_beg, m_end) of the determinant-ordered member lists, screened by this
+// warp alone (read directly; they are few).
+template <int W, int MODE, int K>
+__device__ __forceinline__ void old_row_suffix(RowAcc<MODE, K> &R, const EnumArgs &A, const DevInts &I,
+                                               WarpQueue<W> &Q, const Str<W> &si, const Str<W> &other,
+                                               const uint64_t *mstr, const int32_t *mdet, int64_t m_beg,
+                                               int64_t m_end, unsigned long long &cand_local) {
+    const int lane = threadIdx.x & 31;
+    cand_local += lane == 0 ? (unsigned long long)(m_end - m_beg) : 0ull;
+    for (int64_t m0 = m_beg; m0 < m_end; m0 += 32) {
+        const int64_t m = m0 + lane;
+        bool match = false;
+        int32_t j = 0;
+        Str<W> sj{};
+        if (m < m_end) {
+            sj = load_str<W>(mstr, m);
+            const int d = xor_popc<W>(si, sj);
+            match = (d == 2) | (d == 4);
+            if (match) j = __ldg(&mdet[m]);
+        }
+        emit<W, MODE, K>(R, A, I, Q, si, other, match, j, sj, 0);
+    }
+}
 
 // Rows grouped by alpha string: same-spin beta excitations (candidates in the
 // row's own alpha group) and opposite-spin doubles (candidates in the alpha
@@ -420,17 +468,79 @@ template <int W, int MODE, int K>
 __device__ __forceinline__ void enum_alpha_item(const EnumArgs &A, const DevInts &I, int64_t item, Tile<W> &T,
                                                 WarpQueue<W> &Q, unsigned long long &cand_local, int k_active = 0) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    constexpr bool NEED_DET = MODE != ENUM_COUNT;
+    constexpr bool NEED_DET = !ModeOf<MODE>::count;
+    constexpr bool XM = ModeOf<MODE>::inc;
     const int a = A.item_group[item];
     const int64_t g_beg = A.ga_off[a], g_len = A.ga_off[a + 1] - g_beg;
+    const int32_t *rdet = XM ? A.row_det : A.ga_det;
+    const uint64_t *rstr = XM ? A.row_str : A.ga_str;
     const int64_t r = A.item_first[item] + warp;            // this warp's member
-    const bool valid = r < g_len;
-    const int64_t i = valid ? A.ga_det[g_beg + r] : 0;
+    const bool valid = r < (XM ? (int64_t)A.item_end[item] : g_len);
+    const int64_t i = valid ? rdet[g_beg + r] : 0;
     const Str<W> Ai = load_str<W>(A.astr, a);
-    const Str<W> Bi = valid ? load_str<W>(A.ga_str, g_beg + r) : Str<W>{};
+    const Str<W> Bi = valid ? load_str<W>(rstr, g_beg + r) : Str<W>{};
     RowAcc<MODE, K> R;
     row_begin(R, A, i, valid);
     R.ka = k_active ? k_active : (A.k_active ? A.k_active : K);
+    if (XM && A.n_old > 0) {
+        // old rows: the new members of the own group (same-spin beta
+        // excitations) and of the groups of the alpha singles of a
+        // (opposite-spin doubles), by this warp alone
+        if (valid) {
+            const int64_t n_beg = A.ga_new[a];
+            old_row_suffix<W, MODE, K>(R, A, I, Q, Bi, Ai, A.ga_str, A.ga_det, n_beg, g_beg + g_len, cand_local);
+            const int64_t s_beg = A.as_off[a], s_end = A.as_off[a + 1];
+            for (int64_t s0 = s_beg; s0 < s_end; s0 += 32) {
+                // one alpha single per lane: its group's new members and pair context
+                int64_t kb = 0;
+                int len = 0, ctxl = 1;
+                if (s0 + lane < s_end) {
+                    const int k = A.as_idx[s0 + lane];
+                    kb = A.ga_new[k];
+                    len = (int)(A.ga_off[k + 1] - kb);
+                    if (!ModeOf<MODE>::count && len > 0) {
+                        int pq_a, neg_a;
+                        move_info<W>(Ai, load_str<W>(A.astr, k), pq_a, neg_a);
+                        ctxl = (pq_a << 2) | ((neg_a & 1) << 1) | 1;
+                    }
+                }
+                int incl = len;                         // inclusive prefix over the lanes
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                const int total = __shfl_sync(0xffffffffu, incl, 31);
+                cand_local += lane == 0 ? (unsigned long long)total : 0ull;
+                for (int t0 = 0; t0 < total; t0 += 32) {
+                    const int t = t0 + lane;
+                    // the lane q whose range holds candidate t: the first with incl > t
+                    int q = 0;
+#pragma unroll
+                    for (int step = 16; step >= 1; step >>= 1) {
+                        const int v = __shfl_sync(0xffffffffu, incl, q + step - 1);
+                        if (v <= t) q += step;
+                    }
+                    q = min(q, 31);
+                    const int64_t kq = __shfl_sync(0xffffffffu, kb, q);
+                    const int before = __shfl_sync(0xffffffffu, incl - len, q);
+                    const int cq = __shfl_sync(0xffffffffu, ctxl, q);
+                    bool match = false;
+                    int32_t j = 0;
+                    Str<W> Bj{};
+                    if (t < total) {
+                        const int64_t m = kq + (t - before);
+                        Bj = load_str<W>(A.ga_str, m);
+                        match = xor_popc<W>(Bi, Bj) == 2;
+                        if (match) j = __ldg(&A.ga_det[m]);
+                    }
+                    emit<W, MODE, K>(R, A, I, Q, Bi, Ai, match, j, Bj, cq);
+                }
+            }
+        }
+        row_end<W, MODE, K>(R, A, I, Q, Bi, Ai, i, valid);
+        return;
+    }
     // same-spin beta: candidates with the same alpha string
     for (int64_t t0 = 0; t0 < g_len; t0 += ENUM_TILE) {
         const int cnt = (int)min((int64_t)ENUM_TILE, g_len - t0);
@@ -482,7 +592,7 @@ __device__ __forceinline__ void enum_alpha_item(const EnumArgs &A, const DevInts
         const int k = A.as_idx[s];
         const int64_t k_beg = A.ga_off[k], k_len = A.ga_off[k + 1] - k_beg;
         int ctx = 1;
-        if (MODE != ENUM_COUNT) {
+        if (!ModeOf<MODE>::count) {
             int pq_a, neg_a;
             move_info<W>(Ai, load_str<W>(A.astr, k), pq_a, neg_a);
             ctx = (pq_a << 2) | ((neg_a & 1) << 1) | 1;
@@ -562,17 +672,28 @@ template <int W, int MODE, int K>
 __device__ __forceinline__ void enum_beta_item(const EnumArgs &A, const DevInts &I, int64_t item, Tile<W> &T,
                                                WarpQueue<W> &Q, unsigned long long &cand_local, int k_active = 0) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    constexpr bool NEED_DET = MODE != ENUM_COUNT;
+    constexpr bool NEED_DET = !ModeOf<MODE>::count;
+    constexpr bool XM = ModeOf<MODE>::inc;
     const int b = A.item_group[item];
     const int64_t g_beg = A.gb_off[b], g_len = A.gb_off[b + 1] - g_beg;
+    const int32_t *rdet = XM ? A.row_det : A.gb_det;
+    const uint64_t *rstr = XM ? A.row_str : A.gb_str;
     const int64_t r = A.item_first[item] + warp;
-    const bool valid = r < g_len;
-    const int64_t i = valid ? A.gb_det[g_beg + r] : 0;
+    const bool valid = r < (XM ? (int64_t)A.item_end[item] : g_len);
+    const int64_t i = valid ? rdet[g_beg + r] : 0;
     const Str<W> Bi = load_str<W>(A.bstr, b);
-    const Str<W> Ai = valid ? load_str<W>(A.gb_str, g_beg + r) : Str<W>{};
+    const Str<W> Ai = valid ? load_str<W>(rstr, g_beg + r) : Str<W>{};
     RowAcc<MODE, K> R;
     row_begin(R, A, i, valid);
     R.ka = k_active ? k_active : (A.k_active ? A.k_active : K);
+    if (XM && A.n_old > 0) {
+        // old rows: the new members of the own beta group (same-spin alpha excitations)
+        if (valid)
+            old_row_suffix<W, MODE, K>(R, A, I, Q, Ai, Bi, A.gb_str, A.gb_det, A.gb_new[b], g_beg + g_len,
+                                       cand_local);
+        row_end<W, MODE, K>(R, A, I, Q, Ai, Bi, i, valid);
+        return;
+    }
     for (int64_t t0 = 0; t0 < g_len; t0 += ENUM_TILE) {
         const int cnt = (int)min((int64_t)ENUM_TILE, g_len - t0);
         stage<W, NEED_DET>(T, A.gb_str, A.gb_det, g_beg + t0, cnt);
@@ -616,7 +737,7 @@ __global__ void __launch_bounds__(ENUM_THREADS) k_enum_alpha(EnumArgs A, DevInts
         if (item >= A.n_items) break;
         enum_alpha_item<W, MODE, K>(A, I, item, S.T, S.Q[threadIdx.x >> 5], cand_local);
     }
-    if (MODE == ENUM_COUNT && (threadIdx.x & 31) == 0 && cand_local) atomicAdd(A.cand, cand_local);
+    if (ModeOf<MODE>::count && (threadIdx.x & 31) == 0 && cand_local) atomicAdd(A.cand, cand_local);
 }
 
 template <int W, int MODE, int K>
@@ -632,7 +753,7 @@ __global__ void __launch_bounds__(ENUM_THREADS) k_enum_beta(EnumArgs A, DevInts 
         if (item >= A.n_items) break;
         enum_beta_item<W, MODE, K>(A, I, item, S.T, S.Q[threadIdx.x >> 5], cand_local);
     }
-    if (MODE == ENUM_COUNT && (threadIdx.x & 31) == 0 && cand_local) atomicAdd(A.cand, cand_local);
+    if (ModeOf<MODE>::count && (threadIdx.x & 31) == 0 && cand_local) atomicAdd(A.cand, cand_local);
 }
 
 // work items: one per chunk of ENUM_NW members of each group
@@ -648,6 +769,31 @@ static __global__ void k_items_fill(const int64_t *__restrict__ off, const int64
         for (int64_t t = 0; t < c; t++) {
             item_group[start[g] + t] = (int32_t)g;
             item_first[start[g] + t] = (int32_t)(t * ENUM_NW);
+        }
+    }
+}
+
+// incremental update: items over one part of each determinant-ordered group,
+// the old members [0, g_new - off) (part 0) or the new ones (part 1)
+static __global__ void k_items_count_part(const int64_t *__restrict__ off, const int64_t *__restrict__ g_new,
+                                          int64_t n_groups, int part, int64_t *__restrict__ cnt) {
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n_groups; g += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t m = part ? off[g + 1] - g_new[g] : g_new[g] - off[g];
+        cnt[g] = (m + ENUM_NW - 1) / ENUM_NW;
+    }
+}
+
+static __global__ void k_items_fill_part(const int64_t *__restrict__ off, const int64_t *__restrict__ g_new,
+                                         const int64_t *__restrict__ start, int64_t n_groups, int part,
+                                         int32_t *__restrict__ item_group, int32_t *__restrict__ item_first,
+                                         int32_t *__restrict__ item_end) {
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n_groups; g += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t lo = part ? g_new[g] - off[g] : 0, hi = part ? off[g + 1] - off[g] : g_new[g] - off[g];
+        const int64_t c = (hi - lo + ENUM_NW - 1) / ENUM_NW;
+        for (int64_t t = 0; t < c; t++) {
+            item_group[start[g] + t] = (int32_t)g;
+            item_first[start[g] + t] = (int32_t)(lo + t * ENUM_NW);
+            item_end[start[g] + t] = (int32_t)hi;
         }
     }
 }
