@@ -720,6 +720,9 @@ def run_extend(args):
                 ms.append(st["extend_ms"])
             line[arm + "_ms"] = float(np.median(ms))
             line[arm + "_candidates"] = st["candidates"]
+            if arm == "incremental":
+                line["incremental_phase_ms"] = dict(zip(("lists", "count", "alloc_copy", "fill_release"),
+                                                        st["extend_phase_ms"]))
         line["speedup"] = line["rebuild_ms"] / line["incremental_ms"]
         # rows of the incrementally grown matrix (old and new) against the oracle
         rng = np.random.default_rng(int(f * 1000))

@@ -384,6 +384,12 @@ typedef struct {
     double extend_ms;           /* last shci_extend_connectivity, device time */
     int extend_incremental;     /* last shci_extend_connectivity: 1 incremental, 0 rebuilt */
     int64_t extend_n_old;       /* last shci_extend_connectivity: determinants before it */
+    /* last incremental shci_extend_connectivity, device-timeline time per part:
+     * 0 lists (helper lists of the grown V, determinant-ordered groups, work
+     * items), 1 count (new elements per row, row offsets), 2 copy (the grown
+     * matrix's allocation and the old rows' copy), 3 fill (new elements and
+     * the release of the old matrix); zeros after a rebuild */
+    double extend_phase_ms[4];
 } shci_stats_t;
 
 /* Fill *out.  Kernel times are recorded only while timing is enabled. */

@@ -58,6 +58,7 @@ class shci_stats_t(ctypes.Structure):
         ("select_ms", ctypes.c_double), ("select_candidates", ctypes.c_int64),
         ("pt2_ms", ctypes.c_double), ("pt2_batches", ctypes.c_int), ("pt2_terms", ctypes.c_int64),
         ("extend_ms", ctypes.c_double), ("extend_incremental", ctypes.c_int), ("extend_n_old", ctypes.c_int64),
+        ("extend_phase_ms", ctypes.c_double * 4),
     ]
 
 
@@ -451,6 +452,7 @@ def shci_get_stats(ctx) -> dict:
     _check(ctx, load_library().shci_get_stats(ctx, ctypes.byref(s)))
     out = {name: getattr(s, name) for name, _ in shci_stats_t._fields_}
     out["davidson_phase_ms"] = list(s.davidson_phase_ms)
+    out["extend_phase_ms"] = list(s.extend_phase_ms)
     return out
 
 

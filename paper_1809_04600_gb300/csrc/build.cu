@@ -660,10 +660,34 @@ static void build_w(shci_ctx *c, int mode) {
 // only the new candidates, the suffixes of the determinant-ordered groups
 // (j >= s), each warp reading its row's suffixes directly.  The old rows are
 // copied into the grown matrix ahead of their new elements.
+// events on the context's stream marking the parts of an incremental update
+struct PhaseMarks {
+    cudaEvent_t e[5] = {};
+    explicit PhaseMarks(cudaStream_t st) : st_(st) {
+        for (auto &x : e) CUDA_TRY(cudaEventCreate(&x));
+    }
+    ~PhaseMarks() {
+        for (auto &x : e)
+            if (x) cudaEventDestroy(x);
+    }
+    void mark(int i) { CUDA_TRY(cudaEventRecord(e[i], st_)); }
+    // after the stream has been synchronised: milliseconds between marks
+    void read(double *ms, int parts) {
+        for (int i = 0; i < parts; i++) {
+            float t = 0.f;
+            cudaEventElapsedTime(&t, e[i], e[i + 1]);
+            ms[i] = t;
+        }
+    }
+    cudaStream_t st_;
+};
+
 template <int W>
 static void extend_w(shci_ctx *c, int64_t n_old) {
     cudaStream_t st = c->st;
     const int64_t n = c->n_det;
+    PhaseMarks pm(st);
+    pm.mark(0);
     lists_w<W>(c);
     DevInts I = dev_ints(c);
     DevBuf<int64_t> off_tmp, ga_new, gb_new;
@@ -690,6 +714,7 @@ static void extend_w(shci_ctx *c, int64_t n_old) {
     Ao.ga_new = ga_new.p;
     Ao.gb_new = gb_new.p;
 
+    pm.mark(1);
     // count pass: new elements of each row, beta-grouped and alpha-grouped
     DevBuf<unsigned long long> cand;
     cand.alloc(1);
@@ -719,6 +744,7 @@ static void extend_w(shci_ctx *c, int64_t n_old) {
     CUDA_TRY(cudaMemcpyAsync(&ncand, cand.p, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));
     c->candidates = (int64_t)ncand;
+    pm.mark(2);
     // a stored matrix stays stored unless SHCI_AUTO finds no room for the grown one
     int mode = c->mode;
     if (mode == SHCI_STORED && c->mode_req == SHCI_AUTO) mode = decide_mode(c, SHCI_AUTO, nnz);
@@ -731,6 +757,7 @@ static void extend_w(shci_ctx *c, int64_t n_old) {
         k_copy_rows<<<gw, 256, 0, st>>>(c->rowptr.p, c->col.p, c->val.p, n_old, rowptr.p, col.p, val.p);
         KERNEL_CHECK();
         LAUNCHED(1);
+        pm.mark(3);
         for (EnumArgs *E : {&An, &Ao}) {
             E->rowptr = rowptr.p;
             E->col = col.p;
@@ -745,14 +772,17 @@ static void extend_w(shci_ctx *c, int64_t n_old) {
         c->col.swap(col);
         c->val.swap(val);
     } else {
+        pm.mark(3);
         c->col.reset();
         c->val.reset();
     }
+    pm.mark(4);
     c->mode = mode;
     c->rowptr.swap(rowptr);
     c->nnz_full = nnz;
     c->nnz_upper = nnz / 2;
     CUDA_TRY(cudaStreamSynchronize(st));
+    pm.read(c->stats.extend_phase_ms, 4);
 }
 
 void extend(shci_ctx *c, int64_t n_new, const uint64_t *new_dets, int mem, double full_fraction) {
@@ -798,6 +828,8 @@ void extend(shci_ctx *c, int64_t n_new, const uint64_t *new_dets, int mem, doubl
     cudaEventDestroy(e1);
     c->stats.extend_ms = ms;
     c->stats.extend_incremental = incremental ? 1 : 0;
+    if (!incremental)
+        for (double &x : c->stats.extend_phase_ms) x = 0.0;
     c->stats.extend_n_old = n_old;
     c->built = true;
 }

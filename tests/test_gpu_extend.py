@@ -85,6 +85,8 @@ def test_incremental_steps_match_oracle_and_full_build(P, oracle_mod, name, n_de
         st = B.stats()
         assert st["extend_incremental"] == 1 and st["extend_n_old"] == a and st["n_det"] == b
         assert st["extend_ms"] > 0.0
+        ph = st["extend_phase_ms"]
+        assert min(ph) >= 0.0 and ph[0] > 0.0 and sum(ph) <= st["extend_ms"] * (1 + 1e-6) + 1e-3
     _check_against_oracle(P, oracle_mod, B, h, eri, ec)
     _same_as_full_build(P, B, h, eri, ec, cfg.n_alpha, cfg.n_beta)
     B.close()
@@ -117,7 +119,7 @@ def test_threshold_switches_to_full_build(P, oracle_mod):
     cfg, h, eri, ec, dets = G.system("sel_24o_6a6b_1m", 3000)
     B = G.Built(P, h, eri, ec, dets[:2000], cfg.n_alpha, cfg.n_beta)
     _extend(P, B, dets[2000:], full_fraction=0.2)               # 1000 new of 3000: rebuilt
-    assert B.stats()["extend_incremental"] == 0
+    assert B.stats()["extend_incremental"] == 0 and B.stats()["extend_phase_ms"] == [0.0] * 4
     _check_against_oracle(P, oracle_mod, B, h, eri, ec)
     B.close()
     B = G.Built(P, h, eri, ec, dets[:2000], cfg.n_alpha, cfg.n_beta)
