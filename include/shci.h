@@ -114,11 +114,13 @@ int shci_build_connectivity(shci_ctx *ctx, int n_alpha, int n_beta, int64_t n_de
  * switch between the two list orders sits at 20 %; full_fraction <= 0 takes
  * 0.2.  The mode of the last build is kept (SHCI_AUTO re-decides against the
  * memory left); SHCI_ON_THE_FLY contexts get the count only.  n_new = 0 is a
- * no-op.  On any error the context is left unbuilt (SHCI_ERR_STATE until the
- * next shci_build_connectivity).  *nnz_upper_out (may be NULL) as for
- * shci_build_connectivity.  SHCI_ERR_STATE without a completed build;
- * SHCI_ERR_INVALID for n_new < 0, a NULL pointer with n_new > 0 or
- * n_old + n_new > 2^31 - 1. */
+ * no-op.  *nnz_upper_out (may be NULL) as for shci_build_connectivity.
+ * SHCI_ERR_STATE without a completed build; SHCI_ERR_INVALID, with the
+ * context unchanged, for an unknown mem_space, n_new < 0, a NULL pointer with
+ * n_new > 0 or n_old + n_new > 2^31 - 1.  Any later error (SHCI_ERR_INVALID
+ * for a determinant with the wrong electron count or already in V, out of
+ * memory, a CUDA error) leaves the context unbuilt: SHCI_ERR_STATE from the
+ * calls that need a build until the next shci_build_connectivity. */
 int shci_extend_connectivity(shci_ctx *ctx, int64_t n_new, const uint64_t *new_dets, int mem_space,
                              double full_fraction, int64_t *nnz_upper_out);
 

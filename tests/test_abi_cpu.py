@@ -52,3 +52,4 @@ def test_no_device_fails_cleanly(lib):
     # null context is rejected without touching a device
     L = binding.load_library()
     assert L.shci_sigma(None, 1, None, None, 0) == binding.SHCI_ERR_INVALID
+    assert L.shci_extend_connectivity(None, 1, None, 0, 0.2, None) == binding.SHCI_ERR_INVALID
