@@ -102,6 +102,12 @@ def _load():
         lib.oracle_pt2_sample.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, _f64p, _f64p,
                                           ctypes.c_int64, _u64p, _f64p, ctypes.c_double, ctypes.c_double,
                                           ctypes.c_double, ctypes.c_int64, ctypes.c_int64, _i64p, _i64p, _f64p]
+        lib.oracle_upper_csr.restype = ctypes.c_int64
+        lib.oracle_upper_csr.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, _f64p, _f64p, ctypes.c_int64,
+                                         _u64p, _i64p, _i32p, _f64p]
+        lib.oracle_sigma_upper.restype = None
+        lib.oracle_sigma_upper.argtypes = [ctypes.c_int64, _i64p, _i32p, _f64p, _f64p, ctypes.c_int, _f64p,
+                                           _f64p]
         lib.oracle_num_threads.restype = ctypes.c_int
         lib.oracle_num_threads.argtypes = []
         _lib = lib
@@ -250,6 +256,23 @@ class System:
         ii, jj = pairs_allpairs(dets)
         return ii, jj, self.hij_list(dets, ii, jj)
 
+    def upper_csr(self, dets):
+        """The upper triangle of H on V as compressed rows (rowptr int64 [n+1],
+        col int32, val f64; row i holds its connected j > i ascending), by brute
+        force (a) -- 12 bytes per connected pair, for spaces of ~1e6."""
+        dets = _u64(dets)
+        n = dets.shape[0]
+        if n >= 2 ** 31:
+            raise ValueError("upper_csr: n_det must be below 2^31")
+        lib = _load()
+        rowptr = np.empty(n + 1, np.int64)
+        args = (self.n, n_words(dets), self.e_core, _p(self.h, _f64p), _p(self.eri, _f64p), n, _p(dets, _u64p))
+        total = lib.oracle_upper_csr(*args, _p(rowptr, _i64p), None, None)
+        col = np.empty(max(total, 1), np.int32)
+        val = np.empty(max(total, 1))
+        lib.oracle_upper_csr(*args, _p(rowptr, _i64p), _p(col, _i32p), _p(val, _f64p))
+        return rowptr, col[:total], val[:total]
+
     def sparse_h(self, dets):
         """scipy CSR of the full symmetric H on V (assembled from the oracle's pairs)."""
         import scipy.sparse as sp
@@ -271,14 +294,15 @@ class System:
         return H
 
     # ---------------------------------------------------------- eigenpairs
-    def lowest_eigenpairs(self, dets, k=1, tol=1e-10, dense_max=6000):
-        """(E[k], C[k, n]) lowest roots of H on V."""
+    def lowest_eigenpairs(self, dets, k=1, tol=1e-10, dense_max=6000, res_tol=1e-7, guess=None):
+        """(E[k], C[k, n]) lowest roots of H on V: a dense eigensolver up to
+        dense_max determinants, else Davidson on the upper-triangle rows."""
         n = dets.shape[0]
         if n <= dense_max:
             w, v = np.linalg.eigh(self.dense_h(dets))
             return w[:k].copy(), np.ascontiguousarray(v[:, :k].T)
-        H = self.sparse_h(dets)
-        return davidson(H.dot, H.diagonal(), k, tol=tol)
+        op = UpperMatrix(*self.upper_csr(dets), self.hdiag(dets))
+        return davidson(op.matvec, op.diag, k, tol=tol, res_tol=res_tol, guess=guess)
 
     # ---------------------------------------------------------- gradients
     def energy_gradient(self, dets, c):
@@ -332,12 +356,36 @@ def sigma_pairs(n_det, ii, jj, hij, diag, c):
     return out
 
 
+class UpperMatrix:
+    """H from its upper-triangle rows (System.upper_csr) and its diagonal."""
+
+    def __init__(self, rowptr, col, val, diag):
+        self.rowptr, self.col, self.val = _i64(rowptr), np.ascontiguousarray(col, np.int32), _f64(val)
+        self.diag = _f64(diag)
+        self.n = self.diag.size
+
+    @property
+    def nnz_upper(self) -> int:
+        return int(self.rowptr[-1])
+
+    def matvec(self, x):
+        """H x for x [n] or [k, n] (vectors as rows)."""
+        x = _f64(x)
+        one = x.ndim == 1
+        c = np.atleast_2d(x)
+        out = np.empty_like(c)
+        _load().oracle_sigma_upper(self.n, _p(self.rowptr, _i64p), _p(self.col, _i32p), _p(self.val, _f64p),
+                                   _p(self.diag, _f64p), c.shape[0], _p(c, _f64p), _p(out, _f64p))
+        return out[0] if one else out
+
+
 # ------------------------------------------------------------ Davidson
 
-def davidson(matvec, diag, k=1, tol=1e-10, res_tol=1e-7, max_iter=400, max_sub=None):
+def davidson(matvec, diag, k=1, tol=1e-10, res_tol=1e-7, max_iter=400, max_sub=None, guess=None):
     """Diagonally preconditioned Davidson for the k lowest roots (Sec. II.A).
 
-    Start from the unit vectors of the k lowest diagonal entries; each step
+    Start from the unit vectors of the k lowest diagonal entries (or from the
+    rows of ``guess`` [k, n], orthonormalised); each step
     projects H on the subspace, takes the lowest k Ritz pairs, forms residuals
     r = H x - theta x, preconditions them by (theta - H_ii)^-1 and adds the
     orthonormalised corrections.  Stops when every root moved by less than
@@ -345,11 +393,14 @@ def davidson(matvec, diag, k=1, tol=1e-10, res_tol=1e-7, max_iter=400, max_sub=N
     """
     n = diag.size
     max_sub = max_sub or max(8 * k, 24)
-    V = np.zeros((n, 0))
-    for idx in np.argsort(diag, kind="stable")[:k]:
-        e = np.zeros(n)
-        e[idx] = 1.0
-        V = np.column_stack([V, e])
+    if guess is not None:
+        V, _ = np.linalg.qr(np.asarray(guess, dtype=np.float64).reshape(k, n).T)
+    else:
+        V = np.zeros((n, 0))
+        for idx in np.argsort(diag, kind="stable")[:k]:
+            e = np.zeros(n)
+            e[idx] = 1.0
+            V = np.column_stack([V, e])
     AV = np.column_stack([matvec(V[:, a]) for a in range(V.shape[1])])
     theta_old = np.full(k, np.inf)
     for _ in range(max_iter):

@@ -455,6 +455,108 @@ void oracle_sigma_pairs(int64_t n_det, int64_t m, const int64_t *ii, const int64
     free(acc);
 }
 
+/*
+ * The upper triangle of H (Sec. III: elements nonzero only within a double
+ * excitation) as compressed rows: row i holds the connected j > i in
+ * ascending order, found by brute force (a) over all pairs, with H_ij from the
+ * Slater-Condon rules.  With col == NULL, rowptr[0 .. n_det] receives the row
+ * offsets (rowptr[0] = 0) and the call returns the total; otherwise rowptr
+ * must hold those offsets and col (int32) / val are filled.  Needs
+ * n_det < 2^31.
+ */
+int64_t oracle_upper_csr(int n, int W, double e_core, const double *h, const double *eri, int64_t n_det,
+                         const uint64_t *dets, int64_t *rowptr, int32_t *col, double *val)
+{
+    oints I = {n, W, e_core, h, eri};
+    if (!col) {
+        rowptr[0] = 0;
+#pragma omp parallel for schedule(dynamic, 64)
+        for (int64_t i = 0; i < n_det; i++) {
+            int64_t cnt = 0;
+            for (int64_t j = i + 1; j < n_det; j++) {
+                int d = exc_degree2(W, dets + i * 2 * W, dets + j * 2 * W);
+                if (d == 2 || d == 4) cnt++;
+            }
+            rowptr[i + 1] = cnt;
+        }
+        for (int64_t i = 0; i < n_det; i++) rowptr[i + 1] += rowptr[i];
+        return rowptr[n_det];
+    }
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < n_det; i++) {
+        int64_t o = rowptr[i];
+        const uint64_t *di = dets + i * 2 * W;
+        for (int64_t j = i + 1; j < n_det; j++) {
+            int d = exc_degree2(W, di, dets + j * 2 * W);
+            if (d == 2 || d == 4) {
+                col[o] = (int32_t)j;
+                val[o] = matrix_element(&I, di, dets + j * 2 * W);
+                o++;
+            }
+        }
+    }
+    return rowptr[n_det];
+}
+
+/*
+ * sigma = H c from the upper-triangle rows of oracle_upper_csr plus the
+ * diagonal: sigma_i = H_ii c_i + sum_{j>i} H_ij c_j + sum_{j<i} H_ji c_j
+ * (H symmetric).  c and out are [k][n_det].  Rows are shared out over threads
+ * in fixed contiguous blocks, each thread accumulating into its own copy of
+ * sigma; the copies are then added in thread order, so the result depends
+ * only on the number of threads.
+ */
+void oracle_sigma_upper(int64_t n_det, const int64_t *rowptr, const int32_t *col, const double *val,
+                        const double *diag, int k, const double *c, double *out)
+{
+    int nthr = 1;
+#ifdef _OPENMP
+    nthr = omp_get_max_threads();
+#endif
+    double *part = (double *)calloc((size_t)nthr * n_det * k, sizeof(double));
+#pragma omp parallel num_threads(nthr)
+    {
+        int me = 0, nt = 1;
+#ifdef _OPENMP
+        me = omp_get_thread_num();
+        nt = omp_get_num_threads();
+#endif
+        double *acc = part + (size_t)me * n_det * k;
+        /* blocks of equal pair counts */
+        const int64_t total = rowptr[n_det];
+        int64_t lo = 0, hi = n_det;
+        {
+            const int64_t want_lo = total * me / nt, want_hi = total * (me + 1) / nt;
+            int64_t a = 0, b = n_det;
+            while (a < b) { int64_t mid = (a + b) / 2; if (rowptr[mid] < want_lo) a = mid + 1; else b = mid; }
+            lo = a;
+            a = 0; b = n_det;
+            while (a < b) { int64_t mid = (a + b) / 2; if (rowptr[mid] < want_hi) a = mid + 1; else b = mid; }
+            hi = (me == nt - 1) ? n_det : a;
+        }
+        for (int64_t i = lo; i < hi; i++) {
+            for (int v = 0; v < k; v++) {
+                const double *cv = c + (int64_t)v * n_det;
+                double *av = acc + (int64_t)v * n_det;
+                double si = 0.0;
+                for (int64_t e = rowptr[i]; e < rowptr[i + 1]; e++) {
+                    const int64_t j = col[e];
+                    si += val[e] * cv[j];
+                    av[j] += val[e] * cv[i];
+                }
+                av[i] += si;
+            }
+        }
+    }
+    for (int v = 0; v < k; v++)
+        for (int64_t i = 0; i < n_det; i++) {
+            double s = diag[i] * c[(int64_t)v * n_det + i];
+            for (int t = 0; t < nthr; t++) s += part[((size_t)t * k + v) * n_det + i];
+            out[(int64_t)v * n_det + i] = s;
+        }
+    free(part);
+}
+
 /* ------------------------------------------------------------ density matrices */
 
 /*
@@ -580,6 +682,68 @@ static int cmp_det_desc_words(const void *a, const void *b)
  * product |H_ai| |c_i| over V of each; returns their number (which may exceed
  * cap: only cap rows are written), -1 on OOM, -2 on duplicate determinants.
  */
+/* Append to buf (records of R = 2W + 1 words, grown by doubling) every
+ * determinant outside V that one single or double excitation of d reaches
+ * with |H_ad| * ci >= eps1, followed by the bits of that product.  Returns 0,
+ * or -1 on OOM. */
+static int select_from(const oints *I, const dtable *t, const uint64_t *d, double ci, double eps1,
+                       uint64_t **buf, int64_t *m, int64_t *mcap)
+{
+    const int W2 = 2 * I->W, nso = 2 * I->n, R = 2 * I->W + 1;
+    uint64_t x[8];
+    for (int q = 0; q < nso; q++) {
+        if (!occ(I, d, q)) continue;
+        for (int pass = 0; pass < 2; pass++) {
+            /* pass 0: singles q -> p; pass 1: doubles {q, s} -> {p, r} */
+            for (int s = (pass ? q + 1 : nso); s < (pass ? nso : nso + 1); s++) {
+                if (pass && !occ(I, d, s)) continue;
+                for (int p = 0; p < nso; p++) {
+                    if (occ(I, d, p)) continue;
+                    for (int r = (pass ? p + 1 : nso); r < (pass ? nso : nso + 1); r++) {
+                        if (pass && occ(I, d, r)) continue;
+                        if (!pass && so_spin(I, p) != so_spin(I, q)) continue;
+                        if (pass && so_spin(I, q) + so_spin(I, s) != so_spin(I, p) + so_spin(I, r))
+                            continue;
+                        memcpy(x, d, 8 * W2);
+                        put(I, x, q, 0);
+                        put(I, x, p, 1);
+                        if (pass) { put(I, x, s, 0); put(I, x, r, 1); }
+                        if (dtable_find(t, x) >= 0) continue;          /* already in V */
+                        const double prod = fabs(matrix_element(I, x, d)) * ci;
+                        if (!(prod >= eps1)) continue;
+                        if (*m == *mcap) {
+                            int64_t nc = 2 * *mcap;
+                            uint64_t *nb = (uint64_t *)realloc(*buf, sizeof(uint64_t) * R * nc);
+                            if (!nb) return -1;
+                            *buf = nb;
+                            *mcap = nc;
+                        }
+                        memcpy(*buf + *m * R, x, 8 * W2);
+                        memcpy(*buf + *m * R + W2, &prod, 8);
+                        (*m)++;
+                    }
+                }
+            }
+        }
+    }
+    return 0;
+}
+
+/*
+ * The selection criterion of Sec. II.A (Eq. 2): a determinant D_a outside V is
+ * selected when some D_i in V has |H_ai c_i| >= eps1, c_i taken as the largest
+ * |coefficient| of D_i over the k given vectors c[k][n_det].  Brute force:
+ * every single and double excitation of every D_i is generated, its H_ai
+ * evaluated exactly (Slater-Condon, operator form) and the product compared in
+ * FP64 as |H_ai| * |c_i| >= eps1.  The selected determinants are written to
+ * out (cap rows of 2W words) sorted ascending (last stored word most
+ * significant) without repeats, and, when best is not NULL, the largest
+ * product |H_ai| |c_i| over V of each; returns their number (which may exceed
+ * cap: only cap rows are written), -1 on OOM, -2 on duplicate determinants.
+ * The determinants of V are shared out over threads, each collecting its own
+ * records; the records are then concatenated and sorted, so the result does
+ * not depend on the number of threads.
+ */
 int64_t oracle_select(int n, int W, double e_core, const double *h, const double *eri, int64_t n_det,
                       const uint64_t *dets, int k, const double *c, double eps1, int64_t cap, uint64_t *out,
                       double *best)
@@ -588,52 +752,53 @@ int64_t oracle_select(int n, int W, double e_core, const double *h, const double
     dtable t;
     int rc = dtable_init(&t, n_det, W, dets);
     if (rc) { free(t.slot); return rc; }
-    const int W2 = 2 * W, nso = 2 * n, R = 2 * W + 1;
-    int64_t m = 0, mcap = 1024;
-    uint64_t *buf = (uint64_t *)malloc(sizeof(uint64_t) * R * mcap);
-    if (!buf) { free(t.slot); return -1; }
-    uint64_t x[8];
-    for (int64_t i = 0; i < n_det; i++) {
-        const uint64_t *d = dets + i * W2;
-        double ci = 0.0;
-        for (int l = 0; l < k; l++) ci = fmax(ci, fabs(c[(int64_t)l * n_det + i]));
-        if (ci == 0.0) continue;
-        for (int q = 0; q < nso; q++) {
-            if (!occ(&I, d, q)) continue;
-            for (int pass = 0; pass < 2; pass++) {
-                /* pass 0: singles q -> p; pass 1: doubles {q, s} -> {p, r} */
-                for (int s = (pass ? q + 1 : nso); s < (pass ? nso : nso + 1); s++) {
-                    if (pass && !occ(&I, d, s)) continue;
-                    for (int p = 0; p < nso; p++) {
-                        if (occ(&I, d, p)) continue;
-                        for (int r = (pass ? p + 1 : nso); r < (pass ? nso : nso + 1); r++) {
-                            if (pass && occ(&I, d, r)) continue;
-                            if (!pass && so_spin(&I, p) != so_spin(&I, q)) continue;
-                            if (pass && so_spin(&I, q) + so_spin(&I, s) != so_spin(&I, p) + so_spin(&I, r))
-                                continue;
-                            memcpy(x, d, 8 * W2);
-                            put(&I, x, q, 0);
-                            put(&I, x, p, 1);
-                            if (pass) { put(&I, x, s, 0); put(&I, x, r, 1); }
-                            if (dtable_find(&t, x) >= 0) continue;          /* already in V */
-                            const double prod = fabs(matrix_element(&I, x, d)) * ci;
-                            if (!(prod >= eps1)) continue;
-                            if (m == mcap) {
-                                mcap *= 2;
-                                uint64_t *nb = (uint64_t *)realloc(buf, sizeof(uint64_t) * R * mcap);
-                                if (!nb) { free(buf); free(t.slot); return -1; }
-                                buf = nb;
-                            }
-                            memcpy(buf + m * R, x, 8 * W2);
-                            memcpy(buf + m * R + W2, &prod, 8);
-                            m++;
-                        }
-                    }
-                }
+    const int W2 = 2 * W, R = 2 * W + 1;
+    int nthr = 1;
+#ifdef _OPENMP
+    nthr = omp_get_max_threads();
+#endif
+    uint64_t **tbuf = (uint64_t **)calloc((size_t)nthr, sizeof(uint64_t *));
+    int64_t *tm = (int64_t *)calloc((size_t)nthr, sizeof(int64_t));
+    int64_t *tcap = (int64_t *)calloc((size_t)nthr, sizeof(int64_t));
+    int failed = 0;
+#pragma omp parallel num_threads(nthr)
+    {
+        int me = 0;
+#ifdef _OPENMP
+        me = omp_get_thread_num();
+#endif
+        tcap[me] = 1024;
+        tbuf[me] = (uint64_t *)malloc(sizeof(uint64_t) * R * tcap[me]);
+        if (!tbuf[me]) {
+#pragma omp atomic write
+            failed = 1;
+        }
+#pragma omp for schedule(dynamic, 8)
+        for (int64_t i = 0; i < n_det; i++) {
+            if (failed || !tbuf[me]) continue;
+            double ci = 0.0;
+            for (int l = 0; l < k; l++) ci = fmax(ci, fabs(c[(int64_t)l * n_det + i]));
+            if (ci == 0.0) continue;
+            if (select_from(&I, &t, dets + i * W2, ci, eps1, &tbuf[me], &tm[me], &tcap[me])) {
+#pragma omp atomic write
+                failed = 1;
             }
         }
     }
     free(t.slot);
+    int64_t m = 0;
+    for (int e = 0; e < nthr; e++) m += tm[e];
+    uint64_t *buf = failed ? NULL : (uint64_t *)malloc(sizeof(uint64_t) * R * (m > 0 ? m : 1));
+    if (buf) {
+        int64_t o = 0;
+        for (int e = 0; e < nthr; e++) {
+            memcpy(buf + o * R, tbuf[e], sizeof(uint64_t) * R * tm[e]);
+            o += tm[e];
+        }
+    }
+    for (int e = 0; e < nthr; e++) free(tbuf[e]);
+    free(tbuf); free(tm); free(tcap);
+    if (!buf) return -1;
     g_sel_words = W2;
     qsort(buf, (size_t)m, sizeof(uint64_t) * R, cmp_det_desc_words);
     int64_t u = 0;

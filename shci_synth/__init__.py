@@ -22,8 +22,11 @@ space sizes).  Their recipe is fixed here so that every run is reproducible.
 """
 from __future__ import annotations
 
+import hashlib
 import itertools
+import json
 import math
+import os
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -31,6 +34,7 @@ import numpy as np
 __all__ = [
     "n_words", "n_pair", "eri_len", "integrals", "strings_from_occ", "fci_dets",
     "selected_dets", "hf_dets", "random_vectors", "CONFIGS", "config", "make_system",
+    "colex_det_ranks", "load_selected_space", "selected_space_meta", "SPACES_DIR",
 ]
 
 
@@ -238,6 +242,66 @@ def selected_dets(n_orb: int, n_alpha: int, n_beta: int, orb_energy: np.ndarray,
     keys = [dets[:, c] for c in range(2 * w - 1, -1, -1)] + [score]
     order = np.lexsort(keys)
     return np.ascontiguousarray(dets[order])
+
+
+# ---------------------------------------------------------------- stored selected spaces
+# Heat-bath-selected spaces are written by tests/golden/make_selected_spaces.py
+# (which runs the selection with the CPU oracle) and read back here by both the
+# oracle's tests and the library's tests and benchmark.
+
+SPACES_DIR = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "tests", "golden")
+
+
+def _sorted_strings(n_orb: int, n_e: int) -> np.ndarray:
+    """Every one-word string of n_e electrons in n_orb orbitals, ascending as
+    integers: position k holds the string of colex rank k."""
+    if n_orb > 64:
+        raise ValueError("stored spaces hold one-word strings (n_orb <= 64)")
+    return np.sort(_all_strings(n_orb, n_e)[:, 0])
+
+
+def colex_det_ranks(dets: np.ndarray, n_orb: int, n_alpha: int, n_beta: int) -> np.ndarray:
+    """rank(beta) * C(n_orb, n_alpha) + rank(alpha) per determinant (colex
+    ranks, which order strings like their integer values)."""
+    ta, tb = _sorted_strings(n_orb, n_alpha), _sorted_strings(n_orb, n_beta)
+    ra = np.searchsorted(ta, dets[:, 0])
+    rb = np.searchsorted(tb, dets[:, 1])
+    if not (np.array_equal(ta[ra], dets[:, 0]) and np.array_equal(tb[rb], dets[:, 1])):
+        raise ValueError("determinant with a wrong electron count")
+    return rb.astype(np.uint64) * np.uint64(ta.size) + ra.astype(np.uint64)
+
+
+def selected_space_meta(name: str) -> dict:
+    with open(os.path.join(SPACES_DIR, name + ".json")) as f:
+        return json.load(f)
+
+
+def load_selected_space(name: str, check_hash: bool = True, n_det: int | None = None) -> np.ndarray:
+    """The stored heat-bath-selected space ``name`` as uint64 [n_det, 2] in
+    generation order (its first n_det determinants if given: the space of an
+    earlier selection stage plus part of the next block).  The decoded array's
+    SHA-256 is checked against the one recorded beside it."""
+    z = np.load(os.path.join(SPACES_DIR, name + ".npz"))
+    n_orb, na, nb = (int(x) for x in z["shape"])
+    ta, tb = _sorted_strings(n_orb, na), _sorted_strings(n_orb, nb)
+    parts = []
+    for b in range(z["blocks"].size):
+        planes = z["planes_%d" % b]
+        width = planes.shape[0]
+        gaps = np.ascontiguousarray(planes.T).view(np.uint32 if width == 4 else np.uint64).ravel()
+        first = z["first_%d" % b][0]
+        ranks = np.concatenate([[first], first + np.cumsum(gaps.astype(np.uint64), dtype=np.uint64)])
+        parts.append(ranks.astype(np.uint64))
+    ranks = np.concatenate(parts)
+    dets = np.empty((ranks.size, 2), np.uint64)
+    dets[:, 0] = ta[(ranks % np.uint64(ta.size)).astype(np.int64)]
+    dets[:, 1] = tb[(ranks // np.uint64(ta.size)).astype(np.int64)]
+    if check_hash:
+        want = selected_space_meta(name)["sha256"]
+        got = hashlib.sha256(dets.tobytes()).hexdigest()
+        if got != want:
+            raise ValueError("stored space %s: SHA-256 %s, expected %s" % (name, got, want))
+    return dets if n_det is None else np.ascontiguousarray(dets[:n_det])
 
 
 def random_vectors(n: int, k: int, seed: int) -> np.ndarray:

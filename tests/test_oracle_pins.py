@@ -65,6 +65,47 @@ def test_matrix_elements_match_second_quantised_h(oracle_mod, n, na, nb):
     assert not np.any(nz & ~mask)          # every nonzero element is a listed pair
 
 
+# ------------------------------------------------------------------ two-word strings (n_orb > 64)
+
+EMBED_AT = 62          # the small system's orbitals 0..3 become orbitals 62..65: both words of a string
+
+
+def embedded_two_word_system(n_big=76, n=4, na=2, nb=2, e_core=0.37, seed=151):
+    """A 4-orbital system placed at orbitals 62..65 of a 76-orbital space (all
+    other integrals zero, electrons only in those orbitals) and the small
+    system's Jordan-Wigner Hamiltonian on the same determinants.  The relative
+    order of the occupied orbitals is unchanged, so the signed elements must
+    be identical; strings straddle the word boundary at orbital 64."""
+    h4, eri4, _ = small_system(n, 5, seed)
+    g4 = jw.eri_full(eri4, n)
+    h = np.zeros((n_big, n_big))
+    h[EMBED_AT:EMBED_AT + n, EMBED_AT:EMBED_AT + n] = h4
+    eri = np.zeros(S.eri_len(n_big))
+    for p, q, r, s_ in itertools.product(range(n), repeat=4):
+        P, Q, R, Sx = (EMBED_AT + x for x in (p, q, r, s_))
+        a = max(P, Q) * (max(P, Q) + 1) // 2 + min(P, Q)
+        b = max(R, Sx) * (max(R, Sx) + 1) // 2 + min(R, Sx)
+        eri[max(a, b) * (max(a, b) + 1) // 2 + min(a, b)] = g4[p, q, r, s_]
+    small = S.fci_dets(n, na, nb)
+    occ = lambda w: [k for k in range(n) if (int(w) >> k) & 1]
+    big = np.concatenate([
+        S.strings_from_occ(np.array([[EMBED_AT + k for k in occ(d[0])] for d in small]), n_big),
+        S.strings_from_occ(np.array([[EMBED_AT + k for k in occ(d[1])] for d in small]), n_big)], axis=1)
+    straddle = lambda w0, w1: np.any((w0 != 0) & (w1 != 0))
+    assert big.shape[1] == 4 and straddle(big[:, 0], big[:, 1]) and straddle(big[:, 2], big[:, 3])
+    return h, eri, e_core, big, jw.projected(h4, eri4, small, e_core)
+
+
+def test_two_word_strings_match_embedded_small_system(oracle_mod):
+    """Orbitals >= 64 (the second word of a string, Sec. V.A's bit layout): the
+    oracle's signed H on the embedded determinants equals the small system's
+    Jordan-Wigner Hamiltonian entry by entry."""
+    h, eri, ec, dets, ref = embedded_two_word_system()
+    got = oracle_mod.System(h, eri, ec).dense_h(dets)
+    np.testing.assert_allclose(got, ref, atol=1e-12, rtol=0)
+    assert np.count_nonzero(np.abs(ref) > 1e-12) > dets.shape[0]
+
+
 # ------------------------------------------------------------------ hand signs
 
 def test_hand_worked_signs(oracle_mod):
@@ -191,6 +232,30 @@ def test_sigma_rows_and_pairs_match_dense(oracle_mod):
     np.testing.assert_allclose(vals, H[17, cols], atol=1e-15)
 
 
+def test_upper_rows_sigma_matches_dense(oracle_mod):
+    """The upper-triangle rows hold exactly the pairs of brute force (a), and
+    H x from them (with the diagonal) equals the dense matrix, whose entries
+    the Jordan-Wigner pin checks, for one and several vectors, one- and
+    two-word strings."""
+    cfg = S.config("sel_24o_6a6b_1m")
+    h, eri, ec, dets = S.make_system(cfg, n_det=2500)
+    cases = [(h, eri, ec, dets)]
+    hb, eb, ecb, db, _ = embedded_two_word_system()
+    cases.append((hb, eb, ecb, db))
+    for hh, ee, cc, dd in cases:
+        O = oracle_mod.System(hh, ee, cc)
+        rowptr, col, val = O.upper_csr(dd)
+        ii, jj = oracle_mod.pairs_allpairs(dd)
+        assert rowptr[-1] == ii.size
+        assert np.array_equal(np.repeat(np.arange(dd.shape[0]), np.diff(rowptr)), ii)
+        assert np.array_equal(col.astype(np.int64), jj)
+        op = oracle_mod.UpperMatrix(rowptr, col, val, O.hdiag(dd))
+        Hd = O.dense_h(dd)
+        x = S.random_vectors(dd.shape[0], 3, 8)
+        np.testing.assert_allclose(op.matvec(x), x @ Hd.T, atol=1e-11, rtol=0)
+        np.testing.assert_allclose(op.matvec(x[1]), Hd @ x[1], atol=1e-11, rtol=0)
+
+
 # ------------------------------------------------------------------ eigenpairs
 
 def test_davidson_matches_dense_and_arpack(oracle_mod):
@@ -209,6 +274,10 @@ def test_davidson_matches_dense_and_arpack(oracle_mod):
         r = H.dot(C[a]) - e[a] * C[a]
         assert np.linalg.norm(r) < 1e-7
     np.testing.assert_allclose(C @ C.T, np.eye(2), atol=1e-10)
+    # started from a guess (the route the selection loop takes), through the upper rows
+    guess = C + 1e-3 * S.random_vectors(dets.shape[0], 2, 9)
+    e2, _ = O.lowest_eigenpairs(dets, 2, tol=1e-12, dense_max=0, res_tol=1e-8, guess=guess)
+    np.testing.assert_allclose(e2, w, atol=1e-9)
 
 
 # ------------------------------------------------------------------ RDMs and gradients
@@ -249,6 +318,26 @@ def test_rdm_no_two_body_closed_form(oracle_mod):
     np.testing.assert_allclose(oracle_mod.rdm1_full(dets, c, n), ref, atol=1e-10)
 
 
+def test_packed_gradient_entries_equal_folded_rdm2(oracle_mod):
+    """Per-slot gradient entries (the symmetry orbit of each packed slot,
+    gathered from single Gamma entries) equal the fold of the full 2-RDM, which
+    the energy identity and the finite differences pin; every (p,q,r,s) is a
+    member of exactly one slot."""
+    n, na, nb = 5, 2, 2
+    h, eri, _ = small_system(n, 5, 41)
+    dets = S.fci_dets(n, na, nb)
+    O, E, c = _ground(oracle_mod, h, eri, 0.0, dets)
+    members = oracle_mod.slot_members(n)
+    assert sorted(members) == list(range(S.eri_len(n)))
+    assert sum(len(m) for m in members.values()) == n ** 4
+    slots = np.arange(S.eri_len(n))
+    got = oracle_mod.packed_gradient_entries(dets, c, n, slots, members)
+    want = oracle_mod.fold_rdm2_to_packed(oracle_mod.rdm2_full(dets, c, n), n)
+    np.testing.assert_allclose(got, want, atol=1e-13, rtol=0)
+    _, ge = O.energy_gradient(dets, c)
+    np.testing.assert_allclose(got, ge, atol=1e-13, rtol=0)
+
+
 def test_gradient_matches_central_differences(oracle_mod):
     n, na, nb = 5, 2, 2
     h, eri, _ = small_system(n, 5, 31)
@@ -281,12 +370,14 @@ MUTATIONS = {
                                "    int ph = 1;\n    put(I, d, so, 1);"),
     "diagonal exchange dropped": ("e += 0.5 * (eri_so(I, k, k, l, l) - eri_so(I, k, l, l, k));",
                                   "e += 0.5 * (eri_so(I, k, k, l, l));"),
+    "two-word index": ("spin * I->W + (p >> 6)", "spin + (p >> 6)"),
 }
 
 
 @pytest.mark.parametrize("name", sorted(MUTATIONS))
 def test_planted_mistake_is_caught(oracle_mod, tmp_path, name):
-    """A mistake planted in a copy of the oracle's C source must fail the JW pin."""
+    """A mistake planted in a copy of the oracle's C source must fail the JW pin
+    (one-word strings, or the 4-orbital system embedded across two words)."""
     src = open(os.path.join(os.path.dirname(oracle_mod.__file__), "shci_oracle.c")).read()
     old, new = MUTATIONS[name]
     assert old in src
@@ -299,18 +390,25 @@ def test_planted_mistake_is_caught(oracle_mod, tmp_path, name):
     u64p = ctypes.POINTER(ctypes.c_uint64)
     lib.oracle_hij.restype = ctypes.c_double
     lib.oracle_hij.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, f64p, f64p, u64p, u64p]
+
+    def worst(n, h, eri, ec, dets, ref):
+        W = dets.shape[1] // 2
+        got = np.empty_like(ref)
+        for i in range(dets.shape[0]):
+            for j in range(dets.shape[0]):
+                di = np.ascontiguousarray(dets[i])
+                dj = np.ascontiguousarray(dets[j])
+                got[i, j] = lib.oracle_hij(n, W, ec, h.ctypes.data_as(f64p), eri.ctypes.data_as(f64p),
+                                           di.ctypes.data_as(u64p), dj.ctypes.data_as(u64p))
+        return np.max(np.abs(got - ref))
+
     n, na, nb = 4, 2, 2
     h, eri, _ = small_system(n, 5, 140 + na)
     dets = S.fci_dets(n, na, nb)
-    ref = jw.projected(h, eri, dets, 0.0)
-    got = np.empty_like(ref)
-    for i in range(dets.shape[0]):
-        for j in range(dets.shape[0]):
-            di = np.ascontiguousarray(dets[i])
-            dj = np.ascontiguousarray(dets[j])
-            got[i, j] = lib.oracle_hij(n, 1, 0.0, h.ctypes.data_as(f64p), eri.ctypes.data_as(f64p),
-                                       di.ctypes.data_as(u64p), dj.ctypes.data_as(u64p))
-    assert np.max(np.abs(got - ref)) > 1e-6, "planted mistake was not detected"
+    err = worst(n, h, eri, 0.0, dets, jw.projected(h, eri, dets, 0.0))
+    hb, eb, ecb, db, refb = embedded_two_word_system()
+    err = max(err, worst(hb.shape[0], hb, eb, ecb, db, refb))
+    assert err > 1e-6, "planted mistake was not detected"
 
 
 # ---------------------------------------------------------------- heat-bath selection (Sec. II.A, Eq. 2)
