@@ -56,6 +56,28 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
+PEAK_KINDS = ("dfma", "dadd", "imad", "xor_popc", "atomic_add_f64_l2", "gather_8b_l2")
+
+
+def measure_peaks(device=0, which=PEAK_KINDS):
+    """Operations per second of the project's peak-rate microbenchmarks
+    (paper_1809_04600_gb300/measure/peaks.cu) on this GPU, now."""
+    import ctypes
+    from paper_1809_04600_gb300 import build_lib
+    lib = ctypes.CDLL(build_lib.build_peaks())
+    lib.shci_peak_rate.restype = ctypes.c_int
+    lib.shci_peak_rate.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                   ctypes.POINTER(ctypes.c_double)]
+    out = {}
+    for name in which:
+        rate, ms = ctypes.c_double(), ctypes.c_double()
+        rc = lib.shci_peak_rate(device, PEAK_KINDS.index(name), 4, ctypes.byref(rate), ctypes.byref(ms))
+        if rc != 0:
+            raise RuntimeError("peak microbenchmark %s failed with CUDA error %d" % (name, rc))
+        out[name] = rate.value
+    return out
+
+
 def replica_totals(dist, seconds, units, device="cpu"):
     """Whole-job figures of N independent replicas: the slowest rank's time and
     the units all ranks processed (value = units / time).  ``dist`` is
@@ -187,6 +209,7 @@ def run_ours(args):
 
     for _ in range(args.warmup):
         step()
+    peaks = measure_peaks(local, ("dfma",))
     # timed region: device-timed with CUDA events on the library's stream
     P.shci_set_timing(H, True)
     launches0 = P.shci_get_stats(H)["kernel_launches"]
@@ -240,6 +263,7 @@ def run_ours(args):
     bytes_alg = 12.0 * (nnz_full - n) + n * (8.0 + 16.0 * kbar)
     achieved_tf = flops / (per_launch_ms / 1e3) / 1e12
     hbm_peak, peak_kind = load_peaks()
+    fp64_peak_tf = 2.0 * peaks["dfma"] / 1e12
     achieved_gbs = bytes_alg / (per_launch_ms / 1e3) / 1e9
     traffic = sigma_traffic(cfg.name, nnz_full - n)
 
@@ -282,10 +306,12 @@ def run_ours(args):
         "davidson_iters": int(np.mean(iters)),
         "energies": [float(x) for x in energies],
         "sigma_kernel_ms": per_launch_ms,
-        "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved_tf / NOMINAL_FP64_TFLOPS, "traffic": traffic,
+        "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": fp64_peak_tf, "unit": "TFLOP/s",
+                     "frac": achieved_tf / fp64_peak_tf, "traffic": traffic,
                      "kernel": "k_sigma_stored (FP64 FMA per stored nonzero per vector)",
-                     "peak_kind": "nominal FP64 (GB300 dense FP64, 2 DFMA/clk/SM at 2070 MHz)"},
+                     "peak_kind": "measured: independent FP64 FMAs of the project microbenchmark "
+                                  "(paper_1809_04600_gb300/measure/peaks.cu) in this run, 2 flops each",
+                     "nominal_peak": NOMINAL_FP64_TFLOPS, "frac_of_nominal": achieved_tf / NOMINAL_FP64_TFLOPS},
         "roofline_hbm": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
                          "frac": achieved_gbs / hbm_peak, "peak_kind": peak_kind},
         "clocks": clocks,
@@ -846,6 +872,26 @@ def run_batch(args):
     ctx.close()
 
 
+def run_peaks(args):
+    """The peak-rate microbenchmarks (FP64 FMA and add, INT32 multiply-add,
+    XOR + popcount, FP64 atomics and random gathers in L2), with the clocks
+    sampled while they run."""
+    import torch
+    torch.cuda.init()
+    sampler = ClockSampler(0)
+    sampler.start()
+    rates = measure_peaks(0)
+    rates2 = measure_peaks(0)          # twice: the better of two
+    clocks = sampler.stop()
+    best = {k: max(rates[k], rates2[k]) for k in rates}
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    mhz = clocks.get("sm_mhz") or 2070.0
+    print(json.dumps({"workload": "peak-rate microbenchmarks (measure/peaks.cu), 4 CTAs x 256 threads per SM",
+                      "ops_per_s": best, "fp64_fma_tflops": 2.0 * best["dfma"] / 1e12,
+                      "per_sm_per_clock": {k: v / sms / (mhz * 1e6) for k, v in best.items()},
+                      "sms": sms, "clocks": clocks}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -861,7 +907,7 @@ def main():
     ap.add_argument("--sigma-only", type=int, default=0,
                     help="profiling only: build once, then launch the sigma kernel this many times")
     ap.add_argument("--workload", default="main",
-                    choices=["main", "fci", "large", "adjoint", "batch", "select", "extend"],
+                    choices=["main", "fci", "large", "adjoint", "batch", "select", "extend", "peaks"],
                     help="main: the bench line; others print the measurement line of another workload")
     ap.add_argument("--batch-budget-gb", type=float, default=180.0)
     ap.add_argument("--eps1", type=float, action="append", help="selection thresholds (select workload)")
@@ -876,7 +922,7 @@ def main():
     args = ap.parse_args()
     if args.workload != "main":
         {"fci": run_fci, "large": run_large, "adjoint": run_adjoint, "batch": run_batch,
-         "select": run_select, "extend": run_extend}[args.workload](args)
+         "select": run_select, "extend": run_extend, "peaks": run_peaks}[args.workload](args)
     elif args.sigma_only:
         run_sigma_only(args)
     elif args.impl == "reference":

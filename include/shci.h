@@ -149,17 +149,26 @@ int shci_sigma(shci_ctx *ctx, int k, const double *c, double *sigma, int mem_spa
 /* sigma = H c like shci_sigma, for device pointers only, with no device
  * allocation of any kind.  The paper has no counterpart: this entry point is
  * for callers that cannot let a library call cudaMalloc -- a process whose
- * device memory is already handed to another allocator, or a latency-critical
- * loop that must not pay the device-wide synchronisation of cudaMalloc.
+ * device memory is already handed to another allocator (a framework's caching
+ * pool that reserved nearly all of HBM, where a cudaMalloc fails), or a
+ * latency-critical loop that must not pay the device-wide synchronisation of
+ * cudaMalloc / cudaFree.
  * Its layout scratch is one file-scope __device__ array of 2 x 524,288
  * doubles (8 MiB), held on every GPU that loads the library until exit.
- * Requirements: built in SHCI_STORED mode, k in [1, 8],
- * k * n_det <= 524,288 (SHCI_ERR_INVALID otherwise), c and sigma device
- * [k][n_det], not overlapping.  The first call on a device looks up the
- * array's address with that device current: make it before any stream
- * capture.  All calls share the array, so calls that overlap on the GPU race;
- * nothing in it needs to start at zero.  Synchronises the context's stream
- * before returning. */
+ * Set-up: shci_create, with the context's device current, looks up the
+ * array's device address and loads the kernels this call launches, so that
+ * with lazy module loading the array's memory is taken there and no call of
+ * this entry point allocates.  Should that look-up fail in shci_create, the
+ * first call on the device retries it (and reports a failure as
+ * SHCI_ERR_CUDA); that first call should then come before any stream capture.
+ * Requirements: built in SHCI_STORED mode (SHCI_ERR_STATE otherwise), k in
+ * [1, 8], k * n_det <= 524,288 (SHCI_ERR_INVALID otherwise, before any
+ * launch), c and sigma device [k][n_det], not overlapping.  All calls share
+ * the array, which keeps the last call's contents, so calls that overlap on
+ * the GPU (other streams, contexts or threads) race; nothing in it needs to
+ * start at zero, since every element a call reads was written earlier in that
+ * call.  The caller's current device is restored before returning.
+ * Synchronises the context's stream before returning. */
 int shci_sigma_noalloc(shci_ctx *ctx, int k, const double *c, double *sigma);
 
 /* Lowest k_roots (in [1, 8]) eigenpairs of H on V by diagonally
@@ -354,6 +363,13 @@ int shci_batch_create(shci_ctx *ctx, int n_sys, const shci_system_desc *systems,
 int shci_batch_davidson(shci_batch *b, int k_roots, double tol, int max_iter, double *energies, int *iters,
                         int *converged);
 int shci_batch_get_stats(shci_batch *b, shci_batch_stats_t *out);
+/* Bound of the grid barrier's wait in shci_batch_davidson (no counterpart in
+ * the paper): a block that has waited `naps` naps of about 100 ns for the
+ * others gives up, every block then leaves the kernel, and the call returns
+ * SHCI_ERR_TIMEOUT with the context still usable.  naps < 0 restores the
+ * default (2^27 naps, at least ~13 s); 0 gives up at the first wait, which
+ * failure-handling tests use to make the bound run out. */
+int shci_batch_set_wait_limit(shci_batch *b, long long naps);
 void shci_batch_destroy(shci_batch *b);
 
 /* Library-side measurements of the last build / Davidson run (for reports). */

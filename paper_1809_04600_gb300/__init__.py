@@ -16,6 +16,10 @@ from .binding import shci_extend_connectivity  # noqa: F401
 from .binding import shci_alias_draw, shci_pt2_3step, shci_pt2_samples, shci_pt2_semistochastic  # noqa: F401
 from .binding import (  # noqa: F401
     shci_batch_create, shci_batch_davidson, shci_batch_destroy, shci_batch_get_stats,
+    shci_batch_set_wait_limit,
+)
+from .binding import (  # noqa: F401
+    SHCI_ERR_CUDA, SHCI_ERR_INVALID, SHCI_ERR_NOT_CONVERGED, SHCI_ERR_OOM, SHCI_ERR_STATE, SHCI_ERR_TIMEOUT, SHCI_OK,
 )
 from .build_lib import build  # noqa: F401
 

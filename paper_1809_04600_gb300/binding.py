@@ -36,7 +36,8 @@ _STATUS = {1: "INVALID", 2: "OOM", 3: "CUDA", 4: "NOT_CONVERGED", 5: "TIMEOUT", 
 EXPORTED = [
     "shci_create", "shci_destroy", "shci_last_error", "shci_load_integrals", "shci_build_connectivity",
     "shci_extend_connectivity", "shci_get_diag", "shci_get_pairs", "shci_get_row", "shci_sigma", "shci_sigma_noalloc", "shci_energy_backward",
-    "shci_batch_create", "shci_batch_davidson", "shci_batch_get_stats", "shci_batch_destroy", "shci_davidson",
+    "shci_batch_create", "shci_batch_davidson", "shci_batch_get_stats", "shci_batch_set_wait_limit", "shci_batch_destroy",
+    "shci_davidson",
     "shci_davidson_history", "shci_select", "shci_pt2", "shci_alias_draw", "shci_pt2_samples",
     "shci_pt2_semistochastic", "shci_pt2_3step", "shci_get_stats", "shci_set_timing",
 ]
@@ -117,6 +118,7 @@ def load_library(path: str = LIB_PATH):
         "shci_batch_create": (i32, [vp, i32, ctypes.POINTER(shci_system_desc), i32, f64, ctypes.POINTER(vp)]),
         "shci_batch_davidson": (i32, [vp, i32, f64, i32, vp, vp, vp]),
         "shci_batch_get_stats": (i32, [vp, ctypes.POINTER(shci_batch_stats_t)]),
+        "shci_batch_set_wait_limit": (i32, [vp, ctypes.c_longlong]),
         "shci_batch_destroy": (None, [vp]),
         "shci_davidson": (i32, [vp, i32, f64, i32, vp, vp, vp, i32, ctypes.POINTER(i32)]),
         "shci_davidson_history": (i32, [vp, i32, vp, vp, vp, ctypes.POINTER(i32)]),
@@ -441,6 +443,13 @@ def shci_batch_get_stats(batch) -> dict:
     out = {name: getattr(s, name) for name, _ in shci_batch_stats_t._fields_}
     out["phase_ms"] = list(s.phase_ms)
     return out
+
+
+def shci_batch_set_wait_limit(batch, naps):
+    """Bound of the batch solver's grid-barrier wait, in ~100 ns naps (< 0: the default)."""
+    rc = load_library().shci_batch_set_wait_limit(batch, int(naps))
+    if rc != SHCI_OK:
+        raise ShciError(rc, "shci_batch_set_wait_limit failed")
 
 
 def shci_batch_destroy(batch):

@@ -1,4 +1,6 @@
-"""Compile the CUDA library (sm_103a) in-tree: csrc/*.cu -> libshci.so.
+"""Compile the CUDA library (sm_103a) in-tree: csrc/*.cu -> libshci.so, and
+the peak-rate microbenchmarks measure/peaks.cu -> libshci_peaks.so (used by
+bench.py for the roofline denominators, not by the library).
 
 Each translation unit is compiled by nvcc in parallel into _build/, then
 linked with nvcc -shared.  No torch headers are involved, so the build takes
@@ -17,6 +19,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(os.path.dirname(HERE), "_build")
 LIB = os.path.join(HERE, "libshci.so")
+PEAKS_SRC = os.path.join(HERE, "measure", "peaks.cu")
+PEAKS_LIB = os.path.join(HERE, "libshci_peaks.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
@@ -45,7 +49,22 @@ def _stale(lib: str) -> bool:
     return any(os.path.getmtime(f) > t for f in _sources() + _headers())
 
 
+def build_peaks(force: bool = False) -> str:
+    """The peak-rate microbenchmark library (one translation unit)."""
+    if not force and os.path.exists(PEAKS_LIB) and os.path.getmtime(PEAKS_LIB) >= os.path.getmtime(PEAKS_SRC):
+        return PEAKS_LIB
+    tmp = PEAKS_LIB + ".%d.tmp" % os.getpid()
+    cmd = [_nvcc(), *ARCH, "-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-shared", "-o", tmp, PEAKS_SRC,
+           "-lcudart"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("nvcc failed on %s:\n%s\n%s" % (PEAKS_SRC, r.stdout, r.stderr))
+    os.replace(tmp, PEAKS_LIB)
+    return PEAKS_LIB
+
+
 def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
+    build_peaks(force)
     if not force and not _stale(LIB):
         return LIB
     nvcc = _nvcc()

@@ -67,6 +67,7 @@ int shci_create(shci_ctx **out, int device, void *cuda_stream) {
         }
         CUDA_TRY(cudaEventCreate(&c->ev0));
         CUDA_TRY(cudaEventCreate(&c->ev1));
+        shci::noalloc_prepare(device);
     } catch (const ShciError &e) {
         g_create_error = e.msg;
         delete c;

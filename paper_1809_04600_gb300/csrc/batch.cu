@@ -34,7 +34,7 @@ constexpr int BT = 256;                    // threads per CTA
 constexpr int VSLICE = 8192;               // vector elements per vector work item
 constexpr int GA = 8;                      // basis rows per register block in slice Gram products
 constexpr int PSTRIDE = SHCI_MAX_SUB * BK + BK * BK + BK + 12;   // partial sums per vector item
-constexpr long long BARRIER_SPIN_LIMIT = 1ll << 27;             // x ~100 ns naps: >= ~13 s
+constexpr long long BARRIER_SPIN_LIMIT = 1ll << 27;             // default: x ~100 ns naps >= ~13 s
 constexpr int OFF_S0 = SHCI_MAX_SUB * BK;                        // partial layout offsets
 constexpr int OFF_RN = SHCI_MAX_SUB * BK + BK * BK;
 
@@ -94,6 +94,7 @@ struct BatchArgs {
     int64_t n_v;
     double *partial;                       // [n_v][PSTRIDE]
     BarrierState *bar;
+    long long spin_limit;                  // naps a waiting block takes before it gives up
 };
 
 // ---------------------------------------------------------------- barrier and helpers
@@ -105,8 +106,9 @@ __device__ __forceinline__ unsigned long long global_ns() {
 }
 
 // Grid-wide barrier; `phase` names the phase that ends here (block 0 adds
-// the time since the previous barrier to that phase's total).
-__device__ bool grid_sync(BarrierState *b, int phase) {
+// the time since the previous barrier to that phase's total).  A block that
+// has waited `limit` naps of ~100 ns gives up and raises the error flag.
+__device__ bool grid_sync(BarrierState *b, int phase, long long limit) {
     __shared__ int ok;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -125,7 +127,7 @@ __device__ bool grid_sync(BarrierState *b, int phase) {
                 long long spins = 0;
                 while (*vgen == g) {
                     if (*(volatile int *)&b->err) { good = 0; break; }
-                    if (++spins > BARRIER_SPIN_LIMIT) {
+                    if (++spins > limit) {
                         atomicExch(&b->err, 1);
                         good = 0;
                         break;
@@ -351,7 +353,7 @@ __global__ void __launch_bounds__(BT, MINB) k_batch_davidson(BatchArgs B) {
         }
         __syncthreads();
     }
-    if (!grid_sync(B.bar, 0)) return;
+    if (!grid_sync(B.bar, 0, B.spin_limit)) return;
 
     for (int it = 0; it < B.max_iter; it++) {
         // ---- A1: sigma for stored rows and alpha-grouped on-the-fly items
@@ -369,7 +371,7 @@ __global__ void __launch_bounds__(BT, MINB) k_batch_davidson(BatchArgs B) {
                 batch_alpha_item(S, B.a1_local[item], es, nb);
             }
         }
-        if (!grid_sync(B.bar, 1)) return;
+        if (!grid_sync(B.bar, 1, B.spin_limit)) return;
         // ---- A2: beta-grouped on-the-fly items (adds the same-spin-alpha part)
         while (true) {
             const int item = next_item(B.bar);
@@ -380,7 +382,7 @@ __global__ void __launch_bounds__(BT, MINB) k_batch_davidson(BatchArgs B) {
             if (!active || nb == 0) continue;
             batch_beta_item(S, B.a2_local[item], es, nb);
         }
-        if (!grid_sync(B.bar, 2)) return;
+        if (!grid_sync(B.bar, 2, B.spin_limit)) return;
 
         // ---- B: AV[m + q] = Y[:, q]; partial Gram columns V[a] . Y[:, q], a < m + nb
         for (int64_t item = blockIdx.x; item < B.n_v; item += gridDim.x) {
@@ -401,7 +403,7 @@ __global__ void __launch_bounds__(BT, MINB) k_batch_davidson(BatchArgs B) {
             };
             slice_gram(B.partial + item * PSTRIDE, V, S.n, m + nb, i0, i1, loadY, red);
         }
-        if (!grid_sync(B.bar, 3)) return;
+        if (!grid_sync(B.bar, 3, B.spin_limit)) return;
 
         // ---- C: per system: new G columns, subspace eigen-decomposition
         for (int s = blockIdx.x; s < B.S; s += gridDim.x) {
@@ -425,7 +427,7 @@ __global__ void __launch_bounds__(BT, MINB) k_batch_davidson(BatchArgs B) {
             }
             __syncthreads();
         }
-        if (!grid_sync(B.bar, 4)) return;
+        if (!grid_sync(B.bar, 4, B.spin_limit)) return;
 
         // ---- D: Ritz vectors, residuals and corrections T[l] = r_l / (theta_l - H_ii);
         //         partials |r_l|^2, S0 = T^T T, C = V^T T
@@ -484,7 +486,7 @@ __global__ void __launch_bounds__(BT, MINB) k_batch_davidson(BatchArgs B) {
             };
             slice_gram(part, V, S.n, m, i0, i1, loadT, red);
         }
-        if (!grid_sync(B.bar, 5)) return;
+        if (!grid_sync(B.bar, 5, B.spin_limit)) return;
 
         // ---- E: per system: convergence, restart decision, coefficients of the kept corrections
         for (int s = blockIdx.x; s < B.S; s += gridDim.x) {
@@ -559,7 +561,7 @@ __global__ void __launch_bounds__(BT, MINB) k_batch_davidson(BatchArgs B) {
             if (tid < BK) S.coefS0[tid] = tid < ntodo ? S0[st.todo[tid] * BK + st.todo[tid]] : 1.0;
             __syncthreads();
         }
-        if (!grid_sync(B.bar, 6)) return;
+        if (!grid_sync(B.bar, 6, B.spin_limit)) return;
         {
             int any = 0;
             for (int s = 0; s < B.S; s++) any |= ldi(&B.st[s].active);
@@ -623,7 +625,7 @@ __global__ void __launch_bounds__(BT, MINB) k_batch_davidson(BatchArgs B) {
             };
             slice_gram(B.partial + item * PSTRIDE, Vp, S.n, m, i0, i1, loadT2, red);
         }
-        if (!grid_sync(B.bar, 7)) return;
+        if (!grid_sync(B.bar, 7, B.spin_limit)) return;
 
         // ---- G: per system: switch to the rotated buffers; second-pass coefficients
         for (int s = blockIdx.x; s < B.S; s += gridDim.x) {
@@ -639,7 +641,7 @@ __global__ void __launch_bounds__(BT, MINB) k_batch_davidson(BatchArgs B) {
             }
             __syncthreads();
         }
-        if (!grid_sync(B.bar, 8)) return;
+        if (!grid_sync(B.bar, 8, B.spin_limit)) return;
 
         // ---- H: second projection T2 -= V C2; partial S = T2^T T2
         for (int64_t item = blockIdx.x; item < B.n_v; item += gridDim.x) {
@@ -674,7 +676,7 @@ __global__ void __launch_bounds__(BT, MINB) k_batch_davidson(BatchArgs B) {
             }
             item_reduce<BK * BK>(B.partial + item * PSTRIDE, s2, BK * BK, red);
         }
-        if (!grid_sync(B.bar, 9)) return;
+        if (!grid_sync(B.bar, 9, B.spin_limit)) return;
 
         // ---- I: per system: Cholesky-QR coefficients, pass 1 (dependence test
         //         against the norms before projection)
@@ -688,7 +690,7 @@ __global__ void __launch_bounds__(BT, MINB) k_batch_davidson(BatchArgs B) {
             if (tid == 0) st.cnt1 = cholqr_coef(S.coefS, nt, S.coefS0, 1e-20, S.coefM);
             __syncthreads();
         }
-        if (!grid_sync(B.bar, 10)) return;
+        if (!grid_sync(B.bar, 10, B.spin_limit)) return;
 
         // ---- J: T = T2 M (zero past cnt1); partial S = T^T T
         for (int64_t item = blockIdx.x; item < B.n_v; item += gridDim.x) {
@@ -723,7 +725,7 @@ __global__ void __launch_bounds__(BT, MINB) k_batch_davidson(BatchArgs B) {
             }
             item_reduce<BK * BK>(B.partial + item * PSTRIDE, s2, BK * BK, red);
         }
-        if (!grid_sync(B.bar, 11)) return;
+        if (!grid_sync(B.bar, 11, B.spin_limit)) return;
 
         // ---- K: per system: Cholesky-QR coefficients, pass 2
         for (int s = blockIdx.x; s < B.S; s += gridDim.x) {
@@ -739,7 +741,7 @@ __global__ void __launch_bounds__(BT, MINB) k_batch_davidson(BatchArgs B) {
             }
             __syncthreads();
         }
-        if (!grid_sync(B.bar, 12)) return;
+        if (!grid_sync(B.bar, 12, B.spin_limit)) return;
 
         // ---- L: new basis vectors V[m + l] = T M2 (l < cnt2) and the next sigma input X
         for (int64_t item = blockIdx.x; item < B.n_v; item += gridDim.x) {
@@ -770,7 +772,7 @@ __global__ void __launch_bounds__(BT, MINB) k_batch_davidson(BatchArgs B) {
             }
             __syncthreads();
         }
-        if (!grid_sync(B.bar, 13)) return;
+        if (!grid_sync(B.bar, 13, B.spin_limit)) return;
 
         // ---- M: per system: the new block is ready for the next sigma
         if (tid == 0)
@@ -780,7 +782,7 @@ __global__ void __launch_bounds__(BT, MINB) k_batch_davidson(BatchArgs B) {
                 st.nb = st.cnt2;
                 if (st.cnt2 == 0) st.active = 0;     // no new direction: this system stops here
             }
-        if (!grid_sync(B.bar, 14)) return;
+        if (!grid_sync(B.bar, 14, B.spin_limit)) return;
     }
 }
 
@@ -825,6 +827,8 @@ struct shci_batch {
     bool tuned = false;
     cudaGraphExec_t gexec = nullptr;
     int graph_max_iter = -1;
+    long long spin_limit = shci::BARRIER_SPIN_LIMIT;
+    long long graph_spin_limit = -1;
     double graph_tol = -1.0;
     bool graph_ok = false;
     shci_batch_stats_t stats{};
@@ -871,6 +875,7 @@ void launch_batch(shci_batch *b, int max_iter, bool capture_ok) {
     A.n_v = b->n_v;
     A.partial = b->partial.p;
     A.bar = b->d_bar.p;
+    A.spin_limit = b->spin_limit;
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3((unsigned)b->grid);
     cfg.blockDim = dim3(BT);
@@ -888,7 +893,7 @@ void launch_batch(shci_batch *b, int max_iter, bool capture_ok) {
     };
     if (capture_ok) {
         // one persistent launch captured in a CUDA graph, re-instantiated when its parameters change
-        if (!b->gexec || b->graph_max_iter != max_iter) {
+        if (!b->gexec || b->graph_max_iter != max_iter || b->graph_spin_limit != b->spin_limit) {
             if (b->gexec) {
                 cudaGraphExecDestroy(b->gexec);
                 b->gexec = nullptr;
@@ -908,6 +913,7 @@ void launch_batch(shci_batch *b, int max_iter, bool capture_ok) {
                 b->gexec = nullptr;
             }
             b->graph_max_iter = max_iter;
+            b->graph_spin_limit = b->spin_limit;
         }
         if (b->gexec) {
             CUDA_TRY(cudaGraphLaunch(b->gexec, st));
@@ -1230,6 +1236,12 @@ int shci_batch_davidson(shci_batch *b, int k_roots, double tol, int max_iter, do
         ctx->err = e.what();
         return SHCI_ERR_INVALID;
     }
+}
+
+int shci_batch_set_wait_limit(shci_batch *b, long long naps) {
+    if (!b) return SHCI_ERR_INVALID;
+    b->spin_limit = naps < 0 ? shci::BARRIER_SPIN_LIMIT : naps;
+    return SHCI_OK;
 }
 
 int shci_batch_get_stats(shci_batch *b, shci_batch_stats_t *out) {

@@ -120,6 +120,10 @@ void export_pairs(shci_ctx *c, int64_t cap, int64_t *i_out, int64_t *j_out, doub
 // sigma.cu: y = H x for k vectors; `inter` selects the interleaved [n][k]
 // layout (otherwise vector-major [k][n]).
 void sigma(shci_ctx *c, int k, const double *x, double *y, bool inter);
+void sigma_stored_preload();
+
+// noalloc.cu: the allocation-free sigma's per-device set-up (at shci_create)
+void noalloc_prepare(int device);
 
 // select.cu: heat-bath selection of new determinants (Sec. II)
 void select_dets(shci_ctx *c, int k, const double *coef, double eps1, int64_t cap, uint64_t *out, int64_t *n_out,

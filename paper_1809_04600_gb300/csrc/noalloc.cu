@@ -14,9 +14,14 @@
 //    total); every GPU that loads the library holds this array until the
 //    process exits.  Calls with k * n_det > SHCI_NOALLOC_MAX_ELEMS return
 //    SHCI_ERR_INVALID.
-//  - the first call on a device looks up the array's device address
-//    (cudaGetSymbolAddress) with that device current; make that first call
-//    before any stream capture.
+//  - set-up, once per device, with that device current: shci_create looks up
+//    the array's device address (cudaGetSymbolAddress) and loads the kernels
+//    this call launches (cudaFuncGetAttributes), so that with lazy module
+//    loading (CUDA 12's default) the module holding the array is loaded --
+//    and its 8 MiB taken -- when a context is created, not inside a call.  If
+//    that look-up failed at shci_create, the first call on the device retries
+//    it; that first call should then come before any stream capture.
+//  - the call restores the caller's current device before returning.
 //  - every call shares the one array: calls that overlap on the GPU (other
 //    streams, other contexts, other host threads) race on it.
 //  - nothing in the scratch has to start at zero: each element a call reads
@@ -36,7 +41,12 @@ constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mutex;
 double *g_noalloc_ptr[kMaxDevices] = {nullptr};
 
-// device address of the scratch array on `device` (which must be current)
+// src [rows][cols] -> dst [cols][rows]
+__global__ void k_noalloc_transpose(const double *__restrict__ src, int rows, int64_t cols,
+                                    double *__restrict__ dst);
+
+// device address of the scratch array on `device` (which must be current);
+// the first look-up on a device also loads the kernels the call launches
 double *noalloc_scratch(int device) {
     if (device < 0 || device >= kMaxDevices) throw ShciError{SHCI_ERR_INVALID, "device index out of range"};
     std::lock_guard<std::mutex> lock(g_noalloc_mutex);
@@ -46,12 +56,29 @@ double *noalloc_scratch(int device) {
         if (e != cudaSuccess || !p)
             throw ShciError{SHCI_ERR_CUDA, std::string("cudaGetSymbolAddress(noalloc scratch): ") +
                                                cudaGetErrorString(e)};
+        cudaFuncAttributes fa;
+        e = cudaFuncGetAttributes(&fa, k_noalloc_transpose);
+        if (e != cudaSuccess)
+            throw ShciError{SHCI_ERR_CUDA, std::string("loading the noalloc transpose: ") + cudaGetErrorString(e)};
+        shci::sigma_stored_preload();
         g_noalloc_ptr[device] = static_cast<double *>(p);
     }
     return g_noalloc_ptr[device];
 }
 
-// src [rows][cols] -> dst [cols][rows]
+// restores the caller's current device when the call returns
+struct DeviceRestore {
+    int prev = -1;
+    explicit DeviceRestore(int want) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != want) CUDA_TRY(cudaSetDevice(want));
+    }
+    ~DeviceRestore() {
+        int now = -1;
+        if (prev >= 0 && cudaGetDevice(&now) == cudaSuccess && now != prev) cudaSetDevice(prev);
+    }
+};
+
 __global__ void k_noalloc_transpose(const double *__restrict__ src, int rows, int64_t cols,
                                     double *__restrict__ dst) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < rows * cols;
@@ -64,12 +91,24 @@ __global__ void k_noalloc_transpose(const double *__restrict__ src, int rows, in
 
 }  // namespace
 
+namespace shci {
+
+// set-up at context creation (device current); a failure here is left for the
+// first call to report
+void noalloc_prepare(int device) {
+    try {
+        noalloc_scratch(device);
+    } catch (const ShciError &) {
+        cudaGetLastError();
+    }
+}
+
+}  // namespace shci
+
 extern "C" int shci_sigma_noalloc(shci_ctx *c, int k, const double *x, double *y) {
     if (!c) return SHCI_ERR_INVALID;
     try {
-        int dev = -1;
-        cudaGetDevice(&dev);
-        if (dev != c->device) CUDA_TRY(cudaSetDevice(c->device));
+        DeviceRestore on_device(c->device);
         c->err.clear();
         if (!c->built || c->mode != SHCI_STORED)
             throw ShciError{SHCI_ERR_STATE, "shci_sigma_noalloc needs a Hamiltonian built in SHCI_STORED mode"};

@@ -108,6 +108,27 @@ static void dispatch_stored(shci_ctx *c, int k, const double *x, double *y) {
 
 void sigma_otf(shci_ctx *c, int k, const double *x, double *y, bool inter);
 
+// loads every stored-sigma kernel onto the current device (with lazy module
+// loading a kernel's module is otherwise loaded, and device memory taken, at
+// its first launch)
+template <bool INTER>
+static void preload_stored() {
+    cudaFuncAttributes fa;
+    CUDA_TRY(cudaFuncGetAttributes(&fa, k_sigma_stored<1, INTER>));
+    CUDA_TRY(cudaFuncGetAttributes(&fa, k_sigma_stored<2, INTER>));
+    CUDA_TRY(cudaFuncGetAttributes(&fa, k_sigma_stored<3, INTER>));
+    CUDA_TRY(cudaFuncGetAttributes(&fa, k_sigma_stored<4, INTER>));
+    CUDA_TRY(cudaFuncGetAttributes(&fa, k_sigma_stored<5, INTER>));
+    CUDA_TRY(cudaFuncGetAttributes(&fa, k_sigma_stored<6, INTER>));
+    CUDA_TRY(cudaFuncGetAttributes(&fa, k_sigma_stored<7, INTER>));
+    CUDA_TRY(cudaFuncGetAttributes(&fa, k_sigma_stored<8, INTER>));
+}
+
+void sigma_stored_preload() {
+    preload_stored<false>();
+    preload_stored<true>();
+}
+
 void sigma(shci_ctx *c, int k, const double *x, double *y, bool inter) {
     if (!c->built) throw ShciError{SHCI_ERR_STATE, "build the connectivity before sigma"};
     if (c->timing) CUDA_TRY(cudaEventRecord(c->ev0, c->st));

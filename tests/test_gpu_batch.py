@@ -72,6 +72,40 @@ def test_batch_matches_sequential_solves(P):
     ctx.close()
 
 
+@pytest.mark.parametrize("before_tuning", [False, True])
+def test_batch_barrier_timeout_is_reported_and_recoverable(P, before_tuning):
+    """The grid barrier's wait is bounded: with the bound forced to zero the
+    first block that has to wait gives up, every block leaves the kernel and
+    the call returns SHCI_ERR_TIMEOUT (no hang, no fault).  The context stays
+    usable and the default bound solves the same batch to the same energies;
+    both while the autotuner times its trials and in the captured graph."""
+    systems = small_batch(n_sys=4, cap=2000, seed=5200)
+    ctx = P.Context(0, torch.cuda.current_stream())
+    b = P.shci_batch_create(ctx.handle, systems)
+    e0 = None
+    if not before_tuning:
+        e0, _, _, rc = P.shci_batch_davidson(ctx.handle, b, len(systems), 2, tol=1e-10)
+        assert rc == 0
+    P.shci_batch_set_wait_limit(b, 0)
+    with pytest.raises(P.ShciError) as exc:
+        P.shci_batch_davidson(ctx.handle, b, len(systems), 2, tol=1e-10)
+    assert exc.value.code == P.SHCI_ERR_TIMEOUT
+    assert "timed out" in P.shci_last_error(ctx.handle)
+    torch.cuda.synchronize()                                 # no sticky error
+    P.shci_batch_set_wait_limit(b, -1)
+    e1, _, conv, rc = P.shci_batch_davidson(ctx.handle, b, len(systems), 2, tol=1e-10)
+    assert rc == 0 and conv.all()
+    if e0 is not None:
+        np.testing.assert_allclose(e1, e0, atol=1e-12, rtol=0)
+    for s, d in enumerate(systems):
+        B = G.Built(P, d["h"], d["eri"], d["e_core"], d["dets"], d["n_alpha"], d["n_beta"])
+        es, _, _ = B.davidson(2, tol=1e-10)
+        B.close()
+        np.testing.assert_allclose(e1[s], es, atol=E_TOL, rtol=0)
+    P.shci_batch_destroy(b)
+    ctx.close()
+
+
 def test_batch_rejects_bad_arguments(P):
     systems = small_batch(n_sys=2, cap=500)
     ctx = P.Context(0, torch.cuda.current_stream())

@@ -1,9 +1,14 @@
 """Heat-bath selection (Sec. II.A, Eq. 2) on the GPU against the oracle's brute
 force: the selected sets are compared as sets of determinants, bit-exact.
 The GPU tests |H_ai| |c_i| >= eps1 in FP64 with matrix elements summed in
-another order than the oracle's, so products within 1e-9 of eps1 may fall
-either way: the GPU set at eps1 must contain the oracle set at
-eps1 (1 + 1e-9) and lie inside the oracle set at eps1 (1 - 1e-9)."""
+another order than the oracle's.  A matrix element is a sum of at most
+m = 2 n_e + 1 terms; two summation orders of the same terms differ by at most
+2 gamma_{m-1} sum|t|, gamma_j = j u / (1 - j u), u = 2^-53 (the bound on
+recursive summation): about 6e-15 sum|t| for the 28 electrons of the largest
+case.  BAND = 1e-12 relative covers term sums up to ~160 times the element, so
+products within BAND of eps1 may fall either way: the GPU set at eps1 must
+contain the oracle set at eps1 (1 + BAND) and lie inside the oracle set at
+eps1 (1 - BAND)."""
 import numpy as np
 import pytest
 import torch
@@ -12,6 +17,8 @@ import shci_synth as S
 from tests import gpu_common as G
 
 pytestmark = pytest.mark.gpu
+
+BAND = 1e-12
 
 @pytest.fixture(scope="module")
 def P():
@@ -33,9 +40,9 @@ def _check(P, O, B, dets, c, eps1, device=True):
     assert len(g) == got.shape[0]                              # no repeats
     keys = [tuple(int(x) for x in d[::-1]) for d in got.view(np.uint64)]
     assert keys == sorted(keys)                                # ascending, last word most significant
-    ref, best = O.select(dets, c, eps1 * (1 - 1e-9), with_best=True)
+    ref, best = O.select(dets, c, eps1 * (1 - BAND), with_best=True)
     hi = _rows(ref)
-    lo = _rows(ref[best >= eps1 * (1 + 1e-9)])
+    lo = _rows(ref[best >= eps1 * (1 + BAND)])
     assert lo <= g <= hi
     assert not (g & _rows(dets))                               # nothing already in V
     st = P.shci_get_stats(B.ctx.handle)
@@ -107,12 +114,12 @@ def test_full_space_selects_nothing_and_bad_arguments(P, oracle_mod):
 # ---------------------------------------------------------------- screened Epstein-Nesbet PT2 (Sec. II.B, Eq. 7)
 
 def _pt2_check(P, O, B, dets, c, e_var, eps2, n_batches=0):
-    """GPU dE2 against the oracle's.  Terms within 1e-9 of eps2 may be kept on
+    """GPU dE2 against the oracle's.  Terms within BAND of eps2 may be kept on
     one side and dropped on the other: the GPU value must match the oracle
-    at eps2 (1 - 1e-9) or at eps2 (1 + 1e-9), to 1e-10 relative."""
+    at eps2 (1 - BAND) or at eps2 (1 + BAND), to 1e-10 relative."""
     got, npert = P.shci_pt2(B.ctx.handle, G.dev(c), e_var, eps2, n_batches)
-    lo = O.pt2(dets, c, e_var, eps2 * (1 - 1e-9))
-    hi = O.pt2(dets, c, e_var, eps2 * (1 + 1e-9))
+    lo = O.pt2(dets, c, e_var, eps2 * (1 - BAND))
+    hi = O.pt2(dets, c, e_var, eps2 * (1 + BAND))
     ok = [abs(got - r[0]) <= 1e-10 * max(1e-6, abs(r[0])) and npert == r[1] for r in (lo, hi)]
     assert any(ok), (got, npert, lo, hi)
     st = P.shci_get_stats(B.ctx.handle)
@@ -180,7 +187,7 @@ def _draws(c, n_samples, n_d, seed):
 def _samples_check(P, O, B, dets, c, e_var, eps2, eps2_d, draws):
     got = P.shci_pt2_samples(B.ctx.handle, G.dev(c), e_var, eps2, eps2_d, G.dev(draws))
     for s in range(draws.shape[0]):
-        refs = [O.pt2_sample(dets, c, e_var, eps2 * f, eps2_d * f, draws[s]) for f in (1 - 1e-9, 1 + 1e-9)]
+        refs = [O.pt2_sample(dets, c, e_var, eps2 * f, eps2_d * f, draws[s]) for f in (1 - BAND, 1 + BAND)]
         ok = [all(abs(got[s, j] - r[j]) <= 1e-10 * max(1e-8, abs(r[j])) for j in (0, 1)) for r in refs]
         assert any(ok), (s, got[s], refs)
     return got
