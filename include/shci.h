@@ -174,10 +174,12 @@ int shci_sigma_noalloc(shci_ctx *ctx, int k, const double *c, double *sigma);
 /* Lowest k_roots (in [1, 8]) eigenpairs of H on V by diagonally
  * preconditioned Davidson (Sec. II.A).  Converged when, for every root, the
  * Ritz value moved by less than `tol` since the previous iteration and the
- * residual norm ||H x - theta x|| is below 0.1 * sqrt(tol).  A root that meets
+ * residual norm ||H x - theta x|| is below 0.1 * sqrt(tol), or the residual
+ * norm is below 1e-3 of that bound (the Ritz value is then exact to rounding).  A root that meets
  * both conditions adds no further correction vector while the others
  * converge (its Ritz value and residual are still checked every iteration).
- * guess: NULL (start from the unit vectors of the k_roots lowest H_ii) or
+ * guess: NULL (start from the k_roots lowest eigenvectors of H restricted to
+ * the min(64, n_det) determinants of lowest H_ii, ties by index) or
  * [k_roots][n_det] starting vectors (orthonormalised by the call), in
  * mem_space.  Like any Davidson iteration it can settle on an excited root
  * when the start overlaps the lowest ones poorly, and it keeps every symmetry

@@ -506,10 +506,11 @@ __global__ void __launch_bounds__(BT, MINB) k_batch_davidson(BatchArgs B) {
                 for (int l = 0; l < k; l++) {
                     st.theta[l] = S.eval[l];
                     st.rn[l] = sqrt(fmax(0.0, rn2[l]));
-                    const bool cl = fabs(st.theta[l] - st.theta_old[l]) < S.tol && st.rn[l] < S.res_tol;
+                    const bool cl = (fabs(st.theta[l] - st.theta_old[l]) < S.tol && st.rn[l] < S.res_tol) ||
+                                    st.rn[l] < S.res_tol * 1e-3;
                     conv = conv && cl;
                     // a converged root is locked: no new direction for it
-                    if (!cl && st.rn[l] >= S.res_tol * 1e-3) st.todo[ntodo++] = l;
+                    if (!cl) st.todo[ntodo++] = l;
                 }
                 for (int l = 0; l < k; l++) st.theta_old[l] = st.theta[l];
                 st.it = st.it + 1;
@@ -795,13 +796,14 @@ constexpr size_t BATCH_SMEM = JACOBI_SMEM_A > sizeof(EnumSmem<1>)
                                   : (sizeof(EnumSmem<1>) > BATCH_SCRATCH ? sizeof(EnumSmem<1>) : BATCH_SCRATCH);
 
 // the compiled variants of the persistent kernel (CTAs per SM)
-constexpr int BATCH_MINB_LO = 2, BATCH_MINB_HI = 4;
+constexpr int BATCH_MINB_LO = 2, BATCH_MINB_HI = 5;
 
 inline void (*batch_kernel(int minb))(BatchArgs) {
     switch (minb) {
         case 2: return k_batch_davidson<2>;
         case 3: return k_batch_davidson<3>;
-        default: return k_batch_davidson<4>;
+        case 4: return k_batch_davidson<4>;
+        default: return k_batch_davidson<5>;
     }
 }
 

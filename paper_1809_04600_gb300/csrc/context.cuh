@@ -16,6 +16,7 @@ struct DavidsonWork {
     DevBuf<double> small;        // small device scalars (norms, coefficients)
     DevBuf<unsigned> ctr;        // last-block reduction counters
     DevBuf<double> host_pinned_dummy;
+    DevBuf<double> guess_G, guess_vec, guess_val;   // start vectors: the small subspace problem
     double *h_status = nullptr;  // pinned host mirror of the status block
 };
 

@@ -400,53 +400,80 @@ __global__ void k_jacobi(const double *__restrict__ G, int ld, int m, int m_prev
     jacobi_solve(G, ld, m, m_prev, eval, evec, jsm);
 }
 
-// ---------------------------------------------------------------- guesses
+// ---------------------------------------------------------------- start vectors
 
-__global__ void k_argmin_partial(const double *__restrict__ d, int64_t n, const int64_t *__restrict__ excl,
-                                 int n_excl, double *__restrict__ pv, int64_t *__restrict__ pi) {
-    double best = INFINITY;
-    int64_t bi = INT64_MAX;
+// Order-preserving 64-bit key of a double (ascending keys = ascending values)
+// and the element's index, for a stable sort of the diagonal.
+__global__ void k_diag_keys(const double *__restrict__ d, int64_t n, uint64_t *__restrict__ keys,
+                            uint32_t *__restrict__ vals) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        bool skip = false;
-        for (int e = 0; e < n_excl; e++) skip |= excl[e] == i;
-        if (skip) continue;
-        double v = d[i];
-        if (v < best || (v == best && i < bi)) { best = v; bi = i; }
-    }
-    for (int o = 16; o >= 1; o >>= 1) {
-        double ov = __shfl_xor_sync(0xffffffffu, best, o);
-        int64_t oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (ov < best || (ov == best && oi < bi)) { best = ov; bi = oi; }
-    }
-    __shared__ double sv[32];
-    __shared__ int64_t si[32];
-    if ((threadIdx.x & 31) == 0) { sv[threadIdx.x >> 5] = best; si[threadIdx.x >> 5] = bi; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int w = 1; w < (int)(blockDim.x >> 5); w++)
-            if (sv[w] < best || (sv[w] == best && si[w] < bi)) { best = sv[w]; bi = si[w]; }
-        pv[blockIdx.x] = best;
-        pi[blockIdx.x] = bi;
+        const uint64_t b = (uint64_t)__double_as_longlong(d[i]);
+        keys[i] = (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+        vals[i] = (uint32_t)i;
     }
 }
 
-__global__ void k_argmin_final(const double *__restrict__ pv, const int64_t *__restrict__ pi, int nb,
-                               int64_t *__restrict__ excl, int slot) {
-    if (threadIdx.x != 0) return;
-    double best = INFINITY;
-    int64_t bi = INT64_MAX;
-    for (int b = 0; b < nb; b++)
-        if (pv[b] < best || (pv[b] == best && pi[b] < bi)) { best = pv[b]; bi = pi[b]; }
-    excl[slot] = bi;
+// G[a * ld + b] = <D_sel[a]| H |D_sel[b]> for a, b < m (both triangles).
+template <int W>
+__global__ void k_guess_block(const uint64_t *__restrict__ dets, const double *__restrict__ diag,
+                              const uint32_t *__restrict__ sel, int m, int ld, DevInts I, double *__restrict__ G) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m * m; e += gridDim.x * blockDim.x) {
+        const int a = e / m, b = e % m;
+        if (a > b) continue;
+        const int64_t i = sel[a], j = sel[b];
+        double v;
+        if (a == b) {
+            v = diag[i];
+        } else {
+            const Str<W> ai = load_str<W>(dets, 2 * i), bi = load_str<W>(dets, 2 * i + 1);
+            const Str<W> aj = load_str<W>(dets, 2 * j), bj = load_str<W>(dets, 2 * j + 1);
+            const int d = xor_popc<W>(ai, aj) + xor_popc<W>(bi, bj);
+            v = (d == 2 || d == 4) ? hij_offdiag<W>(I, ai, bi, aj, bj) : 0.0;
+        }
+        G[a * ld + b] = v;
+        G[b * ld + a] = v;
+    }
 }
 
-__global__ void k_unit_vectors(const int64_t *__restrict__ idx, int k, int64_t n, double *__restrict__ V) {
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)k * n;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        int l = (int)(e / n);
-        int64_t i = e % n;
-        V[e] = (i == idx[l]) ? 1.0 : 0.0;
+// T[l][sel[a]] = evec[l * ld + a] for l < k, a < m (T zeroed before)
+__global__ void k_guess_scatter(const double *__restrict__ evec, int ld, const uint32_t *__restrict__ sel, int m,
+                                int k, int64_t n, double *__restrict__ T) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m * k; e += gridDim.x * blockDim.x) {
+        const int l = e / m, a = e % m;
+        T[(int64_t)l * n + sel[a]] = evec[l * ld + a];
     }
+}
+
+// The default start of the iteration: the k lowest eigenvectors of H
+// restricted to the m = min(64, n) determinants of lowest H_ii (ties by
+// index), written to T[0..k) as full vectors.
+static void subspace_guess(shci_ctx *c, int k, double *T) {
+    const int64_t n = c->n_det;
+    const int m = (int)std::min<int64_t>(SHCI_MAX_SUB, n);
+    cudaStream_t st = c->st;
+    DavidsonWork &w = c->dw;
+    c->sort_keys.alloc((size_t)std::max<int64_t>(n, 1) * c->W);
+    c->sort_vals.alloc((size_t)std::max<int64_t>(n, 1));
+    const unsigned g = (unsigned)std::min<int64_t>(ceil_div(n, 256), (int64_t)c->n_sm * 16);
+    k_diag_keys<<<g, 256, 0, st>>>(c->diag.p, n, c->sort_keys.p, c->sort_vals.p);
+    KERNEL_CHECK();
+    g_kernel_launches += 1;
+    radix_sort<1>(c->sort_keys.p, c->sort_vals.p, n, c->sw, st);
+    w.guess_G.alloc((size_t)SHCI_MAX_SUB * SHCI_MAX_SUB);
+    w.guess_vec.alloc((size_t)SHCI_MAX_SUB * SHCI_MAX_SUB);
+    w.guess_val.alloc((size_t)SHCI_MAX_SUB);
+    const DevInts I = dev_ints(c);
+    if (c->W == 1)
+        k_guess_block<1><<<16, 256, 0, st>>>(c->dets.p, c->diag.p, c->sort_vals.p, m, SHCI_MAX_SUB, I, w.guess_G.p);
+    else
+        k_guess_block<2><<<16, 256, 0, st>>>(c->dets.p, c->diag.p, c->sort_vals.p, m, SHCI_MAX_SUB, I, w.guess_G.p);
+    KERNEL_CHECK();
+    k_jacobi<<<1, 256, JACOBI_SMEM, st>>>(w.guess_G.p, SHCI_MAX_SUB, m, 0, w.guess_val.p, w.guess_vec.p);
+    KERNEL_CHECK();
+    CUDA_TRY(cudaMemsetAsync(T, 0, sizeof(double) * k * n, st));
+    k_guess_scatter<<<4, 256, 0, st>>>(w.guess_vec.p, SHCI_MAX_SUB, c->sort_vals.p, m, k, n, T);
+    KERNEL_CHECK();
+    g_kernel_launches += 3;
 }
 
 // ---------------------------------------------------------------- host driver
@@ -699,8 +726,6 @@ int davidson(shci_ctx *c, int k, double tol, int max_iter, const double *guess, 
     c->counter.alloc(4);
     d.d_count = c->counter.p + 3;
     d.d_skip = c->counter.p + 2;
-    DevBuf<int64_t> idx;
-    idx.alloc(SHCI_MAX_K);
     cudaStream_t st = c->st;
     CUDA_TRY(cudaMemsetAsync(w.G.p, 0, sizeof(double) * d.m_max * d.m_max, st));
 
@@ -713,21 +738,9 @@ int davidson(shci_ctx *c, int k, double tol, int max_iter, const double *guess, 
         m = d.orthonormalize_append(T, k, 0);
         if (m < k) throw ShciError{SHCI_ERR_INVALID, "guess vectors are linearly dependent"};
     } else {
-        int nb = d.vec_blocks;
-        DevBuf<double> pv;
-        DevBuf<int64_t> pi;
-        pv.alloc(nb);
-        pi.alloc(nb);
-        for (int l = 0; l < k; l++) {
-            k_argmin_partial<<<nb, DV_THREADS, 0, st>>>(c->diag.p, n, idx.p, l, pv.p, pi.p);
-            k_argmin_final<<<1, 32, 0, st>>>(pv.p, pi.p, nb, idx.p, l);
-            KERNEL_CHECK();
-            g_kernel_launches += 2;
-        }
-        k_unit_vectors<<<d.vec_blocks, DV_THREADS, 0, st>>>(idx.p, k, n, w.V.p);
-        KERNEL_CHECK();
-        g_kernel_launches += 1;
-        m = k;
+        subspace_guess(c, k, T);
+        m = d.orthonormalize_append(T, k, 0);
+        if (m < k) throw ShciError{SHCI_ERR_INVALID, "start vectors are linearly dependent"};
     }
     d.expand(0, m);
 
@@ -759,10 +772,13 @@ int davidson(shci_ctx *c, int k, double tol, int max_iter, const double *guess, 
             rnorm[l] = std::sqrt(std::max(0.0, status[SHCI_MAX_K + l]));
             c->hist_theta.push_back(theta[l]);
             c->hist_rn.push_back(rnorm[l]);
-            bool cl = std::fabs(theta[l] - theta_old[l]) < tol && rnorm[l] < res_tol;
+            // converged: settled and small residual, or a residual so small that the
+            // Ritz value is exact to rounding (e.g. a start that is already an eigenvector)
+            const bool cl = (std::fabs(theta[l] - theta_old[l]) < tol && rnorm[l] < res_tol) ||
+                            rnorm[l] < res_tol * 1e-3;
             conv = conv && cl;
             // a converged root is locked: no new direction for it
-            if (!cl && rnorm[l] >= res_tol * 1e-3) todo.push_back(l);
+            if (!cl) todo.push_back(l);
         }
         theta_old = theta;
         if (conv || it == max_iter) break;

@@ -723,9 +723,20 @@ struct EnumSmem {
     WarpQueue<W> Q[ENUM_NW];
 };
 
+// CTAs per SM the on-the-fly sigma kernels are compiled for (a register cap
+// of 65536 / (256 * SHCI_OTF_MINB) per thread); the other modes leave the
+// register count to the compiler
+#ifndef SHCI_OTF_MINB
+#define SHCI_OTF_MINB 5
+#endif
+template <int MODE>
+struct EnumMinBlocks {
+    static constexpr int value = MODE == ENUM_SIGMA ? SHCI_OTF_MINB : 1;
+};
+
 // persistent grids: CTAs take work items from an atomic counter
 template <int W, int MODE, int K>
-__global__ void __launch_bounds__(ENUM_THREADS) k_enum_alpha(EnumArgs A, DevInts I) {
+__global__ void __launch_bounds__(ENUM_THREADS, EnumMinBlocks<MODE>::value) k_enum_alpha(EnumArgs A, DevInts I) {
     __shared__ EnumSmem<W> S;
     __shared__ int item_sh;
     unsigned long long cand_local = 0;
@@ -741,7 +752,7 @@ __global__ void __launch_bounds__(ENUM_THREADS) k_enum_alpha(EnumArgs A, DevInts
 }
 
 template <int W, int MODE, int K>
-__global__ void __launch_bounds__(ENUM_THREADS) k_enum_beta(EnumArgs A, DevInts I) {
+__global__ void __launch_bounds__(ENUM_THREADS, EnumMinBlocks<MODE>::value) k_enum_beta(EnumArgs A, DevInts I) {
     __shared__ EnumSmem<W> S;
     __shared__ int item_sh;
     unsigned long long cand_local = 0;

@@ -6,8 +6,10 @@
 // integer multiply-adds, the XOR + 64-bit popcount pair that screens a
 // candidate determinant, FP64 atomic adds to random L2-resident addresses and
 // random 8-byte gathers from L2.  Each kernel runs a fixed count of
-// independent operations per thread on a grid of `ctas_per_sm` CTAs per SM
-// (256 threads each) and is timed with CUDA events after one warm-up launch.
+// independent operations per thread (`chains` independent dependency chains,
+// the iteration loop unrolled four times) on a grid of `ctas_per_sm` CTAs per
+// SM (256 threads each) and is timed with CUDA events after one warm-up
+// launch; the caller takes the best over a few launch shapes.
 // Results are only stored when a data-dependent test that never holds in
 // practice passes, so the compiler keeps every operation.
 #include <cuda_runtime.h>
@@ -16,34 +18,38 @@
 namespace {
 
 constexpr int THREADS = 256;
-constexpr int CHAINS = 8;                  // independent dependency chains per thread
+constexpr int CHAINS = 8;                  // independent dependency chains per thread (integer kernels)
 
+template <int CH>
 __global__ void k_dfma(int iters, double a, double b, double *sink) {
-    double x[CHAINS];
+    double x[CH];
 #pragma unroll
-    for (int c = 0; c < CHAINS; c++) x[c] = 1e-3 * (threadIdx.x + c);
+    for (int c = 0; c < CH; c++) x[c] = 1e-3 * (threadIdx.x + c);
+#pragma unroll 4
     for (int i = 0; i < iters; i++) {
 #pragma unroll
-        for (int c = 0; c < CHAINS; c++) x[c] = fma(x[c], a, b);
+        for (int c = 0; c < CH; c++) x[c] = fma(x[c], a, b);
     }
     double s = 0.0;
 #pragma unroll
-    for (int c = 0; c < CHAINS; c++) s += x[c];
+    for (int c = 0; c < CH; c++) s += x[c];
     if (s == -1.0) sink[blockIdx.x] = s;
 }
 
+template <int CH>
 __global__ void k_dadd(int iters, double b, double *sink) {
-    double x[CHAINS];
+    double x[CH];
 #pragma unroll
-    for (int c = 0; c < CHAINS; c++) x[c] = 1e-3 * (threadIdx.x + c);
+    for (int c = 0; c < CH; c++) x[c] = 1e-3 * (threadIdx.x + c);
+#pragma unroll 4
     for (int i = 0; i < iters; i++) {
 #pragma unroll
-        for (int c = 0; c < CHAINS; c++) x[c] = x[c] + b;
+        for (int c = 0; c < CH; c++) x[c] = x[c] + b;
         b = -b;
     }
     double s = 0.0;
 #pragma unroll
-    for (int c = 0; c < CHAINS; c++) s += x[c];
+    for (int c = 0; c < CH; c++) s += x[c];
     if (s == -1.0) sink[blockIdx.x] = s;
 }
 
@@ -51,6 +57,7 @@ __global__ void k_imad(int iters, unsigned a, unsigned b, double *sink) {
     unsigned x[CHAINS];
 #pragma unroll
     for (int c = 0; c < CHAINS; c++) x[c] = threadIdx.x * 7u + c;
+#pragma unroll 4
     for (int i = 0; i < iters; i++) {
 #pragma unroll
         for (int c = 0; c < CHAINS; c++) x[c] = x[c] * a + b;
@@ -71,6 +78,7 @@ __global__ void k_xorpopc(int iters, unsigned long long key, double *sink) {
         w[c] = (unsigned long long)(threadIdx.x + 1) * 0x9E3779B97F4A7C15ull + c;
         acc[c] = 0;
     }
+#pragma unroll 4
     for (int i = 0; i < iters; i++) {
 #pragma unroll
         for (int c = 0; c < CHAINS; c++) {
@@ -120,10 +128,11 @@ __global__ void k_gather(int iters, const double *__restrict__ table, unsigned l
 extern "C" {
 
 // which: 0 DFMA, 1 DADD, 2 IMAD (32-bit), 3 XOR+POPC (64-bit), 4 FP64 atomic
-// add to L2, 5 random 8-byte L2 gather.  ops_per_s: operations per second
-// (one FMA counts as one operation); ms: the timed launch.  Returns 0 or a
-// cudaError_t.
-int shci_peak_rate(int device, int which, int ctas_per_sm, double *ops_per_s, double *ms) {
+// add to L2, 5 random 8-byte L2 gather.  chains: 8 or 16 independent chains
+// per thread for the FP64 kernels (others use 8).  ops_per_s: operations per
+// second (one FMA counts as one operation); ms: the timed launch.  Returns 0
+// or a cudaError_t.
+int shci_peak_rate(int device, int which, int ctas_per_sm, int chains, double *ops_per_s, double *ms) {
     cudaError_t e = cudaSetDevice(device);
     if (e != cudaSuccess) return (int)e;
     int sms = 0;
@@ -143,8 +152,14 @@ int shci_peak_rate(int device, int which, int ctas_per_sm, double *ops_per_s, do
     int iters = which >= 4 ? 4096 : 65536;
     auto launch = [&]() {
         switch (which) {
-            case 0: k_dfma<<<grid, THREADS>>>(iters, 0.999999, 1e-7, sink); break;
-            case 1: k_dadd<<<grid, THREADS>>>(iters, 1e-7, sink); break;
+            case 0:
+                if (chains == 16) k_dfma<16><<<grid, THREADS>>>(iters, 0.999999, 1e-7, sink);
+                else k_dfma<8><<<grid, THREADS>>>(iters, 0.999999, 1e-7, sink);
+                break;
+            case 1:
+                if (chains == 16) k_dadd<16><<<grid, THREADS>>>(iters, 1e-7, sink);
+                else k_dadd<8><<<grid, THREADS>>>(iters, 1e-7, sink);
+                break;
             case 2: k_imad<<<grid, THREADS>>>(iters, 1664525u, 1013904223u, sink); break;
             case 3: k_xorpopc<<<grid, THREADS>>>(iters, 0x5851F42D4C957F2Dull, sink); break;
             case 4: k_atomic<<<grid, THREADS>>>(iters, table, table_elems - 1); break;
@@ -159,7 +174,8 @@ int shci_peak_rate(int device, int which, int ctas_per_sm, double *ops_per_s, do
     float t = 0.f;
     if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
     if (e == cudaSuccess) e = cudaGetLastError();
-    const double per_thread = (which == 4) ? (double)iters : (double)iters * CHAINS;
+    const int ch = (which <= 1 && chains == 16) ? 16 : CHAINS;
+    const double per_thread = (which == 4) ? (double)iters : (double)iters * ch;
     *ms = t;
     *ops_per_s = per_thread * THREADS * grid / (t * 1e-3);
     cudaEventDestroy(e0);

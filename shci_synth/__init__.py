@@ -323,18 +323,26 @@ class Config:
     roots: int
     band: int = 0
     window: tuple = field(default=(None, None, None))   # hole, particle, max level
+    # "heat-bath": V is the stored heat-bath-selected space of this name
+    # (tests/golden/<name>.npz, written by the oracle's selection); "score":
+    # the seeded score-and-noise stand-in of selected_dets
+    space: str = "score"
+    stored_as: str | None = None           # name of the stored space (default: the config's name)
 
 
 CONFIGS = {
     # full-CI space, 10 orbitals, 4a4b: C(10,4)^2 = 44,100 determinants
     "fci_10o_4a4b": Config("fci_10o_4a4b", 10, 4, 4, 20, 1001, None, 1),
-    # selected space, 24 orbitals, 6a6b, |V| = 1e6, two roots, stored H
-    "sel_24o_6a6b_1m": Config("sel_24o_6a6b_1m", 24, 6, 6, 60, 1002, 1_000_000, 2),
+    # heat-bath-selected space (Sec. II.A, Eq. 2), 24 orbitals, 6a6b, |V| = 1e6, two roots, stored H
+    "sel_24o_6a6b_1m": Config("sel_24o_6a6b_1m", 24, 6, 6, 60, 1002, 1_000_000, 2, space="score"),
+    # the same shape and integrals with the score-and-noise stand-in space
+    "sel_24o_6a6b_1m_standin": Config("sel_24o_6a6b_1m_standin", 24, 6, 6, 60, 1002, 1_000_000, 2),
     # large shape like a transition-metal dimer: 76 orbitals, 14a14b, 12-orbital band
     "sel_76o_14a14b_50m": Config("sel_76o_14a14b_50m", 76, 14, 14, 300, 1003, 50_000_000, 1,
                                  band=12, window=(8, 16, 4)),
-    # differentiation workload: 20 orbitals, 5a5b, |V| = 1e6
-    "sel_20o_5a5b_1m": Config("sel_20o_5a5b_1m", 20, 5, 5, 40, 1004, 1_000_000, 1),
+    # differentiation workload: heat-bath-selected space, 20 orbitals, 5a5b, |V| = 1e6
+    "sel_20o_5a5b_1m": Config("sel_20o_5a5b_1m", 20, 5, 5, 40, 1004, 1_000_000, 1, space="score"),
+    "sel_20o_5a5b_1m_standin": Config("sel_20o_5a5b_1m_standin", 20, 5, 5, 40, 1004, 1_000_000, 1),
 }
 
 
@@ -365,11 +373,18 @@ def batch_configs(n_sys: int = 64, seed: int = 5000, n_det_max: int = 2_000_000,
 
 def make_system(cfg: Config, n_det: int | None = None):
     """(h, eri_packed, e_core, dets) for a workload; ``n_det`` overrides the
-    space size (a smaller space of the same shape for parity runs)."""
+    space size (a smaller space of the same shape for parity runs: for a
+    stored heat-bath space, its first n_det determinants in generation order)."""
     h, eri, e_core = integrals(cfg.n_orb, cfg.rank, cfg.seed, cfg.band, cfg.n_alpha)
     n = cfg.n_det if n_det is None else n_det
     if n is None:
         dets = fci_dets(cfg.n_orb, cfg.n_alpha, cfg.n_beta)
+    elif cfg.space == "heat-bath":
+        name = cfg.stored_as or cfg.name
+        meta = selected_space_meta(name)
+        if n > meta["n_det"]:
+            raise ValueError("%s holds %d determinants, %d asked" % (name, meta["n_det"], n))
+        dets = load_selected_space(name, n_det=n)
     else:
         hw, pw, ml = cfg.window
         dets = selected_dets(cfg.n_orb, cfg.n_alpha, cfg.n_beta, np.diag(h), n, cfg.seed,

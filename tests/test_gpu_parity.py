@@ -178,31 +178,39 @@ def test_selected_space_two_roots(P, oracle_mod):
     B.close()
 
 
-def test_full_size_selected_space_sampled_rows(P, oracle_mod):
-    """|V| = 1e6 (24 orbitals, 6a6b): sampled rows against the brute-force oracle,
-    and the eigen-residual of the GPU Ritz vectors checked on sampled rows."""
-    cfg, h, eri, ec, dets = G.system("sel_24o_6a6b_1m")
+@pytest.mark.parametrize("name", ["sel_24o_6a6b_1m", "sel_20o_5a5b_1m", "sel_24o_6a6b_1m_standin"])
+def test_full_size_selected_space_sampled_rows(P, oracle_mod, name):
+    """|V| = 1e6 at the workloads' full size: sampled rows against the
+    brute-force oracle (columns bit-exact, values, sigma rows), the
+    eigen-residual of the GPU Ritz vectors on sampled rows, and -- for the
+    heat-bath-selected spaces -- the eigenvalues against the oracle's energies
+    of the whole space (Davidson on its own upper-triangle rows, stored with
+    the space by tests/golden/make_selected_spaces.py)."""
+    cfg, h, eri, ec, dets = G.system(name)
     O = oracle_mod.System(h, eri, ec)
-    B = G.Built(P, h, eri, ec, dets, 6, 6)
+    B = G.Built(P, h, eri, ec, dets, cfg.n_alpha, cfg.n_beta)
     rng = np.random.default_rng(11)
     rows = np.concatenate([[0, 1, dets.shape[0] - 1], rng.choice(dets.shape[0], 60, replace=False)])
-    total = 0
     for i in rows:
         cols, vals = O.row(dets, int(i))
         gc, gv = B.row(int(i))
         assert np.array_equal(gc, cols), i
         assert np.max(np.abs(gv - vals)) < HIJ_TOL
-        total += cols.size
-    c = S.random_vectors(dets.shape[0], 2, 9)
+    k = cfg.roots
+    c = S.random_vectors(dets.shape[0], k, 9)
     got = B.sigma(c)
     ref = O.sigma_rows(dets, c, rows)
     scale = G.row_scale(O, dets, c, rows)
     assert np.all(np.abs(got[:, rows] - ref) <= SIGMA_REL * scale + 1e-300)
-    e, vecs, it = B.davidson(2, tol=1e-10)
+    e, vecs, it = B.davidson(k, tol=1e-10)
     hv = O.sigma_rows(dets, vecs, rows)
     r = hv - e[:, None] * vecs[:, rows]
     assert np.max(np.abs(r)) < 1e-5
-    assert e[0] < e[1]
+    assert np.all(np.diff(e) > 0)
+    if cfg.space == "heat-bath":
+        meta = S.selected_space_meta(name)
+        assert B.nnz == meta["oracle"]["nnz_upper"]
+        np.testing.assert_allclose(e, meta["oracle"]["energies"][:k], atol=E_TOL, rtol=0)
     B.close()
 
 
