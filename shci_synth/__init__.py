@@ -334,7 +334,7 @@ CONFIGS = {
     # full-CI space, 10 orbitals, 4a4b: C(10,4)^2 = 44,100 determinants
     "fci_10o_4a4b": Config("fci_10o_4a4b", 10, 4, 4, 20, 1001, None, 1),
     # heat-bath-selected space (Sec. II.A, Eq. 2), 24 orbitals, 6a6b, |V| = 1e6, two roots, stored H
-    "sel_24o_6a6b_1m": Config("sel_24o_6a6b_1m", 24, 6, 6, 60, 1002, 1_000_000, 2, space="score"),
+    "sel_24o_6a6b_1m": Config("sel_24o_6a6b_1m", 24, 6, 6, 60, 1002, 1_000_000, 2, space="heat-bath"),
     # the same shape and integrals with the score-and-noise stand-in space
     "sel_24o_6a6b_1m_standin": Config("sel_24o_6a6b_1m_standin", 24, 6, 6, 60, 1002, 1_000_000, 2),
     # large shape like a transition-metal dimer: 76 orbitals, 14a14b, 12-orbital band

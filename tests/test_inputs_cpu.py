@@ -41,3 +41,34 @@ def test_full_ci_space_and_integral_layout():
     assert np.array_equal(h, h.T)
     assert eri.shape == (S.eri_len(10),)
     assert S.eri_len(10) == S.n_pair(10) * (S.n_pair(10) + 1) // 2
+
+
+@pytest.mark.parametrize("name", ["sel_24o_6a6b_1m", "sel_20o_5a5b_1m"])
+def test_stored_heat_bath_space(name, oracle_mod):
+    """A stored heat-bath space: its SHA-256 matches the record, it is laid out
+    as the library expects, its blocks add up, and its first two blocks are
+    exactly what the oracle's selection (Sec. II.A, Eq. 2) gives from the aufbau
+    determinant at eps1 = 1e-2 and, after the dense ground state(s) of that
+    space, at 1e-2 x 0.7."""
+    import os
+    if not os.path.exists(os.path.join(S.SPACES_DIR, name + ".npz")):
+        pytest.skip("space %s not stored" % name)
+    cfg = S.config(name)
+    meta = S.selected_space_meta(name)
+    V = S.load_selected_space(name)                       # checks the SHA-256
+    assert V.shape == (meta["n_det"], 2) and V.dtype == np.uint64
+    blocks = meta["selection"]["blocks"]
+    assert sum(blocks) == V.shape[0] and blocks[0] == 1
+    assert np.array_equal(V[0], S.hf_dets(cfg.n_orb, cfg.n_alpha, cfg.n_beta)[0])
+    assert np.unique(V, axis=0).shape[0] == V.shape[0]
+    assert np.all(_popcounts(V[:, :1]) == cfg.n_alpha) and np.all(_popcounts(V[:, 1:]) == cfg.n_beta)
+    h, eri, ec = S.integrals(cfg.n_orb, cfg.rank, cfg.seed, cfg.band, cfg.n_alpha)
+    O = oracle_mod.System(h, eri, ec)
+    eps1 = meta["selection"]["eps1_start"]
+    b1 = O.select(V[:1], np.ones((1, 1)), eps1)
+    assert np.array_equal(b1, V[1:1 + blocks[1]])
+    n2 = 1 + blocks[1]
+    k = min(meta["selection"]["roots"], n2)
+    _, c = O.lowest_eigenpairs(V[:n2], k)
+    b2 = O.select(V[:n2], c, eps1 * meta["selection"]["eps1_factor"])
+    assert np.array_equal(b2, V[n2:n2 + blocks[2]])
