@@ -15,10 +15,24 @@ namespace shci {
 
 constexpr int SIGMA_THREADS = 256;
 
-// One warp per row.  x and y are [n][K] (INTER) or [K][n].  Each lane takes
-// SR nonzeros per step and issues all their loads before the FMAs (more
-// gathers of x in flight per warp); a lane still accumulates its nonzeros in
-// ascending order.
+// Rows per warp group: a warp takes R consecutive rows one after another,
+// keeps each row's per-lane partial sums in registers, and reduces the R rows
+// together at the end (below); fewer rows for more vectors (registers).
+template <int K>
+struct SigmaRows {
+    static constexpr int R = K <= 2 ? 8 : (K <= 4 ? 4 : 2);
+};
+
+// A warp per group of R consecutive rows.  x and y are [n][K] (INTER) or
+// [K][n].  For each row of the group, each lane takes SR nonzeros per step and
+// issues all their loads before the FMAs (more gathers of x in flight); a step
+// slot with no nonzero of the row in any lane is skipped by a warp-uniform
+// branch.  The FP64 pipe is the binding unit, so the per-row cost besides the
+// one FMA per nonzero and vector is kept small: instead of a 5-level shuffle
+// reduction per row and vector, the R rows' partial sums are reduced together
+// by a butterfly that halves the rows a lane holds at each of the first
+// log2(R) levels ((R - 1) + (5 - log2 R) adds per vector for R rows), and one
+// lane per row writes y = H_ii x + sum.
 template <int K, bool INTER>
 __global__ void __launch_bounds__(SIGMA_THREADS) k_sigma_stored(int64_t n, const int64_t *__restrict__ rowptr,
                                                                 const int32_t *__restrict__ col,
@@ -26,58 +40,93 @@ __global__ void __launch_bounds__(SIGMA_THREADS) k_sigma_stored(int64_t n, const
                                                                 const double *__restrict__ diag,
                                                                 const double *__restrict__ x, double *__restrict__ y) {
     constexpr int SR = K <= 2 ? 4 : 2;
+    constexpr int R = SigmaRows<K>::R;
+    constexpr int LOG_R = R == 8 ? 3 : (R == 4 ? 2 : (R == 2 ? 1 : 0));
     const int lane = threadIdx.x & 31;
+    const int64_t n_groups = (n + R - 1) / R;
     const int64_t warps = (int64_t)gridDim.x * (SIGMA_THREADS / 32);
-    for (int64_t i = ((int64_t)blockIdx.x * SIGMA_THREADS + threadIdx.x) >> 5; i < n; i += warps) {
-        double acc[K];
+    for (int64_t g = ((int64_t)blockIdx.x * SIGMA_THREADS + threadIdx.x) >> 5; g < n_groups; g += warps) {
+        const int64_t i0 = g * R;
+        double acc[R][K];
 #pragma unroll
-        for (int q = 0; q < K; q++) acc[q] = 0.0;
-        const int64_t beg = rowptr[i], end = rowptr[i + 1];
-        for (int64_t p0 = beg + lane; p0 < end; p0 += 32 * SR) {
-            int64_t j[SR];
-            double v[SR], xv[SR][K];
+        for (int r = 0; r < R; r++)
 #pragma unroll
-            for (int u = 0; u < SR; u++) {
-                const int64_t p = p0 + 32 * u;
-                const bool in = p < end;
-                j[u] = in ? (int64_t)__ldg(&col[p]) : -1;
-                v[u] = in ? __ldg(&val[p]) : 0.0;
-            }
+            for (int q = 0; q < K; q++) acc[r][q] = 0.0;
 #pragma unroll
-            for (int u = 0; u < SR; u++) {
-                if (j[u] >= 0) {
-                    if (INTER && K == 2) {
-                        const double2 c2 = __ldg(reinterpret_cast<const double2 *>(x) + j[u]);
-                        xv[u][0] = c2.x;
-                        xv[u][K - 1] = c2.y;
+        for (int r = 0; r < R; r++) {
+            if (i0 + r >= n) break;                       // warp-uniform: the last group may be short
+            const int64_t beg = rowptr[i0 + r], end = rowptr[i0 + r + 1];
+            for (int64_t p0 = beg; p0 < end; p0 += 32 * SR) {
+                int64_t j[SR];
+                double v[SR], xv[SR][K];
+#pragma unroll
+                for (int u = 0; u < SR; u++) {
+                    const int64_t p = p0 + 32 * u + lane;
+                    const bool in = p < end;
+                    j[u] = in ? (int64_t)__ldg(&col[p]) : -1;
+                    v[u] = in ? __ldg(&val[p]) : 0.0;
+                }
+#pragma unroll
+                for (int u = 0; u < SR; u++) {
+                    if (j[u] >= 0) {
+                        if (INTER && K == 2) {
+                            const double2 c2 = __ldg(reinterpret_cast<const double2 *>(x) + j[u]);
+                            xv[u][0] = c2.x;
+                            xv[u][K - 1] = c2.y;
+                        } else {
+#pragma unroll
+                            for (int q = 0; q < K; q++)
+                                xv[u][q] = INTER ? __ldg(&x[j[u] * K + q]) : __ldg(&x[q * n + j[u]]);
+                        }
                     } else {
 #pragma unroll
-                        for (int q = 0; q < K; q++) xv[u][q] = INTER ? __ldg(&x[j[u] * K + q]) : __ldg(&x[q * n + j[u]]);
+                        for (int q = 0; q < K; q++) xv[u][q] = 0.0;
                     }
-                } else {
-#pragma unroll
-                    for (int q = 0; q < K; q++) xv[u][q] = 0.0;
                 }
-            }
 #pragma unroll
-            for (int u = 0; u < SR; u++) {
-                if (j[u] >= 0) {
+                for (int u = 0; u < SR; u++) {
+                    if (p0 + 32 * u < end) {                  // warp-uniform: some lane holds a nonzero
 #pragma unroll
-                    for (int q = 0; q < K; q++) acc[q] = fma(v[u], xv[u][q], acc[q]);
+                        for (int q = 0; q < K; q++) acc[r][q] = fma(v[u], xv[u][q], acc[r][q]);
+                    }
                 }
             }
         }
+        // butterfly over the group's rows: at level t (lane mask 16 >> t) a lane
+        // keeps the upper or lower half of the rows it holds and adds its
+        // partner's partial sums of the half it keeps
 #pragma unroll
-        for (int q = 0; q < K; q++) {
+        for (int t = 0; t < LOG_R; t++) {
+            const int mask = 16 >> t;
+            const int half = R >> (t + 1);
+            const bool upper = (lane & mask) != 0;
 #pragma unroll
-            for (int o = 16; o >= 1; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+            for (int r = 0; r < half; r++) {
+#pragma unroll
+                for (int q = 0; q < K; q++) {
+                    const double send = upper ? acc[r][q] : acc[r + half][q];
+                    const double keep = upper ? acc[r + half][q] : acc[r][q];
+                    acc[r][q] = keep + __shfl_xor_sync(0xffffffffu, send, mask);
+                }
+            }
         }
-        if (lane == 0) {
+        // the remaining 5 - log2(R) levels: plain sums over the lanes that hold the same row
+#pragma unroll
+        for (int mask = 16 >> LOG_R; mask >= 1; mask >>= 1) {
+#pragma unroll
+            for (int q = 0; q < K; q++) acc[0][q] += __shfl_xor_sync(0xffffffffu, acc[0][q], mask);
+        }
+        // the row this lane now holds: bit (4 - t) of the lane selects half R >> (t + 1)
+        int r_own = 0;
+#pragma unroll
+        for (int t = 0; t < LOG_R; t++) r_own += ((lane >> (4 - t)) & 1) * (R >> (t + 1));
+        const int64_t i = i0 + r_own;
+        if ((lane & ((32 >> LOG_R) - 1)) == 0 && i < n) {
             const double d = diag[i];
 #pragma unroll
             for (int q = 0; q < K; q++) {
                 const int64_t xi = INTER ? i * K + q : q * n + i;
-                y[xi] = fma(d, x[xi], acc[q]);
+                y[xi] = fma(d, x[xi], acc[0][q]);
             }
         }
     }
