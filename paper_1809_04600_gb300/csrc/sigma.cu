@@ -15,12 +15,29 @@ namespace shci {
 
 constexpr int SIGMA_THREADS = 256;
 
+// Shape of the stored product for up to two vectors: rows per warp group,
+// nonzeros per lane per step, CTAs per SM the kernel is compiled for.  On the
+// 1e6-determinant heat-bath space (two vectors, GB300) 8 / 4 / 4 (64
+// registers) took 4.94 ms; shapes that fit more CTAs were slower: 4 / 4 / 5
+// 5.16 ms, 4 / 2 / 5 5.39, 2 / 4 / 6 5.85, 4 / 2 / 6 6.30.
+#ifndef SHCI_SIGMA_R2
+#define SHCI_SIGMA_R2 8
+#endif
+#ifndef SHCI_SIGMA_SR2
+#define SHCI_SIGMA_SR2 4
+#endif
+#ifndef SHCI_SIGMA_MINB2
+#define SHCI_SIGMA_MINB2 4
+#endif
+
 // Rows per warp group: a warp takes R consecutive rows one after another,
 // keeps each row's per-lane partial sums in registers, and reduces the R rows
 // together at the end (below); fewer rows for more vectors (registers).
 template <int K>
 struct SigmaRows {
-    static constexpr int R = K <= 2 ? 8 : (K <= 4 ? 4 : 2);
+    static constexpr int R = K <= 2 ? SHCI_SIGMA_R2 : (K <= 4 ? 4 : 2);
+    static constexpr int SR = K <= 2 ? SHCI_SIGMA_SR2 : 2;
+    static constexpr int MINB = K <= 2 ? SHCI_SIGMA_MINB2 : 1;
 };
 
 // A warp per group of R consecutive rows.  x and y are [n][K] (INTER) or
@@ -34,12 +51,13 @@ struct SigmaRows {
 // log2(R) levels ((R - 1) + (5 - log2 R) adds per vector for R rows), and one
 // lane per row writes y = H_ii x + sum.
 template <int K, bool INTER>
-__global__ void __launch_bounds__(SIGMA_THREADS) k_sigma_stored(int64_t n, const int64_t *__restrict__ rowptr,
+__global__ void __launch_bounds__(SIGMA_THREADS, SigmaRows<K>::MINB) k_sigma_stored(int64_t n,
+                                                                                   const int64_t *__restrict__ rowptr,
                                                                 const int32_t *__restrict__ col,
                                                                 const double *__restrict__ val,
                                                                 const double *__restrict__ diag,
                                                                 const double *__restrict__ x, double *__restrict__ y) {
-    constexpr int SR = K <= 2 ? 4 : 2;
+    constexpr int SR = SigmaRows<K>::SR;
     constexpr int R = SigmaRows<K>::R;
     constexpr int LOG_R = R == 8 ? 3 : (R == 4 ? 2 : (R == 2 ? 1 : 0));
     const int lane = threadIdx.x & 31;
