@@ -257,11 +257,14 @@ __device__ void sigma_rows(const BSys &S, int nb, int64_t r0, int cnt) {
                 }
             }
         }
-        // reduce over the row's LPR lanes (the whole warp takes part)
+        // reduce over the row's LPR lanes (the whole warp takes part), only
+        // the nb vectors in use (nb is warp-uniform; FP64 adds are the scarce unit)
 #pragma unroll
         for (int q = 0; q < BK; q++) {
+            if (q < nb) {
 #pragma unroll
-            for (int o = LPR / 2; o >= 1; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+                for (int o = LPR / 2; o >= 1; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+            }
         }
         if (ok && sl == 0) {
             const double d = S.diag[i];
