@@ -341,7 +341,7 @@ CONFIGS = {
     "sel_76o_14a14b_50m": Config("sel_76o_14a14b_50m", 76, 14, 14, 300, 1003, 50_000_000, 1,
                                  band=12, window=(8, 16, 4)),
     # differentiation workload: heat-bath-selected space, 20 orbitals, 5a5b, |V| = 1e6
-    "sel_20o_5a5b_1m": Config("sel_20o_5a5b_1m", 20, 5, 5, 40, 1004, 1_000_000, 1, space="score"),
+    "sel_20o_5a5b_1m": Config("sel_20o_5a5b_1m", 20, 5, 5, 40, 1004, 1_000_000, 1, space="heat-bath"),
     "sel_20o_5a5b_1m_standin": Config("sel_20o_5a5b_1m_standin", 20, 5, 5, 40, 1004, 1_000_000, 1),
 }
 
