@@ -17,14 +17,16 @@ constexpr int SIGMA_THREADS = 256;
 
 // Shape of the stored product for up to two vectors: rows per warp group,
 // nonzeros per lane per step, CTAs per SM the kernel is compiled for.  On the
-// 1e6-determinant heat-bath space (two vectors, GB300) 8 / 4 / 4 (64
-// registers) took 4.94 ms; shapes that fit more CTAs were slower: 4 / 4 / 5
-// 5.16 ms, 4 / 2 / 5 5.39, 2 / 4 / 6 5.85, 4 / 2 / 6 6.30.
+// 1e6-determinant heat-bath space (two vectors, GB300) 4 / 8 / 4 (64
+// registers) took 4.83 ms and 8 / 4 / 4 4.93 ms; shapes that fit more CTAs
+// were slower (4 / 4 / 5 5.16 ms, 4 / 2 / 5 5.39, 2 / 4 / 6 5.85, 4 / 2 / 6
+// 6.30), and so were deeper steps at fewer CTAs (8 / 6 / 3 5.18, 4 / 8 / 3
+// 5.25, 8 / 8 / 3 5.32, 8 / 8 / 2 5.59); deeper steps at 4 CTAs spill.
 #ifndef SHCI_SIGMA_R2
-#define SHCI_SIGMA_R2 8
+#define SHCI_SIGMA_R2 4
 #endif
 #ifndef SHCI_SIGMA_SR2
-#define SHCI_SIGMA_SR2 4
+#define SHCI_SIGMA_SR2 8
 #endif
 #ifndef SHCI_SIGMA_MINB2
 #define SHCI_SIGMA_MINB2 4
@@ -33,11 +35,13 @@ constexpr int SIGMA_THREADS = 256;
 // Rows per warp group: a warp takes R consecutive rows one after another,
 // keeps each row's per-lane partial sums in registers, and reduces the R rows
 // together at the end (below); fewer rows for more vectors (registers).
-template <int K>
+template <int K, bool INTER>
 struct SigmaRows {
-    static constexpr int R = K <= 2 ? SHCI_SIGMA_R2 : (K <= 4 ? 4 : 2);
-    static constexpr int SR = K <= 2 ? SHCI_SIGMA_SR2 : 2;
-    static constexpr int MINB = K <= 2 ? SHCI_SIGMA_MINB2 : 1;
+    // the shapes the Davidson iteration launches (one vector, or two interleaved)
+    static constexpr bool TUNED = K == 1 || (K == 2 && INTER);
+    static constexpr int R = TUNED ? SHCI_SIGMA_R2 : (K <= 4 ? 4 : 2);
+    static constexpr int SR = TUNED ? SHCI_SIGMA_SR2 : 2;
+    static constexpr int MINB = TUNED ? SHCI_SIGMA_MINB2 : 1;
 };
 
 // A warp per group of R consecutive rows.  x and y are [n][K] (INTER) or
@@ -51,14 +55,14 @@ struct SigmaRows {
 // log2(R) levels ((R - 1) + (5 - log2 R) adds per vector for R rows), and one
 // lane per row writes y = H_ii x + sum.
 template <int K, bool INTER>
-__global__ void __launch_bounds__(SIGMA_THREADS, SigmaRows<K>::MINB) k_sigma_stored(int64_t n,
+__global__ void __launch_bounds__(SIGMA_THREADS, SigmaRows<K, INTER>::MINB) k_sigma_stored(int64_t n,
                                                                                    const int64_t *__restrict__ rowptr,
                                                                 const int32_t *__restrict__ col,
                                                                 const double *__restrict__ val,
                                                                 const double *__restrict__ diag,
                                                                 const double *__restrict__ x, double *__restrict__ y) {
-    constexpr int SR = SigmaRows<K>::SR;
-    constexpr int R = SigmaRows<K>::R;
+    constexpr int SR = SigmaRows<K, INTER>::SR;
+    constexpr int R = SigmaRows<K, INTER>::R;
     constexpr int LOG_R = R == 8 ? 3 : (R == 4 ? 2 : (R == 2 ? 1 : 0));
     const int lane = threadIdx.x & 31;
     const int64_t n_groups = (n + R - 1) / R;
