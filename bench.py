@@ -972,18 +972,14 @@ def run_batch(args):
     torch.cuda.synchronize()
     t_batch = time.perf_counter() - t
     st = P.shci_batch_get_stats(b)
+    modes = P.shci_batch_get_modes(b, len(systems))
     P.shci_batch_destroy(b)
-    # sequential: one context per system, same storage decisions, Davidson timed alone
+    # sequential: one context per system, the batch's storage decisions, Davidson timed alone
     seq_time, seq_e, seq_it = 0.0, [], []
-    left = budget
-    for d in systems:
+    for d, mode in zip(systems, modes):
         c2 = P.Context(0, torch.cuda.current_stream())
         P.shci_load_integrals(c2.handle, d["n_orb"], d["e_core"], d["h"], d["eri"])
-        nnz = P.shci_build_connectivity(c2.handle, d["n_alpha"], d["n_beta"], d["dets"], P.SHCI_ON_THE_FLY)
-        mode = P.SHCI_STORED if 12.0 * (2 * nnz + 0) < left else P.SHCI_ON_THE_FLY
-        if mode == P.SHCI_STORED:
-            P.shci_build_connectivity(c2.handle, d["n_alpha"], d["n_beta"], d["dets"], P.SHCI_STORED)
-            left -= 12.0 * 2 * nnz
+        P.shci_build_connectivity(c2.handle, d["n_alpha"], d["n_beta"], d["dets"], int(mode))
         torch.cuda.synchronize()
         t = time.perf_counter()
         es, its, rcs = P.shci_davidson(c2.handle, k, TOL, MAX_ITER, check=False)
@@ -996,7 +992,8 @@ def run_batch(args):
     print(json.dumps({"workload": "64 systems: n_orb U{12..30}, 3-8 electrons per spin, |V| log-uniform "
                                   "1e4..2e6 (capped at half the full-CI size), 4 roots each, FP64",
                       "total_det": st["total_det"], "total_nnz_upper": st["total_nnz_upper"],
-                      "n_stored": st["n_stored"], "n_on_the_fly": st["n_on_the_fly"], "gen_s": t_gen,
+                      "n_stored": st["n_stored"], "n_stored_upper": st["n_stored_upper"],
+                      "n_on_the_fly": st["n_on_the_fly"], "gen_s": t_gen,
                       "create_s": t_create, "batched_s": t_batch, "batched_device_ms": st["solve_ms"],
                       "sequential_s": seq_time, "speedup": seq_time / t_batch,
                       "max_abs_dE_vs_sequential": float(np.max(np.abs(e - seq_e))),
@@ -1046,7 +1043,8 @@ def main():
     ap.add_argument("--workload", default="main",
                     choices=["main", "fci", "large", "adjoint", "batch", "select", "extend", "peaks"],
                     help="main: the bench line; others print the measurement line of another workload")
-    ap.add_argument("--batch-budget-gb", type=float, default=180.0)
+    ap.add_argument("--batch-budget-gb", type=float, default=240.0,
+                    help="batch workload: device memory the stored matrices may take (capped at 0.8 x free)")
     ap.add_argument("--large-iters", type=int, default=3,
                     help="main bench line: Davidson iterations of the bounded 5e7 section (0: skip it)")
     ap.add_argument("--large-davidson", action="store_true",

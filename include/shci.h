@@ -62,9 +62,16 @@ enum shci_status {
 
 enum shci_mem_space { SHCI_MEM_HOST = 0, SHCI_MEM_DEVICE = 1 };
 
-/* How H is applied: stored upper+lower sparse rows, recomputed each product,
- * or stored when it fits the device's free memory (with a margin). */
-enum shci_mode { SHCI_STORED = 0, SHCI_ON_THE_FLY = 1, SHCI_AUTO = 2 };
+/* How H is applied (Sec. III; Sec. VIII for the on-the-fly product):
+ * SHCI_STORED      both triangles as sparse rows, 12 bytes per nonzero (the
+ *                  product is a pure gather, the fastest form);
+ * SHCI_STORED_UPPER the upper triangle alone, as the paper stores H: half the
+ *                  memory, the transposed half added with atomic adds
+ *                  (summation order then varies between runs);
+ * SHCI_ON_THE_FLY  recomputed each product, nothing stored;
+ * SHCI_AUTO        the first of the three whose storage fits 80 % of the
+ *                  device's free memory (and the batch budget, in a batch). */
+enum shci_mode { SHCI_STORED = 0, SHCI_ON_THE_FLY = 1, SHCI_AUTO = 2, SHCI_STORED_UPPER = 3 };
 
 /* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
  * on that device (NULL: the context creates and owns a non-blocking stream).
@@ -89,7 +96,8 @@ int shci_load_integrals(shci_ctx *ctx, int n_orb, double e_core, const double *h
 /* Build the connectivity of V = dets[0 .. n_det) (Sec. III): helper lists
  * (unique alpha/beta strings, per-string determinant lists, alpha-single
  * lists; Table I), the cached diagonal H_ii (Sec. V.B) and, in SHCI_STORED
- * mode, every off-diagonal H_ij != structural zero in both triangles.
+ * mode, every off-diagonal H_ij != structural zero in both triangles (in
+ * SHCI_STORED_UPPER mode those with i < j).
  * dets: [n_det][2W] uint64 as above, every alpha string with n_alpha bits and
  * every beta string with n_beta bits below n_orb; determinants must be
  * distinct (SHCI_ERR_INVALID otherwise).  n_det in [1, 2^31 - 1].
@@ -113,7 +121,9 @@ int shci_build_connectivity(shci_ctx *ctx, int n_alpha, int n_beta, int64_t n_de
  * (per-string lists in beta order, occupancy-bitmap lookups).  The paper's
  * switch between the two list orders sits at 20 %; full_fraction <= 0 takes
  * 0.2.  The mode of the last build is kept (SHCI_AUTO re-decides against the
- * memory left); SHCI_ON_THE_FLY contexts get the count only.  n_new = 0 is a
+ * memory left: a stored matrix whose grown form no longer fits goes to the
+ * next form of SHCI_AUTO's order, V being rebuilt when both triangles give
+ * way to the upper one); SHCI_ON_THE_FLY contexts get the count only.  n_new = 0 is a
  * no-op.  *nnz_upper_out (may be NULL) as for shci_build_connectivity.
  * SHCI_ERR_STATE without a completed build; SHCI_ERR_INVALID, with the
  * context unchanged, for an unknown mem_space, n_new < 0, a NULL pointer with
@@ -130,7 +140,8 @@ int shci_get_diag(shci_ctx *ctx, double *diag, int mem_space);
 /* Export the stored upper triangle as (i, j, H_ij), i < j, rows ascending and
  * each row in ascending j.  Host buffers of capacity `cap`; *n_out receives
  * the pair count (nothing is written when cap < count).  For parity checks
- * and debugging; SHCI_ERR_STATE unless built in SHCI_STORED mode. */
+ * and debugging; SHCI_ERR_STATE unless built in SHCI_STORED or
+ * SHCI_STORED_UPPER mode. */
 int shci_get_pairs(shci_ctx *ctx, int64_t cap, int64_t *i_out, int64_t *j_out,
                    double *hij_out, int64_t *n_out);
 
@@ -138,7 +149,8 @@ int shci_get_pairs(shci_ctx *ctx, int64_t cap, int64_t *i_out, int64_t *j_out,
  * columns j != row in ascending order and their H_ij (host buffers of
  * capacity `cap`; *n_out receives the row length, nothing is written when
  * cap is smaller).  For sampled-row parity checks on large spaces;
- * SHCI_ERR_STATE unless built in SHCI_STORED mode. */
+ * SHCI_ERR_STATE unless built in SHCI_STORED mode (an upper-triangle matrix
+ * does not hold a row's lower part as a row). */
 int shci_get_row(shci_ctx *ctx, int64_t row, int64_t cap, int64_t *cols, double *vals, int64_t *n_out);
 
 /* sigma = H c for k vectors (k in [1, 8]), c and sigma [k][n_det] (Sec. V.B:
@@ -355,10 +367,22 @@ typedef struct {
      * decision, 7 basis rotation, 8 second-pass coefficients, 9 second
      * projection, 10-12 Cholesky-QR, 13 next block, 14 bookkeeping */
     double phase_ms[16];
+    int n_stored_upper;        /* systems stored as their upper triangle (not in n_stored) */
 } shci_batch_stats_t;
 
+/* Build every system's connectivity (Sec. III) and decide how each H is held
+ * within stored_budget_bytes of device memory (< 0: no budget beyond 80 % of
+ * the free memory), 12 bytes per stored nonzero: when the upper triangles of
+ * all systems fit, every system is stored, as both triangles for the systems
+ * taken in ascending order of pair count while the budget allows and as its
+ * upper triangle for the rest; otherwise upper triangles are stored in that
+ * order while they fit and the remaining systems are applied on the fly.
+ * Systems need n_orb <= 64.  The contexts belong to the batch. */
 int shci_batch_create(shci_ctx *ctx, int n_sys, const shci_system_desc *systems, int mem_space,
                       double stored_budget_bytes, shci_batch **out);
+/* The mode each system was given (SHCI_STORED, SHCI_STORED_UPPER or
+ * SHCI_ON_THE_FLY), host [n_sys]; SHCI_ERR_INVALID if cap < n_sys. */
+int shci_batch_get_modes(const shci_batch *b, int cap, int *modes);
 /* energies: host [n_sys][k_roots]; iters, converged: host [n_sys] or NULL.
  * SHCI_ERR_NOT_CONVERGED if a system hit max_iter (its estimates are still
  * written); SHCI_ERR_TIMEOUT if the grid barrier gave up. */
@@ -388,7 +412,7 @@ typedef struct {
     int64_t sigma_vectors;      /* vectors multiplied since reset */
     int64_t kernel_launches;    /* all kernels this context launched since reset */
     int davidson_iters;
-    int mode;                   /* SHCI_STORED or SHCI_ON_THE_FLY after a build */
+    int mode;                   /* SHCI_STORED, SHCI_STORED_UPPER or SHCI_ON_THE_FLY after a build */
     int n_words;                /* W */
     /* last shci_davidson with phase timing on: device-timeline time per part
      * (gaps while the host decides included in the part that follows):

@@ -6,7 +6,8 @@ this package only builds and binds it.  Importing the package does not load
 the library; the first call does, and fails loudly if it was not built.
 """
 from .binding import (  # noqa: F401
-    EXPORTED, SHCI_AUTO, SHCI_MEM_DEVICE, SHCI_MEM_HOST, SHCI_ON_THE_FLY, SHCI_STORED, Context, ShciError,
+    EXPORTED, SHCI_AUTO, SHCI_MEM_DEVICE, SHCI_MEM_HOST, SHCI_ON_THE_FLY, SHCI_STORED, SHCI_STORED_UPPER, Context,
+    ShciError,
     load_library, shci_build_connectivity, shci_create, shci_davidson, shci_davidson_history, shci_destroy,
     shci_get_diag,
     shci_get_pairs, shci_get_row, shci_get_stats, shci_last_error, shci_load_integrals, shci_set_timing, shci_sigma,
@@ -15,7 +16,7 @@ from .binding import shci_energy_backward, shci_pt2, shci_select, shci_sigma_noa
 from .binding import shci_extend_connectivity  # noqa: F401
 from .binding import shci_alias_draw, shci_pt2_3step, shci_pt2_samples, shci_pt2_semistochastic  # noqa: F401
 from .binding import (  # noqa: F401
-    shci_batch_create, shci_batch_davidson, shci_batch_destroy, shci_batch_get_stats,
+    shci_batch_create, shci_batch_davidson, shci_batch_destroy, shci_batch_get_modes, shci_batch_get_stats,
     shci_batch_set_wait_limit,
 )
 from .binding import (  # noqa: F401

@@ -29,6 +29,7 @@ SHCI_MEM_DEVICE = 1
 SHCI_STORED = 0
 SHCI_ON_THE_FLY = 1
 SHCI_AUTO = 2
+SHCI_STORED_UPPER = 3
 
 _STATUS = {1: "INVALID", 2: "OOM", 3: "CUDA", 4: "NOT_CONVERGED", 5: "TIMEOUT", 6: "STATE"}
 
@@ -36,7 +37,8 @@ _STATUS = {1: "INVALID", 2: "OOM", 3: "CUDA", 4: "NOT_CONVERGED", 5: "TIMEOUT", 
 EXPORTED = [
     "shci_create", "shci_destroy", "shci_last_error", "shci_load_integrals", "shci_build_connectivity",
     "shci_extend_connectivity", "shci_get_diag", "shci_get_pairs", "shci_get_row", "shci_sigma", "shci_sigma_noalloc", "shci_energy_backward",
-    "shci_batch_create", "shci_batch_davidson", "shci_batch_get_stats", "shci_batch_set_wait_limit", "shci_batch_destroy",
+    "shci_batch_create", "shci_batch_get_modes", "shci_batch_davidson", "shci_batch_get_stats",
+    "shci_batch_set_wait_limit", "shci_batch_destroy",
     "shci_davidson",
     "shci_davidson_history", "shci_select", "shci_pt2", "shci_alias_draw", "shci_pt2_samples",
     "shci_pt2_semistochastic", "shci_pt2_3step", "shci_get_stats", "shci_set_timing",
@@ -87,6 +89,7 @@ class shci_batch_stats_t(ctypes.Structure):
         ("tuned_lanes_per_row", ctypes.c_int),
         ("tune_ms", ctypes.c_double), ("solve_ms", ctypes.c_double), ("max_iters", ctypes.c_int),
         ("graph", ctypes.c_int), ("grid_ctas", ctypes.c_int), ("phase_ms", ctypes.c_double * 16),
+        ("n_stored_upper", ctypes.c_int),
     ]
 
 
@@ -116,6 +119,7 @@ def load_library(path: str = LIB_PATH):
         "shci_sigma_noalloc": (i32, [vp, i32, vp, vp]),
         "shci_energy_backward": (i32, [vp, vp, f64, vp, vp, i32]),
         "shci_batch_create": (i32, [vp, i32, ctypes.POINTER(shci_system_desc), i32, f64, ctypes.POINTER(vp)]),
+        "shci_batch_get_modes": (i32, [vp, i32, vp]),
         "shci_batch_davidson": (i32, [vp, i32, f64, i32, vp, vp, vp]),
         "shci_batch_get_stats": (i32, [vp, ctypes.POINTER(shci_batch_stats_t)]),
         "shci_batch_set_wait_limit": (i32, [vp, ctypes.c_longlong]),
@@ -443,6 +447,16 @@ def shci_batch_get_stats(batch) -> dict:
     out = {name: getattr(s, name) for name, _ in shci_batch_stats_t._fields_}
     out["phase_ms"] = list(s.phase_ms)
     return out
+
+
+def shci_batch_get_modes(batch, n_sys):
+    """The storage mode each system of the batch was given (SHCI_STORED,
+    SHCI_STORED_UPPER or SHCI_ON_THE_FLY), as an int array [n_sys]."""
+    modes = np.zeros(n_sys, np.int32)
+    rc = load_library().shci_batch_get_modes(batch, int(n_sys), modes.ctypes.data)
+    if rc != SHCI_OK:
+        raise ShciError(rc, "shci_batch_get_modes failed")
+    return modes
 
 
 def shci_batch_set_wait_limit(batch, naps):

@@ -6,7 +6,9 @@
 // iteration runs for all active systems at once and is separated from the
 // next by a grid-wide barrier:
 //   sigma      rows of stored Hamiltonians (CSR row chunks) and work items of
-//              the on-the-fly enumeration (alpha-grouped, then beta-grouped)
+//              the on-the-fly enumeration (alpha-grouped, then beta-grouped);
+//              an upper-triangle matrix sets Y = diag X in the first sigma
+//              phase and adds its rows and their transposes in the second
 //   vectors    slices of every system's vectors (Gram columns, Ritz vectors
 //              and preconditioned residuals, projections, Cholesky-QR)
 //   systems    one CTA per system (reductions of partial sums, the subspace
@@ -81,10 +83,11 @@ struct BatchArgs {
     const BSys *sys;
     BState *st;
     int max_iter;
-    const int32_t *a1_sys, *a1_kind;       // sigma phase 1: kind 0 stored rows, 1 alpha items
+    const int32_t *a1_sys, *a1_kind;       // sigma phase 1: kind 0 stored rows, 1 alpha items,
+                                           // 2 Y = diag X rows of an upper-triangle matrix
     const int64_t *a1_local;
     int64_t n_a1;
-    const int32_t *a2_sys;                 // sigma phase 2: beta items
+    const int32_t *a2_sys, *a2_kind;       // sigma phase 2: kind 0 beta items, 1 upper-triangle rows
     const int64_t *a2_local;
     int64_t n_a2;
     int srows;                             // rows per stored-sigma item
@@ -219,12 +222,17 @@ __device__ void sigma_rows(const BSys &S, int nb, int64_t r0, int cnt) {
     constexpr int RPW = 32 / LPR;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int sub = lane / LPR, sl = lane % LPR;
+    const int64_t *__restrict__ rowptr = S.rowptr;      // the system's arrays in registers
+    const int32_t *__restrict__ col = S.col;
+    const double *__restrict__ val = S.val;
+    const double *X = S.X;
+    double *Y = S.Y;
     const int64_t r1 = min(r0 + cnt, S.n);
     for (int64_t i0 = r0 + (int64_t)warp * RPW; i0 < r1; i0 += (BT / 32) * RPW) {
         const int64_t i = i0 + sub;
         const bool ok = i < r1;
         double acc[BK] = {0.0, 0.0, 0.0, 0.0};
-        const int64_t beg = ok ? S.rowptr[i] : 0, end = ok ? S.rowptr[i + 1] : 0;
+        const int64_t beg = ok ? rowptr[i] : 0, end = ok ? rowptr[i + 1] : 0;
         // SR nonzeros per lane per step, all loads issued before the FMAs: the
         // persistent grid has few warps per SM, so each warp keeps several
         // gathers of X in flight
@@ -236,15 +244,15 @@ __device__ void sigma_rows(const BSys &S, int nb, int64_t r0, int cnt) {
 #pragma unroll
             for (int u = 0; u < SR; u++) {
                 const int64_t p = p0 + LPR * u;
-                j[u] = p < end ? __ldg(&S.col[p]) : -1;
-                v[u] = p < end ? __ldg(&S.val[p]) : 0.0;
+                j[u] = p < end ? __ldg(&col[p]) : -1;
+                v[u] = p < end ? __ldg(&val[p]) : 0.0;
             }
 #pragma unroll
             for (int u = 0; u < SR; u++) {
-                x01[u] = j[u] >= 0 ? __ldcg(reinterpret_cast<const double2 *>(S.X) + 2 * (int64_t)j[u])
+                x01[u] = j[u] >= 0 ? __ldcg(reinterpret_cast<const double2 *>(X) + 2 * (int64_t)j[u])
                                    : make_double2(0.0, 0.0);
                 x23[u] = (nb > 2 && j[u] >= 0)
-                             ? __ldcg(reinterpret_cast<const double2 *>(S.X) + 2 * (int64_t)j[u] + 1)
+                             ? __ldcg(reinterpret_cast<const double2 *>(X) + 2 * (int64_t)j[u] + 1)
                              : make_double2(0.0, 0.0);
             }
 #pragma unroll
@@ -270,8 +278,124 @@ __device__ void sigma_rows(const BSys &S, int nb, int64_t r0, int cnt) {
             const double d = S.diag[i];
 #pragma unroll
             for (int q = 0; q < BK; q++)
-                if (q < nb) S.Y[i * BK + q] = fma(d, __ldcg(&S.X[i * BK + q]), acc[q]);
+                if (q < nb) Y[i * BK + q] = fma(d, __ldcg(&X[i * BK + q]), acc[q]);
         }
+    }
+}
+
+// Y[...] += v as a global-memory reduction (no result returned).  Y comes
+// from the system descriptor, a pointer the compiler cannot place in global
+// memory, and atomicAdd on it compiles to a returning atomic that waits for
+// L2 (measured: every scatter made a round trip); red.global does not.
+__device__ __forceinline__ void red_add(double *p, double v) {
+    asm volatile("red.relaxed.gpu.global.add.f64 [%0], %1;" ::"l"(__cvta_generic_to_global(p)), "d"(v) : "memory");
+}
+
+// rows [r0, r0 + cnt) of an upper-triangle matrix, after Y = diag X
+// (diag_rows, the phase before): each stored H_ij (j > i) adds H_ij X[j] to
+// row i's sum and H_ij X[i] to Y[j] with an atomic add; the row sums are then
+// added to Y[i] atomically (other rows scatter into it in the same phase).
+// One instance per count of vectors in use, out of line: it gets its registers
+// apart from the rest of the persistent kernel.  The scatter keeps a warp
+// waiting on gathers and atomics, and the persistent grid has few warps per
+// SM, so a variant with the registers for it (MINB <= 2) takes 8 nonzeros
+// per lane per step.
+template <int LPR, int NB, int MINB>
+__device__ __noinline__ void sigma_rows_upper_nb(const BSys &S, int64_t r0, int cnt) {
+    constexpr int RPW = 32 / LPR;
+    constexpr int SR = MINB <= 2 ? 8 : 4;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int sub = lane / LPR, sl = lane % LPR;
+    // the system's arrays in registers: the atomic adds below could alias the
+    // descriptor in global memory, which would reload every pointer after each
+    const int64_t *__restrict__ rowptr = S.rowptr;
+    const int32_t *__restrict__ col = S.col;
+    const double *__restrict__ val = S.val;
+    const double *X = S.X;
+    double *Y = S.Y;
+    const int64_t r1 = min(r0 + cnt, S.n);
+    auto load_x = [&](int64_t j, double (&o)[NB]) {
+        if (NB == 1) {
+            o[0] = __ldcg(&X[j * BK]);
+        } else {
+            const double2 a = __ldcg(reinterpret_cast<const double2 *>(X) + 2 * j);
+            o[0] = a.x;
+            o[NB > 1 ? 1 : 0] = a.y;
+            if (NB > 2) {
+                const double2 b = __ldcg(reinterpret_cast<const double2 *>(X) + 2 * j + 1);
+                o[NB > 2 ? 2 : 0] = b.x;
+                if (NB > 3) o[NB > 3 ? 3 : 0] = b.y;
+            }
+        }
+    };
+    for (int64_t i0 = r0 + (int64_t)warp * RPW; i0 < r1; i0 += (BT / 32) * RPW) {
+        const int64_t i = i0 + sub;
+        const bool ok = i < r1;
+        double acc[NB], xi[NB];
+#pragma unroll
+        for (int q = 0; q < NB; q++) {
+            acc[q] = 0.0;
+            xi[q] = 0.0;
+        }
+        const int64_t beg = ok ? rowptr[i] : 0, end = ok ? rowptr[i + 1] : 0;
+        if (ok) load_x(i, xi);
+        for (int64_t p0 = beg + sl; p0 < end; p0 += LPR * SR) {
+            int32_t j[SR];
+            double v[SR], xv[SR][NB];
+#pragma unroll
+            for (int u = 0; u < SR; u++) {
+                const int64_t p = p0 + LPR * u;
+                j[u] = p < end ? __ldg(&col[p]) : -1;
+                v[u] = p < end ? __ldg(&val[p]) : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < SR; u++) {
+                if (j[u] >= 0) load_x(j[u], xv[u]);
+                else
+#pragma unroll
+                    for (int q = 0; q < NB; q++) xv[u][q] = 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < SR; u++) {
+                if (j[u] < 0) continue;
+                double *yj = Y + (int64_t)j[u] * BK;
+#pragma unroll
+                for (int q = 0; q < NB; q++) {
+                    acc[q] = fma(v[u], xv[u][q], acc[q]);
+                    red_add(yj + q, v[u] * xi[q]);
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < NB; q++) {
+#pragma unroll
+            for (int o = LPR / 2; o >= 1; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+        }
+        if (ok && sl == 0) {
+#pragma unroll
+            for (int q = 0; q < NB; q++)
+                if (acc[q] != 0.0) red_add(&Y[i * BK + q], acc[q]);
+        }
+    }
+}
+
+template <int LPR, int MINB>
+__device__ __forceinline__ void sigma_rows_upper(const BSys &S, int nb, int64_t r0, int cnt) {
+    switch (nb) {
+        case 1: sigma_rows_upper_nb<LPR, 1, MINB>(S, r0, cnt); break;
+        case 2: sigma_rows_upper_nb<LPR, 2, MINB>(S, r0, cnt); break;
+        case 3: sigma_rows_upper_nb<LPR, 3, MINB>(S, r0, cnt); break;
+        default: sigma_rows_upper_nb<LPR, 4, MINB>(S, r0, cnt); break;
+    }
+}
+
+// Y[i][q] = diag_i X[i][q], q < nb, for rows [r0, r0 + cnt): the start of an
+// upper-triangle product
+__device__ void diag_rows(const BSys &S, int nb, int64_t r0, int cnt) {
+    const int64_t r1 = min(r0 + cnt, S.n);
+    for (int64_t e = r0 * BK + threadIdx.x; e < r1 * BK; e += BT) {
+        const int q = (int)(e % BK);
+        if (q < nb) S.Y[e] = S.diag[e / BK] * __ldcg(&S.X[e]);
     }
 }
 
@@ -367,15 +491,19 @@ __global__ void __launch_bounds__(BT, MINB) k_batch_davidson(BatchArgs B) {
             const BSys &S = B.sys[s];
             const int active = ldi(&B.st[s].active), nb = ldi(&B.st[s].nb);
             if (!active || nb == 0) continue;
-            if (B.a1_kind[item] == 0) {
+            const int kind = B.a1_kind[item];
+            if (kind == 0) {
                 if (B.lpr == 32) sigma_rows<32>(S, nb, B.a1_local[item], B.srows);
                 else sigma_rows<8>(S, nb, B.a1_local[item], B.srows);
+            } else if (kind == 2) {
+                diag_rows(S, nb, B.a1_local[item], B.srows);
             } else {
                 batch_alpha_item(S, B.a1_local[item], es, nb);
             }
         }
         if (!grid_sync(B.bar, 1, B.spin_limit)) return;
         // ---- A2: beta-grouped on-the-fly items (adds the same-spin-alpha part)
+        //         and the rows of upper-triangle matrices
         while (true) {
             const int item = next_item(B.bar);
             if (item >= B.n_a2) break;
@@ -383,7 +511,12 @@ __global__ void __launch_bounds__(BT, MINB) k_batch_davidson(BatchArgs B) {
             const BSys &S = B.sys[s];
             const int active = ldi(&B.st[s].active), nb = ldi(&B.st[s].nb);
             if (!active || nb == 0) continue;
-            batch_beta_item(S, B.a2_local[item], es, nb);
+            if (B.a2_kind[item] == 1) {
+                if (B.lpr == 32) sigma_rows_upper<32, MINB>(S, nb, B.a2_local[item], B.srows);
+                else sigma_rows_upper<8, MINB>(S, nb, B.a2_local[item], B.srows);
+            } else {
+                batch_beta_item(S, B.a2_local[item], es, nb);
+            }
         }
         if (!grid_sync(B.bar, 2, B.spin_limit)) return;
 
@@ -824,11 +957,12 @@ struct shci_batch {
     DevBuf<shci::BSys> d_sys;
     DevBuf<shci::BState> d_st;
     DevBuf<shci::BarrierState> d_bar;
-    DevBuf<int32_t> a1_sys, a1_kind, a2_sys, v_sys;
+    DevBuf<int32_t> a1_sys, a1_kind, a2_sys, a2_kind, v_sys;
     DevBuf<int64_t> a1_local, a2_local, v_start;
     DevBuf<double> partial;
     int64_t n_a1 = 0, n_a2 = 0, n_v = 0;
     int srows = 256, blocks_per_sm = 3, lpr = 32, grid = 0;
+    std::vector<int> modes;         // storage mode of each system
     bool tuned = false;
     cudaGraphExec_t gexec = nullptr;
     int graph_max_iter = -1;
@@ -871,6 +1005,7 @@ void launch_batch(shci_batch *b, int max_iter, bool capture_ok) {
     A.a1_local = b->a1_local.p;
     A.n_a1 = b->n_a1;
     A.a2_sys = b->a2_sys.p;
+    A.a2_kind = b->a2_kind.p;
     A.a2_local = b->a2_local.p;
     A.n_a2 = b->n_a2;
     A.srows = b->srows;
@@ -948,7 +1083,7 @@ double time_batch(shci_batch *b, int max_iter) {
 
 // work lists for the current stored-row chunk size
 void build_worklists(shci_batch *b) {
-    std::vector<int32_t> a1s, a1k, a2s;
+    std::vector<int32_t> a1s, a1k, a2s, a2k;
     std::vector<int64_t> a1l, a2l;
     for (int s = 0; s < b->S; s++) {
         shci_ctx *c = b->subs[s];
@@ -958,6 +1093,15 @@ void build_worklists(shci_batch *b) {
                 a1k.push_back(0);
                 a1l.push_back(r);
             }
+        } else if (c->mode == SHCI_STORED_UPPER) {
+            for (int64_t r = 0; r < c->n_det; r += b->srows) {
+                a1s.push_back(s);
+                a1k.push_back(2);
+                a1l.push_back(r);
+                a2s.push_back(s);
+                a2k.push_back(1);
+                a2l.push_back(r);
+            }
         } else {
             for (int64_t t = 0; t < c->n_items_a; t++) {
                 a1s.push_back(s);
@@ -966,6 +1110,7 @@ void build_worklists(shci_batch *b) {
             }
             for (int64_t t = 0; t < c->n_items_b; t++) {
                 a2s.push_back(s);
+                a2k.push_back(0);
                 a2l.push_back(t);
             }
         }
@@ -975,6 +1120,7 @@ void build_worklists(shci_batch *b) {
     upload(b->a1_kind, a1k, st);
     upload(b->a1_local, a1l, st);
     upload(b->a2_sys, a2s, st);
+    upload(b->a2_kind, a2k, st);
     upload(b->a2_local, a2l, st);
     b->n_a1 = (int64_t)a1s.size();
     b->n_a2 = (int64_t)a2s.size();
@@ -1088,7 +1234,7 @@ void autotune(shci_batch *b) {
         if (p != 3) trial(rows_best, p);
     // lanes per stored row: a warp per determinant, or 8 lanes (4 rows per warp)
     int best_lpr = 32;
-    if (b->stats.n_stored > 0) {
+    if (b->stats.n_stored + b->stats.n_stored_upper > 0) {
         const double before = best;
         b->lpr = 8;
         trial(best_rows, best_bps);
@@ -1126,7 +1272,7 @@ int shci_batch_create(shci_ctx *ctx, int n_sys, const shci_system_desc *systems,
         b = new shci_batch();
         b->parent = ctx;
         b->S = n_sys;
-        double budget = stored_budget_bytes;
+        // pass 1: helper lists, diagonal and pair count of every system
         for (int s = 0; s < n_sys; s++) {
             const shci_system_desc &d = systems[s];
             if (d.n_orb < 1 || d.n_orb > 64) throw ShciError{SHCI_ERR_INVALID, "batched systems need n_orb <= 64"};
@@ -1138,17 +1284,48 @@ int shci_batch_create(shci_ctx *ctx, int n_sys, const shci_system_desc *systems,
             c->n_sm = ctx->n_sm;
             CUDA_TRY(cudaEventCreate(&c->ev0));
             CUDA_TRY(cudaEventCreate(&c->ev1));
-            c->stored_budget = budget;
             shci::load_integrals(c, d.n_orb, d.e_core, d.h, d.eri_packed, mem_space);
-            shci::build(c, d.n_alpha, d.n_beta, d.n_det, d.dets, mem_space, SHCI_AUTO);
-            if (c->mode == SHCI_STORED) {
-                budget -= 12.0 * (double)c->nnz_full;
-                b->stats.n_stored++;
-            } else {
-                b->stats.n_on_the_fly++;
-            }
+            shci::build(c, d.n_alpha, d.n_beta, d.n_det, d.dets, mem_space, SHCI_ON_THE_FLY);
             b->stats.total_det += c->n_det;
             b->stats.total_nnz_upper += c->nnz_upper;
+        }
+        // the storage plan: 12 bytes per stored nonzero, systems by ascending
+        // pair count; all upper triangles if they fit, then both triangles for
+        // as many as the rest of the budget takes; else upper triangles while
+        // they fit
+        size_t free_b = 0, total_b = 0;
+        CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+        double left = 0.8 * (double)free_b;
+        if (stored_budget_bytes >= 0.0) left = std::min(left, stored_budget_bytes);
+        std::vector<int> order(n_sys);
+        for (int s = 0; s < n_sys; s++) order[s] = s;
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int x, int y) { return b->subs[x]->nnz_upper < b->subs[y]->nnz_upper; });
+        double all_upper = 0.0;
+        for (auto *c : b->subs) all_upper += 12.0 * (double)c->nnz_upper;
+        b->modes.assign(n_sys, SHCI_ON_THE_FLY);
+        if (all_upper <= left) {
+            left -= all_upper;
+            for (int s : order) {
+                const double extra = 12.0 * (double)b->subs[s]->nnz_upper;
+                b->modes[s] = extra <= left ? SHCI_STORED : SHCI_STORED_UPPER;
+                if (extra <= left) left -= extra;
+            }
+        } else {
+            for (int s : order) {
+                const double need = 12.0 * (double)b->subs[s]->nnz_upper;
+                if (need > left) break;
+                b->modes[s] = SHCI_STORED_UPPER;
+                left -= need;
+            }
+        }
+        // pass 2: store, and describe each system to the kernel
+        for (int s = 0; s < n_sys; s++) {
+            shci_ctx *c = b->subs[s];
+            if (b->modes[s] != SHCI_ON_THE_FLY) shci::store(c, b->modes[s]);
+            if (c->mode == SHCI_STORED) b->stats.n_stored++;
+            else if (c->mode == SHCI_STORED_UPPER) b->stats.n_stored_upper++;
+            else b->stats.n_on_the_fly++;
             shci::BSys S{};
             S.n = c->n_det;
             S.mode = c->mode;
@@ -1241,6 +1418,12 @@ int shci_batch_davidson(shci_batch *b, int k_roots, double tol, int max_iter, do
         ctx->err = e.what();
         return SHCI_ERR_INVALID;
     }
+}
+
+int shci_batch_get_modes(const shci_batch *b, int cap, int *modes) {
+    if (!b || !modes || cap < b->S) return SHCI_ERR_INVALID;
+    for (int s = 0; s < b->S; s++) modes[s] = b->modes[s];
+    return SHCI_OK;
 }
 
 int shci_batch_set_wait_limit(shci_batch *b, long long naps) {

@@ -550,16 +550,23 @@ static void opposite_spin_setup(shci_ctx *c) {
     if (!(c->opp_factor >= 0.0f)) c->opp_factor = 0.5f;
 }
 
-// SHCI_AUTO: store H when its nnz elements (12 bytes each) fit 80 % of the free
-// device memory and the context's budget
-static int decide_mode(shci_ctx *c, int mode, int64_t nnz) {
+// SHCI_AUTO: store both triangles of H when their nnz_full elements (12 bytes
+// each) fit 80 % of the free device memory and the context's budget, else the
+// upper triangle alone when its nnz_full / 2 elements fit, else apply H on the fly
+static int decide_mode(shci_ctx *c, int mode, int64_t nnz_full) {
     if (mode != SHCI_AUTO) return mode;
     size_t free_b = 0, total_b = 0;
     CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
-    double need = (double)nnz * 12.0;
+    double need = (double)nnz_full * 12.0;
     double cap = 0.8 * (double)free_b;
     if (c->stored_budget >= 0.0) cap = std::min(cap, c->stored_budget);
-    return need < cap ? SHCI_STORED : SHCI_ON_THE_FLY;
+    if (need < cap) return SHCI_STORED;
+    return 0.5 * need < cap ? SHCI_STORED_UPPER : SHCI_ON_THE_FLY;
+}
+
+// entries held by a stored matrix: both triangles or the upper one
+static int64_t stored_entries(const shci_ctx *c) {
+    return c->mode == SHCI_STORED_UPPER ? c->nnz_upper : c->nnz_full;
 }
 
 // validation, helper lists (Table I), the diagonal and the work items of V
@@ -600,14 +607,14 @@ static void lists_w(shci_ctx *c) {
     make_items(c, c->gb_off.p, c->Ub, c->item_b_group, c->item_b_first, c->n_items_b);
 }
 
+// count pass: entries of the beta-grouped part and of the alpha-grouped part
+// of each row, their offsets (rowptr) and the pair counts; with upper set,
+// only the pairs j > i
 template <int W>
-static void build_w(shci_ctx *c, int mode) {
+static void count_w(shci_ctx *c, bool upper) {
     cudaStream_t st = c->st;
     const int64_t n = c->n_det;
-    lists_w<W>(c);
     DevInts I = dev_ints(c);
-
-    // count pass: entries of the beta-grouped part and of the alpha-grouped part of each row
     DevBuf<unsigned long long> cand;
     cand.alloc(1);
     CUDA_TRY(cudaMemsetAsync(cand.p, 0, sizeof(unsigned long long), st));
@@ -616,6 +623,7 @@ static void build_w(shci_ctx *c, int mode) {
     c->i64a.alloc((size_t)n + 1);
     c->i64c.alloc((size_t)scan_tmp_len(n + 1));
     EnumArgs A = enum_args(c);
+    A.upper_only = upper ? 1 : 0;
     A.cand = cand.p;
     A.cnt = c->cnt_b.p;
     launch_enum<W, ENUM_COUNT, 0>(c, A, I, false);
@@ -630,26 +638,60 @@ static void build_w(shci_ctx *c, int mode) {
     CUDA_TRY(cudaMemcpyAsync(&nnz, c->rowptr.p + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaMemcpyAsync(&ncand, cand.p, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));
-    c->nnz_full = nnz;
-    c->nnz_upper = nnz / 2;
+    c->nnz_full = upper ? 2 * nnz : nnz;
+    c->nnz_upper = upper ? nnz : nnz / 2;
     c->candidates = (int64_t)ncand;
-    mode = decide_mode(c, mode, nnz);
+    c->rows_upper = upper;
+}
+
+// Store H in mode SHCI_STORED or SHCI_STORED_UPPER after the lists and a
+// count pass (recounted when the row lengths held are of the other form).
+template <int W>
+static void store_w(shci_ctx *c, int mode) {
+    const bool upper = mode == SHCI_STORED_UPPER;
+    if (c->rows_upper != upper) count_w<W>(c, upper);
     c->mode = mode;
-    if (mode == SHCI_STORED) {
-        c->col.alloc((size_t)std::max<int64_t>(nnz, 1));
-        c->val.alloc((size_t)std::max<int64_t>(nnz, 1));
-        A.rowptr = c->rowptr.p;
-        A.col = c->col.p;
-        A.val = c->val.p;
-        A.part_off = nullptr;
-        launch_enum<W, ENUM_FILL, 0>(c, A, I, false);
-        A.part_off = c->cnt_b.p;
-        launch_enum<W, ENUM_FILL, 0>(c, A, I, true);
+    const int64_t nnz = stored_entries(c);
+    c->col.alloc((size_t)std::max<int64_t>(nnz, 1));
+    c->val.alloc((size_t)std::max<int64_t>(nnz, 1));
+    DevInts I = dev_ints(c);
+    EnumArgs A = enum_args(c);
+    A.upper_only = upper ? 1 : 0;
+    A.rowptr = c->rowptr.p;
+    A.col = c->col.p;
+    A.val = c->val.p;
+    A.part_off = nullptr;
+    launch_enum<W, ENUM_FILL, 0>(c, A, I, false);
+    A.part_off = c->cnt_b.p;
+    launch_enum<W, ENUM_FILL, 0>(c, A, I, true);
+    CUDA_TRY(cudaStreamSynchronize(c->st));
+}
+
+template <int W>
+static void build_w(shci_ctx *c, int mode) {
+    lists_w<W>(c);
+    count_w<W>(c, mode == SHCI_STORED_UPPER);
+    mode = decide_mode(c, mode, c->nnz_full);
+    if (mode == SHCI_STORED || mode == SHCI_STORED_UPPER) {
+        store_w<W>(c, mode);
     } else {
+        c->mode = mode;
         c->col.reset();
         c->val.reset();
     }
-    CUDA_TRY(cudaStreamSynchronize(st));
+    CUDA_TRY(cudaStreamSynchronize(c->st));
+}
+
+void store(shci_ctx *c, int mode) {
+    if (!c->built) throw ShciError{SHCI_ERR_STATE, "build the connectivity before storing it"};
+    if (mode != SHCI_STORED && mode != SHCI_STORED_UPPER) throw ShciError{SHCI_ERR_INVALID, "unknown stored form"};
+    if (c->mode == mode) return;
+    c->built = false;
+    c->col.reset();
+    c->val.reset();
+    if (c->W == 1) store_w<1>(c, mode);
+    else store_w<2>(c, mode);
+    c->built = true;
 }
 
 // Incremental update after V grew from n_old determinants (Sec. III,
@@ -682,8 +724,11 @@ struct PhaseMarks {
     cudaStream_t st_;
 };
 
+// Returns false, with nothing built, when SHCI_AUTO finds that both triangles
+// of the grown matrix no longer fit but its upper triangle would: the row
+// lengths counted here are the full ones, so the caller rebuilds V.
 template <int W>
-static void extend_w(shci_ctx *c, int64_t n_old) {
+static bool extend_w(shci_ctx *c, int64_t n_old) {
     cudaStream_t st = c->st;
     const int64_t n = c->n_det;
     PhaseMarks pm(st);
@@ -727,6 +772,8 @@ static void extend_w(shci_ctx *c, int64_t n_old) {
     off_b.alloc((size_t)n);
     rowptr.alloc((size_t)n + 1);
     c->i64c.alloc((size_t)scan_tmp_len(n + 1));
+    // an upper-triangle matrix grows by its new pairs j > i only
+    An.upper_only = Ao.upper_only = c->mode == SHCI_STORED_UPPER ? 1 : 0;
     An.cand = Ao.cand = cand.p;
     An.cnt = Ao.cnt = c->cnt_b.p;
     extend_pass<W, ENUM_COUNT_INC>(c, An, I, false, ib_new, gbd.p, gbs.p);
@@ -745,10 +792,17 @@ static void extend_w(shci_ctx *c, int64_t n_old) {
     CUDA_TRY(cudaStreamSynchronize(st));
     c->candidates = (int64_t)ncand;
     pm.mark(2);
-    // a stored matrix stays stored unless SHCI_AUTO finds no room for the grown one
+    const bool upper = c->mode == SHCI_STORED_UPPER;
+    const int64_t nnz_full = upper ? 2 * nnz : nnz;
+    // a stored matrix stays stored unless SHCI_AUTO finds no room for the grown
+    // one (both triangles may then fall back to the upper one, by a rebuild)
     int mode = c->mode;
-    if (mode == SHCI_STORED && c->mode_req == SHCI_AUTO) mode = decide_mode(c, SHCI_AUTO, nnz);
-    if (mode == SHCI_STORED) {
+    if (mode != SHCI_ON_THE_FLY && c->mode_req == SHCI_AUTO) {
+        const int fit = decide_mode(c, SHCI_AUTO, nnz_full);
+        if (fit == SHCI_ON_THE_FLY) mode = SHCI_ON_THE_FLY;
+        else if (mode == SHCI_STORED && fit == SHCI_STORED_UPPER) return false;
+    }
+    if (mode == SHCI_STORED || mode == SHCI_STORED_UPPER) {
         DevBuf<int32_t> col;
         DevBuf<double> val;
         col.alloc((size_t)std::max<int64_t>(nnz, 1));
@@ -779,10 +833,12 @@ static void extend_w(shci_ctx *c, int64_t n_old) {
     pm.mark(4);
     c->mode = mode;
     c->rowptr.swap(rowptr);
-    c->nnz_full = nnz;
-    c->nnz_upper = nnz / 2;
+    c->nnz_full = nnz_full;
+    c->nnz_upper = upper ? nnz : nnz / 2;
+    c->rows_upper = upper;
     CUDA_TRY(cudaStreamSynchronize(st));
     pm.read(c->stats.extend_phase_ms, 4);
+    return true;
 }
 
 void extend(shci_ctx *c, int64_t n_new, const uint64_t *new_dets, int mem, double full_fraction) {
@@ -807,15 +863,13 @@ void extend(shci_ctx *c, int64_t n_new, const uint64_t *new_dets, int mem, doubl
         c->dets.swap(grown);
     }
     c->n_det = n;
-    const bool incremental = (double)n_new < full_fraction * (double)n;
+    bool incremental = (double)n_new < full_fraction * (double)n;
     cudaEvent_t e0, e1;
     CUDA_TRY(cudaEventCreate(&e0));
     CUDA_TRY(cudaEventCreate(&e1));
     CUDA_TRY(cudaEventRecord(e0, c->st));
-    if (incremental) {
-        if (W == 1) extend_w<1>(c, n_old);
-        else extend_w<2>(c, n_old);
-    } else {
+    if (incremental) incremental = W == 1 ? extend_w<1>(c, n_old) : extend_w<2>(c, n_old);
+    if (!incremental) {
         const int mode = c->mode_req == SHCI_AUTO ? SHCI_AUTO : c->mode;
         if (W == 1) build_w<1>(c, mode);
         else build_w<2>(c, mode);
@@ -840,7 +894,7 @@ void build(shci_ctx *c, int n_alpha, int n_beta, int64_t n_det, const uint64_t *
     if (!dets) throw ShciError{SHCI_ERR_INVALID, "null determinant pointer"};
     if (n_alpha < 0 || n_beta < 0 || n_alpha > c->n_orb || n_beta > c->n_orb)
         throw ShciError{SHCI_ERR_INVALID, "electron counts out of range"};
-    if (mode != SHCI_STORED && mode != SHCI_ON_THE_FLY && mode != SHCI_AUTO)
+    if (mode != SHCI_STORED && mode != SHCI_ON_THE_FLY && mode != SHCI_AUTO && mode != SHCI_STORED_UPPER)
         throw ShciError{SHCI_ERR_INVALID, "unknown mode"};
     if (mem != SHCI_MEM_HOST && mem != SHCI_MEM_DEVICE) throw ShciError{SHCI_ERR_INVALID, "unknown mem_space"};
     const int W = (c->n_orb + 63) / 64;
@@ -872,17 +926,19 @@ void build(shci_ctx *c, int n_alpha, int n_beta, int64_t n_det, const uint64_t *
 // ====================================================================== export
 
 void export_pairs(shci_ctx *c, int64_t cap, int64_t *i_out, int64_t *j_out, double *v_out, int64_t *n_out) {
-    if (!c->built || c->mode != SHCI_STORED) throw ShciError{SHCI_ERR_STATE, "no stored Hamiltonian"};
+    if (!c->built || (c->mode != SHCI_STORED && c->mode != SHCI_STORED_UPPER))
+        throw ShciError{SHCI_ERR_STATE, "no stored Hamiltonian"};
     if (n_out) *n_out = c->nnz_upper;
     if (cap < c->nnz_upper || c->nnz_upper == 0) return;
     if (!i_out || !j_out) throw ShciError{SHCI_ERR_INVALID, "null output pointer"};
     const int64_t n = c->n_det;
     std::vector<int64_t> rp((size_t)n + 1);
-    std::vector<int32_t> cl((size_t)c->nnz_full);
-    std::vector<double> vl((size_t)c->nnz_full);
+    const int64_t held = stored_entries(c);
+    std::vector<int32_t> cl((size_t)held);
+    std::vector<double> vl((size_t)held);
     CUDA_TRY(cudaMemcpyAsync(rp.data(), c->rowptr.p, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost, c->st));
-    CUDA_TRY(cudaMemcpyAsync(cl.data(), c->col.p, sizeof(int32_t) * c->nnz_full, cudaMemcpyDeviceToHost, c->st));
-    CUDA_TRY(cudaMemcpyAsync(vl.data(), c->val.p, sizeof(double) * c->nnz_full, cudaMemcpyDeviceToHost, c->st));
+    CUDA_TRY(cudaMemcpyAsync(cl.data(), c->col.p, sizeof(int32_t) * held, cudaMemcpyDeviceToHost, c->st));
+    CUDA_TRY(cudaMemcpyAsync(vl.data(), c->val.p, sizeof(double) * held, cudaMemcpyDeviceToHost, c->st));
     CUDA_TRY(cudaStreamSynchronize(c->st));
     int64_t o = 0;
     std::vector<std::pair<int32_t, double>> row;

@@ -51,6 +51,7 @@ struct shci_ctx {
     bool built = false;
     int mode = SHCI_STORED;
     int mode_req = SHCI_AUTO;              // the mode the last build was asked for
+    bool rows_upper = false;               // rowptr / cnt_b count the pairs j > i only
     int W = 1, n_alpha = 0, n_beta = 0;
     int64_t n_det = 0;
     DevBuf<uint64_t> dets;                 // [n][2W]
@@ -116,6 +117,9 @@ namespace shci {
 void load_integrals(shci_ctx *c, int n_orb, double e_core, const double *h, const double *eri, int mem);
 void build(shci_ctx *c, int n_alpha, int n_beta, int64_t n_det, const uint64_t *dets, int mem, int mode);
 void extend(shci_ctx *c, int64_t n_new, const uint64_t *new_dets, int mem, double full_fraction);
+// store a context built in any mode as SHCI_STORED or SHCI_STORED_UPPER
+// (the lists are kept; the rows are recounted when their form differs)
+void store(shci_ctx *c, int mode);
 void export_pairs(shci_ctx *c, int64_t cap, int64_t *i_out, int64_t *j_out, double *v_out, int64_t *n_out);
 
 // sigma.cu: y = H x for k vectors; `inter` selects the interleaved [n][k]

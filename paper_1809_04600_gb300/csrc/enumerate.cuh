@@ -77,6 +77,9 @@ struct EnumArgs {
     const int32_t *item_first;              // work item -> first member offset within the group
     int64_t n_items;
     int *work_counter;
+    // count / fill: with upper_only set, only the pairs j > i of each row
+    // (the upper triangle) are counted and stored
+    int upper_only;
     // count
     int64_t *cnt;                           // entries per row of this kernel's part
     unsigned long long *cand;               // candidates screened (statistics)
@@ -336,6 +339,7 @@ __device__ __forceinline__ void emit(RowAcc<MODE, K> &R, const EnumArgs &A, cons
                                      const Str<W> &si, const Str<W> &other, bool match, int32_t j, const Str<W> &sj,
                                      int ctx) {
     const int lane = threadIdx.x & 31;
+    if ((ModeOf<MODE>::count || ModeOf<MODE>::fill) && A.upper_only) match = match && (int64_t)j > R.i;
     const unsigned mask = __ballot_sync(0xffffffffu, match);
     const int nm = __popc(mask);
     R.found += nm;
@@ -372,11 +376,11 @@ struct Tile {
     int32_t det[ENUM_TILE];
 };
 
-template <int W, bool NEED_DET>
+template <int W>
 __device__ __forceinline__ void stage(Tile<W> &T, const uint64_t *__restrict__ mstr, const int32_t *__restrict__ mdet,
-                                      int64_t start, int cnt) {
+                                      int64_t start, int cnt, bool need_det) {
     for (int e = threadIdx.x; e < cnt * W; e += ENUM_THREADS) T.str[e] = __ldg(&mstr[start * W + e]);
-    if (NEED_DET)
+    if (need_det)
         for (int e = threadIdx.x; e < cnt; e += ENUM_THREADS) T.det[e] = __ldg(&mdet[start + e]);
 }
 
@@ -468,7 +472,9 @@ template <int W, int MODE, int K>
 __device__ __forceinline__ void enum_alpha_item(const EnumArgs &A, const DevInts &I, int64_t item, Tile<W> &T,
                                                 WarpQueue<W> &Q, unsigned long long &cand_local, int k_active = 0) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    constexpr bool NEED_DET = !ModeOf<MODE>::count;
+    // member determinant indices: always outside the count modes; in them only
+    // for an upper-triangle count (the filter compares j with the row)
+    const bool need_det = !ModeOf<MODE>::count || A.upper_only;
     constexpr bool XM = ModeOf<MODE>::inc;
     const int a = A.item_group[item];
     const int64_t g_beg = A.ga_off[a], g_len = A.ga_off[a + 1] - g_beg;
@@ -544,7 +550,7 @@ __device__ __forceinline__ void enum_alpha_item(const EnumArgs &A, const DevInts
     // same-spin beta: candidates with the same alpha string
     for (int64_t t0 = 0; t0 < g_len; t0 += ENUM_TILE) {
         const int cnt = (int)min((int64_t)ENUM_TILE, g_len - t0);
-        stage<W, NEED_DET>(T, A.ga_str, A.ga_det, g_beg + t0, cnt);
+        stage<W>(T, A.ga_str, A.ga_det, g_beg + t0, cnt, need_det);
         __syncthreads();
         if (valid) {
             cand_local += lane == 0 ? cnt : 0;
@@ -557,7 +563,7 @@ __device__ __forceinline__ void enum_alpha_item(const EnumArgs &A, const DevInts
                     const int d = xor_popc<W>(Bi, Bj);
                     match = (d == 2) | (d == 4);
                 }
-                emit<W, MODE, K>(R, A, I, Q, Bi, Ai, match, match && NEED_DET ? T.det[e] : 0, Bj, 0);
+                emit<W, MODE, K>(R, A, I, Q, Bi, Ai, match, match && need_det ? T.det[e] : 0, Bj, 0);
             }
         }
         __syncthreads();
@@ -624,7 +630,7 @@ __device__ __forceinline__ void enum_alpha_item(const EnumArgs &A, const DevInts
                     j[u] = 0;
                     Bj[u] = Str<W>{};
                 }
-                if (NEED_DET) {
+                if (need_det) {
                     int64_t m[LU];
 #pragma unroll
                     for (int u = 0; u < LU; u++)
@@ -645,7 +651,7 @@ __device__ __forceinline__ void enum_alpha_item(const EnumArgs &A, const DevInts
         }
         for (int64_t t0 = 0; t0 < k_len; t0 += ENUM_TILE) {
             const int cnt = (int)min((int64_t)ENUM_TILE, k_len - t0);
-            stage<W, NEED_DET>(T, A.ga_str, A.ga_det, k_beg + t0, cnt);
+            stage<W>(T, A.ga_str, A.ga_det, k_beg + t0, cnt, need_det);
             __syncthreads();
             if (valid) {
                 cand_local += lane == 0 ? cnt : 0;
@@ -657,7 +663,7 @@ __device__ __forceinline__ void enum_alpha_item(const EnumArgs &A, const DevInts
                         Bj = tile_str<W>(T, e);
                         match = xor_popc<W>(Bi, Bj) == 2;
                     }
-                    emit<W, MODE, K>(R, A, I, Q, Bi, Ai, match, match && NEED_DET ? T.det[e] : 0, Bj, ctx);
+                    emit<W, MODE, K>(R, A, I, Q, Bi, Ai, match, match && need_det ? T.det[e] : 0, Bj, ctx);
                 }
             }
             __syncthreads();
@@ -672,7 +678,7 @@ template <int W, int MODE, int K>
 __device__ __forceinline__ void enum_beta_item(const EnumArgs &A, const DevInts &I, int64_t item, Tile<W> &T,
                                                WarpQueue<W> &Q, unsigned long long &cand_local, int k_active = 0) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    constexpr bool NEED_DET = !ModeOf<MODE>::count;
+    const bool need_det = !ModeOf<MODE>::count || A.upper_only;
     constexpr bool XM = ModeOf<MODE>::inc;
     const int b = A.item_group[item];
     const int64_t g_beg = A.gb_off[b], g_len = A.gb_off[b + 1] - g_beg;
@@ -696,7 +702,7 @@ __device__ __forceinline__ void enum_beta_item(const EnumArgs &A, const DevInts 
     }
     for (int64_t t0 = 0; t0 < g_len; t0 += ENUM_TILE) {
         const int cnt = (int)min((int64_t)ENUM_TILE, g_len - t0);
-        stage<W, NEED_DET>(T, A.gb_str, A.gb_det, g_beg + t0, cnt);
+        stage<W>(T, A.gb_str, A.gb_det, g_beg + t0, cnt, need_det);
         __syncthreads();
         if (valid) {
             cand_local += lane == 0 ? cnt : 0;
@@ -709,7 +715,7 @@ __device__ __forceinline__ void enum_beta_item(const EnumArgs &A, const DevInts 
                     const int d = xor_popc<W>(Ai, Aj);
                     match = (d == 2) | (d == 4);
                 }
-                emit<W, MODE, K>(R, A, I, Q, Ai, Bi, match, match && NEED_DET ? T.det[e] : 0, Aj, 0);
+                emit<W, MODE, K>(R, A, I, Q, Ai, Bi, match, match && need_det ? T.det[e] : 0, Aj, 0);
             }
         }
         __syncthreads();

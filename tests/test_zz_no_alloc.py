@@ -108,3 +108,13 @@ def test_noalloc_rejects_oversize_and_unbuilt(P):
     assert _noalloc_raw(P, ctx.handle, x, y) == 1          # 8 * 70000 > 524288
     assert "static scratch" in P.shci_last_error(ctx.handle)
     ctx.close()
+
+
+def test_noalloc_rejects_an_upper_triangle_matrix(P):
+    """Only a matrix stored in both triangles qualifies (SHCI_ERR_STATE, before any launch)."""
+    cfg, h, eri, ec, dets = G.system("sel_20o_5a5b_1m", 3001)
+    B = G.Built(P, h, eri, ec, dets, cfg.n_alpha, cfg.n_beta, mode=P.SHCI_STORED_UPPER)
+    x = torch.zeros((1, dets.shape[0]), dtype=torch.float64, device="cuda")
+    y = torch.empty_like(x)
+    assert _noalloc_raw(P, B.ctx.handle, x, y) == 6
+    B.close()
