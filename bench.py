@@ -976,15 +976,21 @@ def run_batch(args):
     P.shci_batch_destroy(b)
     # sequential: one context per system, the batch's storage decisions, Davidson timed alone
     seq_time, seq_e, seq_it = 0.0, [], []
+    seq_parts = np.zeros(7)
+    seq_sigma_by_mode = {}
     for d, mode in zip(systems, modes):
         c2 = P.Context(0, torch.cuda.current_stream())
         P.shci_load_integrals(c2.handle, d["n_orb"], d["e_core"], d["h"], d["eri"])
         P.shci_build_connectivity(c2.handle, d["n_alpha"], d["n_beta"], d["dets"], int(mode))
+        P.shci_set_timing(c2.handle, False, davidson_phases=True)   # per-part device times, events only
         torch.cuda.synchronize()
         t = time.perf_counter()
         es, its, rcs = P.shci_davidson(c2.handle, k, TOL, MAX_ITER, check=False)
         torch.cuda.synchronize()
         seq_time += time.perf_counter() - t
+        parts = np.array(P.shci_get_stats(c2.handle)["davidson_phase_ms"][:7])
+        seq_parts += parts
+        seq_sigma_by_mode[int(mode)] = seq_sigma_by_mode.get(int(mode), 0.0) + parts[5]
         seq_e.append(es)
         seq_it.append(its)
         c2.close()
@@ -999,11 +1005,16 @@ def run_batch(args):
                       "max_abs_dE_vs_sequential": float(np.max(np.abs(e - seq_e))),
                       "graph": st["graph"], "grid_ctas": st["grid_ctas"],
                       "tuned": {"rows_per_item": st["tuned_rows_per_item"], "ctas_per_sm": st["tuned_ctas_per_sm"],
-                                "lanes_per_row": st["tuned_lanes_per_row"],
+                                "lanes_per_row": st["tuned_lanes_per_row"], "vector_slice": st["tuned_vslice"],
                                 "trial_ms": st0["tune_ms"]},
                       "max_iters": st["max_iters"], "all_converged": bool(conv.all()),
                       "iters_sum_batched": int(np.sum(it)), "iters_sum_sequential": int(np.sum(seq_it)),
-                      "phase_ms": {name: round(v, 3) for name, v in zip(BATCH_PHASES, st["phase_ms"])}}))
+                      "phase_ms": {name: round(v, 3) for name, v in zip(BATCH_PHASES, st["phase_ms"])},
+                      "sequential_part_ms": {name: round(float(v), 3) for name, v in zip(
+                          ("start", "eigensolver", "ritz_residuals", "restarts", "orthonormalisation", "sigma",
+                           "gram_columns"), seq_parts)},
+                      "sequential_sigma_ms_by_mode": {{0: "stored", 1: "on_the_fly", 3: "stored_upper"}[m]:
+                                                      round(v, 3) for m, v in seq_sigma_by_mode.items()}}))
     ctx.close()
 
 

@@ -368,6 +368,7 @@ typedef struct {
      * projection, 10-12 Cholesky-QR, 13 next block, 14 bookkeeping */
     double phase_ms[16];
     int n_stored_upper;        /* systems stored as their upper triangle (not in n_stored) */
+    int tuned_vslice;          /* vector elements per work item of the phases over vectors (8192 or 2048) */
 } shci_batch_stats_t;
 
 /* Build every system's connectivity (Sec. III) and decide how each H is held

@@ -89,7 +89,7 @@ class shci_batch_stats_t(ctypes.Structure):
         ("tuned_lanes_per_row", ctypes.c_int),
         ("tune_ms", ctypes.c_double), ("solve_ms", ctypes.c_double), ("max_iters", ctypes.c_int),
         ("graph", ctypes.c_int), ("grid_ctas", ctypes.c_int), ("phase_ms", ctypes.c_double * 16),
-        ("n_stored_upper", ctypes.c_int),
+        ("n_stored_upper", ctypes.c_int), ("tuned_vslice", ctypes.c_int),
     ]
 
 

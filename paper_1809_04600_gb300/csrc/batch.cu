@@ -33,7 +33,7 @@ namespace shci {
 
 constexpr int BK = 4;                      // roots per system in a batch (max)
 constexpr int BT = 256;                    // threads per CTA
-constexpr int VSLICE = 8192;               // vector elements per vector work item
+constexpr int VSLICE = 8192;               // vector elements per vector work item (default; tuned)
 constexpr int GA = 8;                      // basis rows per register block in slice Gram products
 constexpr int PSTRIDE = SHCI_MAX_SUB * BK + BK * BK + BK + 12;   // partial sums per vector item
 constexpr long long BARRIER_SPIN_LIMIT = 1ll << 27;             // default: x ~100 ns naps >= ~13 s
@@ -51,6 +51,7 @@ struct BSys {
                                            // (complete, read in place: no per-item copy)
     DevInts I;
     int64_t v_item_off, v_item_cnt;        // this system's vector items
+    int64_t vslice;                        // and their length (the batch's)
     double *Vb[2], *AVb[2];                // current / rotation target (swapped by index)
     double *T, *T2, *X, *Y;
     double *G, *evec, *erot, *eval;
@@ -214,12 +215,16 @@ __device__ __forceinline__ double sum_items(const BatchArgs &B, const BSys &S, i
     return v;
 }
 
-// stored rows [r0, r0 + cnt): Y[i][q] = diag_i X[i][q] + sum_j H_ij X[j][q], q < nb.
+// stored rows [r0, r0 + cnt): Y[i][q] = diag_i X[i][q] + sum_j H_ij X[j][q], q < NB.
 // LPR lanes per row: 32 is a warp per determinant; fewer lanes work on
-// 32 / LPR rows of a warp at once (short rows leave fewer lanes idle).
-template <int LPR>
-__device__ void sigma_rows(const BSys &S, int nb, int64_t r0, int cnt) {
+// 32 / LPR rows of a warp at once (short rows leave fewer lanes idle).  One
+// instance per count of vectors in use, out of line (its registers apart from
+// the persistent kernel's); SR nonzeros per lane per step with all loads
+// issued before the FMAs, 8 in the variants with the registers for it.
+template <int LPR, int NB, int MINB>
+__device__ __noinline__ void sigma_rows_nb(const BSys &S, int64_t r0, int cnt) {
     constexpr int RPW = 32 / LPR;
+    constexpr int SR = MINB <= 2 ? 8 : 4;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int sub = lane / LPR, sl = lane % LPR;
     const int64_t *__restrict__ rowptr = S.rowptr;      // the system's arrays in registers
@@ -228,19 +233,30 @@ __device__ void sigma_rows(const BSys &S, int nb, int64_t r0, int cnt) {
     const double *X = S.X;
     double *Y = S.Y;
     const int64_t r1 = min(r0 + cnt, S.n);
+    auto load_x = [&](int64_t j, double (&o)[NB]) {
+        if (NB == 1) {
+            o[0] = __ldcg(&X[j * BK]);
+        } else {
+            const double2 a = __ldcg(reinterpret_cast<const double2 *>(X) + 2 * j);
+            o[0] = a.x;
+            o[NB > 1 ? 1 : 0] = a.y;
+            if (NB > 2) {
+                const double2 b = __ldcg(reinterpret_cast<const double2 *>(X) + 2 * j + 1);
+                o[NB > 2 ? 2 : 0] = b.x;
+                if (NB > 3) o[NB > 3 ? 3 : 0] = b.y;
+            }
+        }
+    };
     for (int64_t i0 = r0 + (int64_t)warp * RPW; i0 < r1; i0 += (BT / 32) * RPW) {
         const int64_t i = i0 + sub;
         const bool ok = i < r1;
-        double acc[BK] = {0.0, 0.0, 0.0, 0.0};
+        double acc[NB];
+#pragma unroll
+        for (int q = 0; q < NB; q++) acc[q] = 0.0;
         const int64_t beg = ok ? rowptr[i] : 0, end = ok ? rowptr[i + 1] : 0;
-        // SR nonzeros per lane per step, all loads issued before the FMAs: the
-        // persistent grid has few warps per SM, so each warp keeps several
-        // gathers of X in flight
-        constexpr int SR = 4;
         for (int64_t p0 = beg + sl; p0 < end; p0 += LPR * SR) {
             int32_t j[SR];
-            double v[SR];
-            double2 x01[SR], x23[SR];
+            double v[SR], xv[SR][NB];
 #pragma unroll
             for (int u = 0; u < SR; u++) {
                 const int64_t p = p0 + LPR * u;
@@ -249,37 +265,37 @@ __device__ void sigma_rows(const BSys &S, int nb, int64_t r0, int cnt) {
             }
 #pragma unroll
             for (int u = 0; u < SR; u++) {
-                x01[u] = j[u] >= 0 ? __ldcg(reinterpret_cast<const double2 *>(X) + 2 * (int64_t)j[u])
-                                   : make_double2(0.0, 0.0);
-                x23[u] = (nb > 2 && j[u] >= 0)
-                             ? __ldcg(reinterpret_cast<const double2 *>(X) + 2 * (int64_t)j[u] + 1)
-                             : make_double2(0.0, 0.0);
+                if (j[u] >= 0) load_x(j[u], xv[u]);
+                else
+#pragma unroll
+                    for (int q = 0; q < NB; q++) xv[u][q] = 0.0;
             }
 #pragma unroll
-            for (int u = 0; u < SR; u++) {
-                acc[0] = fma(v[u], x01[u].x, acc[0]);
-                if (nb > 1) acc[1] = fma(v[u], x01[u].y, acc[1]);
-                if (nb > 2) {
-                    acc[2] = fma(v[u], x23[u].x, acc[2]);
-                    if (nb > 3) acc[3] = fma(v[u], x23[u].y, acc[3]);
-                }
-            }
+            for (int u = 0; u < SR; u++)
+#pragma unroll
+                for (int q = 0; q < NB; q++) acc[q] = fma(v[u], xv[u][q], acc[q]);
         }
-        // reduce over the row's LPR lanes (the whole warp takes part), only
-        // the nb vectors in use (nb is warp-uniform; FP64 adds are the scarce unit)
+        // reduce over the row's LPR lanes (the whole warp takes part)
 #pragma unroll
-        for (int q = 0; q < BK; q++) {
-            if (q < nb) {
+        for (int q = 0; q < NB; q++) {
 #pragma unroll
-                for (int o = LPR / 2; o >= 1; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
-            }
+            for (int o = LPR / 2; o >= 1; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
         }
         if (ok && sl == 0) {
             const double d = S.diag[i];
 #pragma unroll
-            for (int q = 0; q < BK; q++)
-                if (q < nb) Y[i * BK + q] = fma(d, __ldcg(&X[i * BK + q]), acc[q]);
+            for (int q = 0; q < NB; q++) Y[i * BK + q] = fma(d, __ldcg(&X[i * BK + q]), acc[q]);
         }
+    }
+}
+
+template <int LPR, int MINB>
+__device__ __forceinline__ void sigma_rows(const BSys &S, int nb, int64_t r0, int cnt) {
+    switch (nb) {
+        case 1: sigma_rows_nb<LPR, 1, MINB>(S, r0, cnt); break;
+        case 2: sigma_rows_nb<LPR, 2, MINB>(S, r0, cnt); break;
+        case 3: sigma_rows_nb<LPR, 3, MINB>(S, r0, cnt); break;
+        default: sigma_rows_nb<LPR, 4, MINB>(S, r0, cnt); break;
     }
 }
 
@@ -493,8 +509,8 @@ __global__ void __launch_bounds__(BT, MINB) k_batch_davidson(BatchArgs B) {
             if (!active || nb == 0) continue;
             const int kind = B.a1_kind[item];
             if (kind == 0) {
-                if (B.lpr == 32) sigma_rows<32>(S, nb, B.a1_local[item], B.srows);
-                else sigma_rows<8>(S, nb, B.a1_local[item], B.srows);
+                if (B.lpr == 32) sigma_rows<32, MINB>(S, nb, B.a1_local[item], B.srows);
+                else sigma_rows<8, MINB>(S, nb, B.a1_local[item], B.srows);
             } else if (kind == 2) {
                 diag_rows(S, nb, B.a1_local[item], B.srows);
             } else {
@@ -530,7 +546,7 @@ __global__ void __launch_bounds__(BT, MINB) k_batch_davidson(BatchArgs B) {
             const int m = ldi(&st.m), cur = ldi(&st.cur);
             const double *V = S.Vb[cur];
             double *AV = S.AVb[cur];
-            const int64_t i0 = B.v_start[item], i1 = min(S.n, i0 + VSLICE);
+            const int64_t i0 = B.v_start[item], i1 = min(S.n, i0 + S.vslice);
             for (int64_t i = i0 + tid; i < i1; i += BT)
                 for (int q = 0; q < nb; q++) AV[(int64_t)(m + q) * S.n + i] = __ldcg(&S.Y[i * BK + q]);
             auto loadY = [&](int64_t i, double (&b)[BK]) {
@@ -582,7 +598,7 @@ __global__ void __launch_bounds__(BT, MINB) k_batch_davidson(BatchArgs B) {
             }
             if (tid < BK) th[tid] = tid < k ? __ldcg(&S.eval[tid]) : 0.0;
             __syncthreads();
-            const int64_t i0 = B.v_start[item], i1 = min(S.n, i0 + VSLICE);
+            const int64_t i0 = B.v_start[item], i1 = min(S.n, i0 + S.vslice);
             double rs[BK * BK + BK];
 #pragma unroll
             for (int e = 0; e < BK * BK + BK; e++) rs[e] = 0.0;
@@ -726,7 +742,7 @@ __global__ void __launch_bounds__(BT, MINB) k_batch_davidson(BatchArgs B) {
             const double *V = S.Vb[cur], *AV = S.AVb[cur];
             double *Vn = S.Vb[cur ^ 1], *AVn = S.AVb[cur ^ 1];
             const double *Vp = restart ? Vn : V;
-            const int64_t i0 = B.v_start[item], i1 = min(S.n, i0 + VSLICE);
+            const int64_t i0 = B.v_start[item], i1 = min(S.n, i0 + S.vslice);
             for (int64_t i = i0 + tid; i < i1; i += BT) {
                 double t[BK];
 #pragma unroll
@@ -791,7 +807,7 @@ __global__ void __launch_bounds__(BT, MINB) k_batch_davidson(BatchArgs B) {
             double *cs = sh;
             for (int e = tid; e < m * BK; e += BT) cs[e] = __ldcg(&S.coefC[e]);
             __syncthreads();
-            const int64_t i0 = B.v_start[item], i1 = min(S.n, i0 + VSLICE);
+            const int64_t i0 = B.v_start[item], i1 = min(S.n, i0 + S.vslice);
             double s2[BK * BK];
 #pragma unroll
             for (int e = 0; e < BK * BK; e++) s2[e] = 0.0;
@@ -839,7 +855,7 @@ __global__ void __launch_bounds__(BT, MINB) k_batch_davidson(BatchArgs B) {
             double *ms = sh;
             for (int e = tid; e < nt * nt; e += BT) ms[e] = __ldcg(&S.coefM[e]);
             __syncthreads();
-            const int64_t i0 = B.v_start[item], i1 = min(S.n, i0 + VSLICE);
+            const int64_t i0 = B.v_start[item], i1 = min(S.n, i0 + S.vslice);
             double s2[BK * BK];
 #pragma unroll
             for (int e = 0; e < BK * BK; e++) s2[e] = 0.0;
@@ -891,7 +907,7 @@ __global__ void __launch_bounds__(BT, MINB) k_batch_davidson(BatchArgs B) {
             double *ms = sh;
             for (int e = tid; e < nt * nt; e += BT) ms[e] = __ldcg(&S.coefM2[e]);
             __syncthreads();
-            const int64_t i0 = B.v_start[item], i1 = min(S.n, i0 + VSLICE);
+            const int64_t i0 = B.v_start[item], i1 = min(S.n, i0 + S.vslice);
             for (int64_t i = i0 + tid; i < i1; i += BT) {
                 double t[BK], o[BK];
 #pragma unroll
@@ -961,6 +977,7 @@ struct shci_batch {
     DevBuf<int64_t> a1_local, a2_local, v_start;
     DevBuf<double> partial;
     int64_t n_a1 = 0, n_a2 = 0, n_v = 0;
+    int vslice = shci::VSLICE;      // vector elements per vector work item
     int srows = 256, blocks_per_sm = 3, lpr = 32, grid = 0;
     std::vector<int> modes;         // storage mode of each system
     bool tuned = false;
@@ -1137,14 +1154,36 @@ void set_grid(shci_batch *b) {
     b->grid = b->parent->n_sm * std::min(occ, b->blocks_per_sm);
 }
 
+// vector work items: slices of b->vslice elements of every system's vectors
+void build_vitems(shci_batch *b) {
+    using namespace shci;
+    std::vector<int32_t> vs;
+    std::vector<int64_t> vst;
+    for (int s = 0; s < b->S; s++) {
+        BSys &S = b->h_sys[s];
+        S.vslice = b->vslice;
+        S.v_item_off = (int64_t)vs.size();
+        for (int64_t i0 = 0; i0 < S.n; i0 += S.vslice) {
+            vs.push_back(s);
+            vst.push_back(i0);
+        }
+        S.v_item_cnt = (int64_t)vs.size() - S.v_item_off;
+    }
+    cudaStream_t st = b->parent->st;
+    upload(b->v_sys, vs, st);
+    upload(b->v_start, vst, st);
+    b->n_v = (int64_t)vs.size();
+    b->partial.alloc((size_t)b->n_v * PSTRIDE);
+    upload(b->d_sys, b->h_sys, st);
+    CUDA_TRY(cudaStreamSynchronize(st));
+}
+
 void prepare_davidson(shci_batch *b, int k, double tol) {
     using namespace shci;
     cudaStream_t st = b->parent->st;
     if (b->k != k) {
         for (auto *x : b->owned) delete x;
         b->owned.clear();
-        std::vector<int32_t> vs;
-        std::vector<int64_t> vst;
         for (int s = 0; s < b->S; s++) {
             shci_ctx *c = b->subs[s];
             BSys &S = b->h_sys[s];
@@ -1182,17 +1221,8 @@ void prepare_davidson(shci_batch *b, int k, double tol) {
             S.coefS = b->alloc(BK * BK);
             S.coefM = b->alloc(BK * BK);
             S.coefM2 = b->alloc(BK * BK);
-            S.v_item_off = (int64_t)vs.size();
-            for (int64_t i0 = 0; i0 < n; i0 += VSLICE) {
-                vs.push_back(s);
-                vst.push_back(i0);
-            }
-            S.v_item_cnt = (int64_t)vs.size() - S.v_item_off;
         }
-        upload(b->v_sys, vs, st);
-        upload(b->v_start, vst, st);
-        b->n_v = (int64_t)vs.size();
-        b->partial.alloc((size_t)b->n_v * PSTRIDE);
+        build_vitems(b);
         b->d_st.alloc((size_t)b->S);
         b->d_bar.alloc(1);
         b->k = k;
@@ -1241,6 +1271,20 @@ void autotune(shci_batch *b) {
         if (best < before) best_lpr = 8;
     }
     b->lpr = best_lpr;
+    // elements per vector item: shorter slices give the phases over vectors
+    // more items when one or a few large systems hold most of the elements
+    // (more partial sums to add up otherwise: the full 64-system batch keeps
+    // 8192, a lone 1e6-determinant system takes 2048)
+    int best_vs = b->vslice;
+    {
+        const double before = best;
+        b->vslice = 2048;
+        build_vitems(b);
+        trial(best_rows, best_bps);
+        if (best < before) best_vs = 2048;
+    }
+    b->vslice = best_vs;
+    build_vitems(b);
     b->srows = best_rows;
     b->blocks_per_sm = best_bps;
     build_worklists(b);
@@ -1248,6 +1292,7 @@ void autotune(shci_batch *b) {
     b->stats.tuned_rows_per_item = best_rows;
     b->stats.tuned_ctas_per_sm = best_bps;
     b->stats.tuned_lanes_per_row = best_lpr;
+    b->stats.tuned_vslice = best_vs;
     b->stats.tune_ms = best;
     b->tuned = true;
     if (b->gexec) {

@@ -44,7 +44,7 @@ def test_batch_matches_oracle(P, oracle_mod, budget, k):
         np.testing.assert_allclose(e[s], w, atol=E_TOL, rtol=0)
     st = P.shci_batch_get_stats(b)
     assert st["tuned_rows_per_item"] in (64, 256, 1024) and st["tuned_ctas_per_sm"] in (2, 3, 4)
-    assert st["tuned_lanes_per_row"] in (8, 32)
+    assert st["tuned_lanes_per_row"] in (8, 32) and st["tuned_vslice"] in (2048, 8192)
     assert st["graph"] in (0, 1) and st["max_iters"] >= 1
     # the per-phase times cover the solve: they add up to at most its device time
     ph = st["phase_ms"]
