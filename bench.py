@@ -1018,6 +1018,41 @@ def run_batch(args):
     ctx.close()
 
 
+def run_upper(args):
+    """The two stored forms of H on the bench space: sigma per launch for 1, 2
+    and 4 vectors with both triangles stored (a pure gather) and with the
+    upper triangle alone (the transposed half added by FP64 atomic adds), and
+    the memory each takes."""
+    torch, P = _gpu_setup()
+    cfg = S.config(args.config)
+    h, eri, ec, dets = S.make_system(cfg, n_det=args.n_det)
+    n = dets.shape[0]
+    out = {"workload": workload_desc(cfg, n).replace("stored H", "stored H in both forms"), "n_det": n,
+           "forms": {}}
+    for mode, name in ((P.SHCI_STORED, "both_triangles"), (P.SHCI_STORED_UPPER, "upper_triangle")):
+        ctx = P.Context(0, torch.cuda.current_stream())
+        P.shci_load_integrals(ctx.handle, cfg.n_orb, ec, _dev(torch, h), _dev(torch, eri))
+        nnz = P.shci_build_connectivity(ctx.handle, cfg.n_alpha, cfg.n_beta, _dev(torch, dets), mode)
+        held = nnz * (2 if mode == P.SHCI_STORED else 1)
+        rec = {"stored_nonzeros": held, "stored_gb": 12.0 * held / 1e9, "sigma_ms": {}}
+        for k in (1, 2, 4):
+            x = torch.randn(k, n, dtype=torch.float64, device="cuda")
+            y = torch.empty_like(x)
+            for _ in range(3):
+                P.shci_sigma(ctx.handle, x, y)
+            P.shci_set_timing(ctx.handle, True)      # CUDA events around every sigma launch
+            for _ in range(10):
+                P.shci_sigma(ctx.handle, x, y)
+            st = P.shci_get_stats(ctx.handle)
+            P.shci_set_timing(ctx.handle, False)
+            rec["sigma_ms"][str(k)] = st["sigma_ms_total"] / max(st["sigma_launches"], 1)
+        rec["upper_pairs_per_s_k1"] = nnz / (rec["sigma_ms"]["1"] * 1e-3)
+        out["forms"][name] = rec
+        out["nnz_upper"] = nnz
+        ctx.close()
+    print(json.dumps(out))
+
+
 def run_peaks(args):
     """The peak-rate microbenchmarks (FP64 FMA and add, INT32 multiply-add,
     XOR + popcount, FP64 atomics and random gathers in L2), with the clocks
@@ -1052,7 +1087,7 @@ def main():
     ap.add_argument("--sigma-only", type=int, default=0,
                     help="profiling only: build once, then launch the sigma kernel this many times")
     ap.add_argument("--workload", default="main",
-                    choices=["main", "fci", "large", "adjoint", "batch", "select", "extend", "peaks"],
+                    choices=["main", "fci", "large", "adjoint", "batch", "select", "extend", "peaks", "upper"],
                     help="main: the bench line; others print the measurement line of another workload")
     ap.add_argument("--batch-budget-gb", type=float, default=240.0,
                     help="batch workload: device memory the stored matrices may take (capped at 0.8 x free)")
@@ -1071,7 +1106,7 @@ def main():
     ap.add_argument("--extend-eps1", type=float, default=1e-3, help="selection threshold (extend workload)")
     args = ap.parse_args()
     if args.workload != "main":
-        {"fci": run_fci, "large": run_large, "adjoint": run_adjoint, "batch": run_batch,
+        {"fci": run_fci, "large": run_large, "adjoint": run_adjoint, "batch": run_batch, "upper": run_upper,
          "select": run_select, "extend": run_extend, "peaks": run_peaks}[args.workload](args)
     elif args.sigma_only:
         run_sigma_only(args)

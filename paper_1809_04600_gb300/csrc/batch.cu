@@ -299,14 +299,6 @@ __device__ __forceinline__ void sigma_rows(const BSys &S, int nb, int64_t r0, in
     }
 }
 
-// Y[...] += v as a global-memory reduction (no result returned).  Y comes
-// from the system descriptor, a pointer the compiler cannot place in global
-// memory, and atomicAdd on it compiles to a returning atomic that waits for
-// L2 (measured: every scatter made a round trip); red.global does not.
-__device__ __forceinline__ void red_add(double *p, double v) {
-    asm volatile("red.relaxed.gpu.global.add.f64 [%0], %1;" ::"l"(__cvta_generic_to_global(p)), "d"(v) : "memory");
-}
-
 // rows [r0, r0 + cnt) of an upper-triangle matrix, after Y = diag X
 // (diag_rows, the phase before): each stored H_ij (j > i) adds H_ij X[j] to
 // row i's sum and H_ij X[i] to Y[j] with an atomic add; the row sums are then

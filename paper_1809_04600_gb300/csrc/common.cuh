@@ -71,6 +71,15 @@ struct DevBuf {
 
 // ---------------------------------------------------------------- device helpers
 
+// *p += v as a global-memory reduction (no result returned).  For a pointer
+// the compiler cannot place in global memory (one read from a struct in
+// memory or a struct argument), atomicAdd compiles to a returning atomic that
+// waits for L2 (measured in the batched solver: every scatter made a round
+// trip, 1.4x slower); red.global does not wait.  p must point to global memory.
+__device__ __forceinline__ void red_add(double *p, double v) {
+    asm volatile("red.relaxed.gpu.global.add.f64 [%0], %1;" ::"l"(__cvta_generic_to_global(p)), "d"(v) : "memory");
+}
+
 __device__ __forceinline__ int popc2(uint64_t a, uint64_t b) { return __popcll(a ^ b); }
 
 template <int W>

@@ -216,7 +216,7 @@ __device__ __forceinline__ void grad_pair(const DevInts &I, double *__restrict__
         move_info<W>(si, sj, pq_b, neg_b);
         const int pq_a = ctx >> 2;
         const int hi = pq_a > pq_b ? pq_a : pq_b, lo = pq_a > pq_b ? pq_b : pq_a;
-        atomicAdd(&geri[(int64_t)hi * (hi + 1) / 2 + lo], flip_sign(w2, ((ctx >> 1) & 1) + neg_b));
+        red_add(&geri[(int64_t)hi * (hi + 1) / 2 + lo], flip_sign(w2, ((ctx >> 1) & 1) + neg_b));
         return;
     }
     const int n = I.n;
@@ -234,22 +234,22 @@ __device__ __forceinline__ void grad_pair(const DevInts &I, double *__restrict__
         for (int k = 0; k < W; k++) common.w[k] = si.w[k] & sj.w[k];
         const int neg = bits_between<W>(common, p < q ? p : q, p < q ? q : p);
         const double sw = flip_sign(w, neg), sw2 = flip_sign(w2, neg);
-        atomicAdd(&gdh[p * n + q], sw);
-        atomicAdd(&gdh[q * n + p], sw);
+        red_add(&gdh[p * n + q], sw);
+        red_add(&gdh[q * n + p], sw);
 #pragma unroll
         for (int k = 0; k < W; k++) {
             uint64_t m = common.w[k];
             while (m) {
                 const int b = 64 * k + __ffsll((long long)m) - 1;
                 m &= m - 1;
-                atomicAdd(&geri[eri_slot(p, q, b, b)], sw2);
-                atomicAdd(&geri[eri_slot(p, b, b, q)], -sw2);
+                red_add(&geri[eri_slot(p, q, b, b)], sw2);
+                red_add(&geri[eri_slot(p, b, b, q)], -sw2);
             }
             uint64_t o = other.w[k];
             while (o) {
                 const int b = 64 * k + __ffsll((long long)o) - 1;
                 o &= o - 1;
-                atomicAdd(&geri[eri_slot(p, q, b, b)], sw2);
+                red_add(&geri[eri_slot(p, q, b, b)], sw2);
             }
         }
         return;
@@ -262,8 +262,8 @@ __device__ __forceinline__ void grad_pair(const DevInts &I, double *__restrict__
     flip_bit<W>(x, p1);
     neg += bits_between<W>(x, p2 < q2 ? p2 : q2, p2 < q2 ? q2 : p2);
     const double sw2 = flip_sign(w2, neg);
-    atomicAdd(&geri[eri_slot(p1, q1, p2, q2)], sw2);
-    atomicAdd(&geri[eri_slot(p1, q2, p2, q1)], -sw2);
+    red_add(&geri[eri_slot(p1, q1, p2, q2)], sw2);
+    red_add(&geri[eri_slot(p1, q2, p2, q1)], -sw2);
 }
 
 // ---------------------------------------------------------------- per-row state
