@@ -623,12 +623,13 @@ static void count_w(shci_ctx *c, bool upper) {
     c->i64a.alloc((size_t)n + 1);
     c->i64c.alloc((size_t)scan_tmp_len(n + 1));
     EnumArgs A = enum_args(c);
-    A.upper_only = upper ? 1 : 0;
     A.cand = cand.p;
     A.cnt = c->cnt_b.p;
-    launch_enum<W, ENUM_COUNT, 0>(c, A, I, false);
+    if (upper) launch_enum<W, ENUM_COUNT_UP, 0>(c, A, I, false);
+    else launch_enum<W, ENUM_COUNT, 0>(c, A, I, false);
     A.cnt = c->i64a.p;
-    launch_enum<W, ENUM_COUNT, 0>(c, A, I, true);
+    if (upper) launch_enum<W, ENUM_COUNT_UP, 0>(c, A, I, true);
+    else launch_enum<W, ENUM_COUNT, 0>(c, A, I, true);
     k_add_i64<<<grid_for(n), 256, 0, st>>>(c->i64a.p, c->cnt_b.p, n);
     KERNEL_CHECK();
     LAUNCHED(1);
@@ -656,14 +657,15 @@ static void store_w(shci_ctx *c, int mode) {
     c->val.alloc((size_t)std::max<int64_t>(nnz, 1));
     DevInts I = dev_ints(c);
     EnumArgs A = enum_args(c);
-    A.upper_only = upper ? 1 : 0;
     A.rowptr = c->rowptr.p;
     A.col = c->col.p;
     A.val = c->val.p;
     A.part_off = nullptr;
-    launch_enum<W, ENUM_FILL, 0>(c, A, I, false);
+    if (upper) launch_enum<W, ENUM_FILL_UP, 0>(c, A, I, false);
+    else launch_enum<W, ENUM_FILL, 0>(c, A, I, false);
     A.part_off = c->cnt_b.p;
-    launch_enum<W, ENUM_FILL, 0>(c, A, I, true);
+    if (upper) launch_enum<W, ENUM_FILL_UP, 0>(c, A, I, true);
+    else launch_enum<W, ENUM_FILL, 0>(c, A, I, true);
     CUDA_TRY(cudaStreamSynchronize(c->st));
 }
 

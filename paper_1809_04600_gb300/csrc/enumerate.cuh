@@ -29,15 +29,22 @@ constexpr int ENUM_QCAP = 64;               // per-warp queue of found pairs
 
 // ENUM_COUNT_INC / ENUM_FILL_INC: count / fill for the incremental update
 // (rows from separate member lists and item ranges; with n_old > 0 the items
-// hold old rows only, which take only the new candidates)
-enum { ENUM_COUNT = 0, ENUM_FILL = 1, ENUM_SIGMA = 2, ENUM_GRAD = 3, ENUM_COUNT_INC = 4, ENUM_FILL_INC = 5 };
+// hold old rows only, which take only the new candidates).
+// ENUM_COUNT_UP / ENUM_FILL_UP: count / fill of the upper triangle (pairs
+// j > i only); the incremental modes take that choice from EnumArgs::upper_only.
+enum {
+    ENUM_COUNT = 0, ENUM_FILL = 1, ENUM_SIGMA = 2, ENUM_GRAD = 3, ENUM_COUNT_INC = 4, ENUM_FILL_INC = 5,
+    ENUM_COUNT_UP = 6, ENUM_FILL_UP = 7
+};
 
 template <int MODE>
 struct ModeOf {
-    static constexpr bool count = MODE == ENUM_COUNT || MODE == ENUM_COUNT_INC;
-    static constexpr bool fill = MODE == ENUM_FILL || MODE == ENUM_FILL_INC;
+    static constexpr bool count = MODE == ENUM_COUNT || MODE == ENUM_COUNT_INC || MODE == ENUM_COUNT_UP;
+    static constexpr bool fill = MODE == ENUM_FILL || MODE == ENUM_FILL_INC || MODE == ENUM_FILL_UP;
     static constexpr bool inc = MODE == ENUM_COUNT_INC || MODE == ENUM_FILL_INC;
+    static constexpr bool up = MODE == ENUM_COUNT_UP || MODE == ENUM_FILL_UP;
 };
+
 
 constexpr int GRAD_REPLICAS = 32;           // gradient copies that spread the atomics
 
@@ -77,8 +84,8 @@ struct EnumArgs {
     const int32_t *item_first;              // work item -> first member offset within the group
     int64_t n_items;
     int *work_counter;
-    // count / fill: with upper_only set, only the pairs j > i of each row
-    // (the upper triangle) are counted and stored
+    // incremental count / fill: with upper_only set, only the pairs j > i of
+    // each row (the upper triangle) are counted and stored
     int upper_only;
     // count
     int64_t *cnt;                           // entries per row of this kernel's part
@@ -99,6 +106,13 @@ struct EnumArgs {
     double *geri;                           // [GRAD_REPLICAS][packed length]
     int64_t geri_len;
 };
+
+// pairs j > i only: always in the upper-triangle modes, by the run-time flag in
+// the incremental ones, never otherwise (compiled away there)
+template <int MODE>
+__device__ __forceinline__ bool upper_only(const EnumArgs &A) {
+    return ModeOf<MODE>::up || (ModeOf<MODE>::inc && A.upper_only != 0);
+}
 
 // ---------------------------------------------------------------- matrix element pieces
 
@@ -339,7 +353,7 @@ __device__ __forceinline__ void emit(RowAcc<MODE, K> &R, const EnumArgs &A, cons
                                      const Str<W> &si, const Str<W> &other, bool match, int32_t j, const Str<W> &sj,
                                      int ctx) {
     const int lane = threadIdx.x & 31;
-    if ((ModeOf<MODE>::count || ModeOf<MODE>::fill) && A.upper_only) match = match && (int64_t)j > R.i;
+    if (upper_only<MODE>(A)) match = match && (int64_t)j > R.i;
     const unsigned mask = __ballot_sync(0xffffffffu, match);
     const int nm = __popc(mask);
     R.found += nm;
@@ -474,7 +488,7 @@ __device__ __forceinline__ void enum_alpha_item(const EnumArgs &A, const DevInts
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     // member determinant indices: always outside the count modes; in them only
     // for an upper-triangle count (the filter compares j with the row)
-    const bool need_det = !ModeOf<MODE>::count || A.upper_only;
+    const bool need_det = !ModeOf<MODE>::count || upper_only<MODE>(A);
     constexpr bool XM = ModeOf<MODE>::inc;
     const int a = A.item_group[item];
     const int64_t g_beg = A.ga_off[a], g_len = A.ga_off[a + 1] - g_beg;
@@ -678,7 +692,7 @@ template <int W, int MODE, int K>
 __device__ __forceinline__ void enum_beta_item(const EnumArgs &A, const DevInts &I, int64_t item, Tile<W> &T,
                                                WarpQueue<W> &Q, unsigned long long &cand_local, int k_active = 0) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const bool need_det = !ModeOf<MODE>::count || A.upper_only;
+    const bool need_det = !ModeOf<MODE>::count || upper_only<MODE>(A);
     constexpr bool XM = ModeOf<MODE>::inc;
     const int b = A.item_group[item];
     const int64_t g_beg = A.gb_off[b], g_len = A.gb_off[b + 1] - g_beg;
