@@ -872,6 +872,10 @@ void extend(shci_ctx *c, int64_t n_new, const uint64_t *new_dets, int mem, doubl
     CUDA_TRY(cudaEventRecord(e0, c->st));
     if (incremental) incremental = W == 1 ? extend_w<1>(c, n_old) : extend_w<2>(c, n_old);
     if (!incremental) {
+        // the rebuild replaces the stored matrix: release it first, so that
+        // SHCI_AUTO decides against the memory the new one can have
+        c->col.reset();
+        c->val.reset();
         const int mode = c->mode_req == SHCI_AUTO ? SHCI_AUTO : c->mode;
         if (W == 1) build_w<1>(c, mode);
         else build_w<2>(c, mode);

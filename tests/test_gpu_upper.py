@@ -154,6 +154,50 @@ def test_auto_picks_the_upper_triangle_when_memory_is_short(P, oracle_mod):
     A.close()
 
 
+def test_auto_growth_that_no_longer_fits_rebuilds(P, oracle_mod):
+    """SHCI_AUTO, both triangles stored, grown incrementally (threshold 1.0) with
+    free memory at which the grown matrix's both triangles do not fit but its
+    upper triangle does: the update gives up and V is rebuilt (the old matrix
+    released first), in the best form that then fits; the result matches the
+    oracle."""
+    cfg, h, eri, ec, dets = G.system("sel_24o_6a6b_1m")
+    n0 = 600000
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    C = G.Built(P, h, eri, ec, dets, cfg.n_alpha, cfg.n_beta, mode=P.SHCI_ON_THE_FLY)
+    nnz_all = C.nnz
+    need = 12.0 * 2 * nnz_all                     # the grown space's both triangles
+    C.close()
+    A = G.Built(P, h, eri, ec, dets[:n0], cfg.n_alpha, cfg.n_beta, mode=P.SHCI_AUTO)
+    assert A.stats()["mode"] == P.SHCI_STORED
+    torch.cuda.synchronize()
+    free = torch.cuda.mem_get_info()[0]
+    # the update's lists and counts take well under 0.5 GB here: 0.8 x the free
+    # memory at its decision lies between the upper triangle (0.5 need) and need
+    target = int(0.9375 * need) + (512 << 20)
+    assert need > (1 << 30) and free > target + (1 << 30)
+    blocker = torch.empty(free - target, dtype=torch.uint8, device="cuda")
+    try:
+        nnz = P.shci_extend_connectivity(A.ctx.handle, G.dev(dets[n0:]), 1.0)
+        st = A.stats()
+        assert st["extend_incremental"] == 0               # gave up the update and rebuilt V
+        assert st["mode"] in (P.SHCI_STORED, P.SHCI_STORED_UPPER)
+        assert nnz == nnz_all and st["n_det"] == dets.shape[0]
+        A.dets, A.n, A.nnz = dets, dets.shape[0], nnz
+        O = oracle_mod.System(h, eri, ec)
+        c = S.random_vectors(dets.shape[0], 2, 8)
+        got = A.sigma(c)
+        rows = np.unique(np.linspace(0, dets.shape[0] - 1, 24).astype(np.int64))
+        orc = O.sigma_rows(dets, c, rows)
+        scale = G.row_scale(O, dets, c, rows)
+        assert np.all(np.abs(got[:, rows] - orc) <= SIGMA_REL * scale + 1e-300)
+        A.close()
+    finally:
+        del blocker
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+
+
 def _batch_systems(n_sys, cap, seed):
     out = []
     for cfg in S.batch_configs(n_sys=n_sys, seed=seed):
