@@ -119,9 +119,21 @@ def replica_totals(dist, seconds, units, device="cpu"):
     return float(t.item()), float(u.item())
 
 
-def kernel_source_digest(path):
+# the stored-sigma kernel's source region in csrc/sigma.cu: its shape macros,
+# k_sigma_stored and its launch (edits elsewhere in the file leave it alone)
+STORED_SIGMA_REGION = ("#ifndef SHCI_SIGMA_R2", "template <bool INTER>\nstatic void dispatch_stored")
+
+
+def kernel_source_digest(path, region=None):
+    """First 16 hex digits of the SHA-256 of a source file, or of the text
+    between two markers of it (the first marker included)."""
     import hashlib
-    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+    text = open(path, "rb").read()
+    if region is not None:
+        a = text.index(region[0].encode())
+        b = text.index(region[1].encode(), a)
+        text = text[a:b]
+    return hashlib.sha256(text).hexdigest()[:16]
 
 
 def sigma_traffic(workload, stored_nnz):
@@ -134,7 +146,7 @@ def sigma_traffic(workload, stored_nnz):
         return None
     try:
         tj = json.load(open(tpath))
-        if tj.get("kernel_source_sha256_16") != kernel_source_digest(src):
+        if tj.get("kernel_source_sha256_16") != kernel_source_digest(src, STORED_SIGMA_REGION):
             return None
         return float(tj["dram_bytes_per_stored_nnz"]) * stored_nnz
     except Exception:
