@@ -172,7 +172,8 @@ int shci_sigma(shci_ctx *ctx, int k, const double *c, double *sigma, int mem_spa
  * with lazy module loading the array's memory is taken there and no call of
  * this entry point allocates.  Should that look-up fail in shci_create, the
  * first call on the device retries it (and reports a failure as
- * SHCI_ERR_CUDA); that first call should then come before any stream capture.
+ * SHCI_ERR_CUDA), and that call then loads the module and takes the array's
+ * memory itself.
  * Requirements: built in SHCI_STORED mode (SHCI_ERR_STATE otherwise), k in
  * [1, 8], k * n_det <= 524,288 (SHCI_ERR_INVALID otherwise, before any
  * launch), c and sigma device [k][n_det], not overlapping.  All calls share

@@ -20,7 +20,7 @@
 //    loading (CUDA 12's default) the module holding the array is loaded --
 //    and its 8 MiB taken -- when a context is created, not inside a call.  If
 //    that look-up failed at shci_create, the first call on the device retries
-//    it; that first call should then come before any stream capture.
+//    it, and that call then loads the module and takes the 8 MiB itself.
 //  - the call restores the caller's current device before returning.
 //  - every call shares the one array: calls that overlap on the GPU (other
 //    streams, other contexts, other host threads) race on it.
