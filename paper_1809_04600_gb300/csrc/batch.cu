@@ -28,6 +28,7 @@
 
 #include "enum_launch.cuh"
 #include "jacobi.cuh"
+#include "plan.h"
 
 namespace shci {
 
@@ -1326,36 +1327,14 @@ int shci_batch_create(shci_ctx *ctx, int n_sys, const shci_system_desc *systems,
             b->stats.total_det += c->n_det;
             b->stats.total_nnz_upper += c->nnz_upper;
         }
-        // the storage plan: 12 bytes per stored nonzero, systems by ascending
-        // pair count; all upper triangles if they fit, then both triangles for
-        // as many as the rest of the budget takes; else upper triangles while
-        // they fit
+        // the storage plan (plan.h) within the budget and 80 % of the free memory
         size_t free_b = 0, total_b = 0;
         CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
         double left = 0.8 * (double)free_b;
         if (stored_budget_bytes >= 0.0) left = std::min(left, stored_budget_bytes);
-        std::vector<int> order(n_sys);
-        for (int s = 0; s < n_sys; s++) order[s] = s;
-        std::stable_sort(order.begin(), order.end(),
-                         [&](int x, int y) { return b->subs[x]->nnz_upper < b->subs[y]->nnz_upper; });
-        double all_upper = 0.0;
-        for (auto *c : b->subs) all_upper += 12.0 * (double)c->nnz_upper;
-        b->modes.assign(n_sys, SHCI_ON_THE_FLY);
-        if (all_upper <= left) {
-            left -= all_upper;
-            for (int s : order) {
-                const double extra = 12.0 * (double)b->subs[s]->nnz_upper;
-                b->modes[s] = extra <= left ? SHCI_STORED : SHCI_STORED_UPPER;
-                if (extra <= left) left -= extra;
-            }
-        } else {
-            for (int s : order) {
-                const double need = 12.0 * (double)b->subs[s]->nnz_upper;
-                if (need > left) break;
-                b->modes[s] = SHCI_STORED_UPPER;
-                left -= need;
-            }
-        }
+        std::vector<int64_t> pairs;
+        for (auto *c : b->subs) pairs.push_back(c->nnz_upper);
+        b->modes = shci::storage_plan(pairs, left);
         // pass 2: store, and describe each system to the kernel
         for (int s = 0; s < n_sys; s++) {
             shci_ctx *c = b->subs[s];
