@@ -155,7 +155,9 @@ int shci_get_row(shci_ctx *ctx, int64_t row, int64_t cap, int64_t *cols, double 
 
 /* sigma = H c for k vectors (k in [1, 8]), c and sigma [k][n_det] (Sec. V.B:
  * the matrix-vector product of the Davidson step).  Uses the stored H, or the
- * on-the-fly product in SHCI_ON_THE_FLY mode.  c and sigma must not overlap. */
+ * on-the-fly product in SHCI_ON_THE_FLY mode.  c and sigma must not overlap.
+ * Repeated calls give bitwise-identical results except in SHCI_STORED_UPPER
+ * mode, whose atomic adds change the summation order (a few ulp). */
 int shci_sigma(shci_ctx *ctx, int k, const double *c, double *sigma, int mem_space);
 
 /* sigma = H c like shci_sigma, for device pointers only, with no device
